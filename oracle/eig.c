@@ -11,8 +11,11 @@
  *   3. implicit Francis double-shift QR iteration on the unreduced trailing
  *      block, eigenvalues only (Golub and Van Loan, "Matrix Computations",
  *      Sections 7.4-7.5), with deflation when a subdiagonal entry is
- *      negligible against its two diagonal neighbours and ad hoc exceptional
- *      shifts after 10 and 20 iterations without deflation.
+ *      negligible (at most eps times the sum of its two diagonal neighbours,
+ *      or eps times the largest entry of the Hessenberg matrix when both are
+ *      zero) and ad hoc exceptional shifts after 10 and 20 iterations without
+ *      deflation.  Householder vectors follow the textbook house(): the norm
+ *      below the leading entry is summed directly.
  * No LAPACK.  Pinned in tests/test_oracle_eig.py against 2x2 swing-equation
  * closed forms, companion matrices with known roots, planted spectra
  * V diag V^-1, trace identities and (test-only) numpy.linalg.eigvals.
@@ -56,11 +59,11 @@ static void balance(int n, double* a)
 static void hessenberg(int n, double* a, double* v)
 {
     for (int k = 0; k + 2 < n; ++k) {
-        double nrm2 = 0.0;
-        for (int i = k + 1; i < n; ++i) nrm2 += A_(i, k) * A_(i, k);
-        double tail = nrm2 - A_(k + 1, k) * A_(k + 1, k);
+        double tail = 0.0;                       /* squared norm below the subdiagonal */
+        for (int i = k + 2; i < n; ++i) tail += A_(i, k) * A_(i, k);
         if (tail == 0.0) continue;               /* already zero below the subdiagonal */
         double x0 = A_(k + 1, k);
+        double nrm2 = x0 * x0 + tail;
         double alpha = (x0 >= 0.0) ? -sqrt(nrm2) : sqrt(nrm2);
         int m = n - k - 1;
         v[0] = x0 - alpha;
@@ -127,6 +130,11 @@ static int house3(int len, const double* x, double* u, double* beta)
 static int hqr(int n, double* a, double* wr, double* wi, int* sweeps_out)
 {
     const double eps = 2.220446049250313e-16;
+    /* scale for the deflation test when both diagonal neighbours are zero */
+    double hmax = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = (i > 0 ? i - 1 : 0); j < n; ++j)
+            if (fabs(A_(i, j)) > hmax) hmax = fabs(A_(i, j));
     int hi = n - 1;
     int its = 0, total = 0;
     while (hi >= 0) {
@@ -134,10 +142,7 @@ static int hqr(int n, double* a, double* wr, double* wi, int* sweeps_out)
         int lo = hi;
         while (lo > 0) {
             double s = fabs(A_(lo - 1, lo - 1)) + fabs(A_(lo, lo));
-            if (s == 0.0) {
-                for (int i = 0; i <= hi; ++i)
-                    for (int j = (i > 0 ? i - 1 : 0); j <= hi; ++j) s += fabs(A_(i, j));
-            }
+            if (s == 0.0) s = hmax;
             if (fabs(A_(lo, lo - 1)) <= eps * s) { A_(lo, lo - 1) = 0.0; break; }
             --lo;
         }
