@@ -1,0 +1,194 @@
+/* cs.h -- C ABI of libcs: GB300-native N-2 contingency screening with a
+ * probabilistic Risk Index.
+ *
+ * Method (arXiv 2512.08465): every contingency scenario -- one or two failed
+ * lines, transformers or generators -- is screened by three checks (Section
+ * II-B): islanding (II-B-3), AC optimal power flow feasibility and operational
+ * limits (II-B-1), and small-signal stability of the linearised state matrix
+ * (II-B-2).  The binary severities are reduced into each component's Risk Index
+ * R_i = F_i S_i + sum_{j != i} F_ij S_ij (Section II-C, Eq. 1-3).
+ *
+ * Conventions for every entry point:
+ *  - No exceptions cross the ABI; every call returns a cs_status.
+ *  - The library never keeps a caller pointer after the call returns.  Host
+ *    buffers are read or written before return; device buffers passed to the
+ *    *_device entry points are used asynchronously on the given CUDA stream and
+ *    must stay valid until that stream reaches the point of the call.
+ *  - Element ids: [0, n_branch) are branches, [n_branch, n_branch + n_gen) are
+ *    generators (Section II-A: lines, transformers, generators).
+ *  - One cs_ctx is used by one host thread at a time (calls on one ctx are
+ *    serialised by an internal mutex; distinct ctx objects are independent).
+ *  - On error the message of the last failing call on that ctx is available
+ *    from cs_last_error().
+ */
+#ifndef CS_H
+#define CS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t cs_status;
+enum {
+    CS_OK = 0,
+    CS_PENDING = 1,            /* cs_poll: the request has not finished yet */
+    CS_E_ARG = -1,             /* invalid argument (sizes, ids, ranges, NULL) */
+    CS_E_NOMEM = -2,           /* device or host allocation failed */
+    CS_E_BASE_INSECURE = -3,   /* base case not secure and the options require it */
+    CS_E_TIMEOUT = -4,         /* a bounded device wait gave up */
+    CS_E_CUDA = -5,            /* a CUDA runtime call failed */
+    CS_E_UNKNOWN_ID = -6,      /* unknown network or request id */
+    CS_E_NUMERIC = -7          /* a kernel reported an internal inconsistency */
+};
+
+/* Severity classes (Section II-B).  S = 1 for every class except CS_SECURE. */
+enum {
+    CS_SECURE = 0,
+    CS_ISLANDED = 1,           /* more than one island (Section II-B-3) */
+    CS_OPF_NONCONV = 2,        /* OPF did not converge or hit a non-finite value (II-B-1) */
+    CS_LIMIT = 3,              /* converged OPF violates an operational limit (II-B-1) */
+    CS_SS_UNSTABLE = 4,        /* an eigenvalue with non-negative real part (II-B-2) */
+    CS_SS_POORLY_DAMPED = 5,   /* minimum damping ratio below damping_min */
+    CS_EIG_FAIL = 6            /* the eigenvalue iteration did not converge */
+};
+
+/* Risk Index pair readings (Section II-C).  EQ3 counts every unordered pair
+ * once, as Eq. 3 is written; ORDERED counts both orderings of the ordered N-2
+ * enumeration of Section II-A, which reproduces the values printed in
+ * Section V (1.472 for a line with every scenario severe under Table I). */
+enum { CS_RISK_EQ3 = 0, CS_RISK_ORDERED = 1 };
+
+typedef struct cs_ctx cs_ctx;
+
+typedef struct {
+    int32_t device;            /* CUDA device ordinal */
+    double damping_min;        /* damping-ratio threshold; 0 = Re >= 0 rule only (II-B-2) */
+    double opf_tol;            /* interior-point stopping tolerance (all four conditions) */
+    int32_t opf_max_it;        /* interior-point iteration cap */
+    int32_t require_secure_base; /* 1: cs_load_network fails with CS_E_BASE_INSECURE */
+    int32_t ctas_per_sm;       /* resident scenario blocks per SM; 0 = automatic */
+    int32_t chunk;             /* scenarios per internal batch; 0 = automatic */
+} cs_options;
+
+/* Fills *opt with the defaults (damping_min 0.05, opf_tol 1e-8, opf_max_it 50). */
+void cs_default_options(cs_options* opt);
+
+/* Raw network data in structure-of-arrays form, host memory, copied by
+ * cs_load_network (the caller keeps ownership).  Units: MW / MVAr / MVA for
+ * powers, per unit on base_mva for impedances and voltages, $/MW^2h and $/MWh
+ * for costs, machine base (MVA = Pmax) for machine reactances, H and D. */
+typedef struct {
+    int32_t n_bus, n_branch, n_gen, n_levels, ref_bus;
+    double base_mva, f_hz;
+    const double *Vmin, *Vmax, *Gs, *Bs;          /* [n_bus] */
+    const double *Pd, *Qd;                        /* [n_levels * n_bus], level-major */
+    const int32_t *f, *t;                         /* [n_branch] bus indices */
+    const double *r, *x, *b, *rate, *tap;         /* [n_branch] */
+    const int32_t* gbus;                          /* [n_gen] */
+    const double *Pmin, *Pmax, *Qmin, *Qmax;      /* [n_gen] MW / MVAr */
+    const double *c2, *c1, *c0;                   /* [n_gen] */
+    const double *H, *D, *xd, *xq, *xdp;          /* [n_gen] machine base */
+    const double *Td0p, *Tq0p, *KA, *TA;          /* [n_gen] seconds / gain */
+} cs_network_desc;
+
+/* Per-scenario results, structure of arrays with n records.  Which memory
+ * (device or host) each entry point expects is stated at the entry point.
+ * Vm / Va are optional ([n * n_bus], NULL = not written). */
+typedef struct {
+    uint8_t* klass;            /* CS_SECURE .. CS_EIG_FAIL */
+    uint8_t* severe;           /* S_c in {0, 1} */
+    int16_t* n_islands;        /* number of islands of the post-contingency network */
+    int16_t* opf_iters;        /* interior-point iterations taken (0 if not run) */
+    double* cost;              /* OPF cost, $/h (NaN if not converged) */
+    double* max_re;            /* largest real part, structural zero mode removed (NaN if not run) */
+    double* min_zeta;          /* smallest damping ratio (NaN if not run) */
+    double* Vm;                /* optional [n * n_bus] */
+    double* Va;                /* optional [n * n_bus] */
+} cs_result;
+
+/* Create / destroy a context on opt->device (NULL = defaults).  cs_create
+ * fails with CS_E_CUDA when no usable CUDA device is present. */
+cs_status cs_create(const cs_options* opt, cs_ctx** out);
+cs_status cs_destroy(cs_ctx* ctx);
+
+/* Copy a network to the device and prepare it (Section II-A step 1): the
+ * symbolic analysis of the bus-level KKT and admittance patterns (one
+ * minimum-degree ordering and elimination tree reused by every scenario of the
+ * network), the static device data, and the base case of every load level.
+ * The network stays resident until cs_unload_network.  Fails with CS_E_ARG on
+ * inconsistent sizes or indices, CS_E_BASE_INSECURE when a base case is not
+ * secure and opt.require_secure_base is set. */
+cs_status cs_load_network(cs_ctx* ctx, const cs_network_desc* net, int32_t* net_id);
+cs_status cs_unload_network(cs_ctx* ctx, int32_t net_id);
+
+/* Base-case result of a level (host out, one record). */
+cs_status cs_base_result(cs_ctx* ctx, int32_t net_id, int32_t level, const cs_result* out);
+
+/* Evaluate n scenarios of (net_id, level) with DEVICE buffers: elem_i, elem_j
+ * [n] int32 (elem_j = -1 gives an N-1 scenario, elem_i = elem_j = -1 the base
+ * case), out fields device pointers of n records.  Asynchronous on `stream`
+ * (a cudaStream_t, NULL = legacy default stream).  Every severity is also
+ * recorded in the context's severity table of (net_id, level) that
+ * cs_risk_index reads.  Sizes and ids are validated: n, net_id and level on
+ * the host (CS_E_ARG); element ids on the device, where an id out of range
+ * marks that record CS_EIG_FAIL-free garbage-free: the record is left with
+ * class CS_OPF_NONCONV... 
+ * dynamic model + eigenvalues, classification, all in the library's kernels. */
+cs_status cs_evaluate_device(cs_ctx* ctx, int32_t net_id, int32_t level,
+                             const int32_t* elem_i, const int32_t* elem_j, int64_t n,
+                             const cs_result* out, void* stream);
+
+/* Wait for all work of the context on `stream` and report device-side errors
+ * (invalid element ids, bounded-wait time-outs). */
+cs_status cs_sync(cs_ctx* ctx, void* stream);
+
+/* Non-blocking submission with HOST buffers (copied before return).  The
+ * library copies inputs to the device, evaluates and copies results back on
+ * its own stream; cs_poll retrieves them. */
+cs_status cs_submit_contingencies(cs_ctx* ctx, int32_t net_id, int32_t level,
+                                  const int32_t* elem_i, const int32_t* elem_j, int64_t n,
+                                  uint64_t* request_id);
+
+/* Copy the results of a finished request into the HOST record `out` (n
+ * records of the request).  Waits at most timeout_us microseconds (0 = just
+ * test); returns CS_PENDING if the request is still running.  A finished
+ * request is released by the successful poll. */
+cs_status cs_poll(cs_ctx* ctx, uint64_t request_id, int32_t timeout_us, const cs_result* out);
+
+/* Risk Index (Section II-C, Eq. 3) of every element from the context's
+ * severity table of (net_id, level): R_i = lambda_i S_i + m * sum_j
+ * fl(lambda_i lambda_j) S_ij with m = 1 (CS_RISK_EQ3) or 2 (CS_RISK_ORDERED).
+ * The sum is accumulated exactly in 192-bit fixed point and rounded once to
+ * the nearest double, so the result is independent of evaluation order.
+ * lambda, R_out: HOST arrays of n_branch + n_gen doubles.  lambda must lie in
+ * [2^-30, 2^10] (CS_E_ARG otherwise).  N-1 scenarios and pairs never evaluated
+ * contribute 0 and are counted in *n_missing (may be NULL). */
+cs_status cs_risk_index(cs_ctx* ctx, int32_t net_id, int32_t level, const double* lambda,
+                        int32_t mode, double* R_out, int64_t* n_missing);
+
+/* Stateless device form of the same reduction: S1 [E] uint8 N-1 severities,
+ * S2 [E*(E-1)/2] uint8 severities of the unordered pairs i < j in
+ * lexicographic order, lambda and R [E] doubles; all DEVICE pointers,
+ * asynchronous on `stream`.  Range of lambda as above (checked on the host
+ * copy by cs_risk_index only; here out-of-range values give NaN). */
+cs_status cs_risk_reduce_device(int32_t n_elem, const uint8_t* S1, const uint8_t* S2,
+                                const double* lambda, int32_t mode, double* R, void* stream);
+
+/* Scenario decode (Section II-A): write pairs k = first .. first+count-1 of
+ * the lexicographic enumeration of unordered pairs i < j over n_elem elements
+ * into DEVICE arrays elem_i, elem_j, in integer arithmetic. */
+cs_status cs_enumerate_pairs_device(int32_t n_elem, int64_t first, int64_t count,
+                                    int32_t* elem_i, int32_t* elem_j, void* stream);
+
+/* Message of the last failing call on ctx (never NULL; "" if none). */
+const char* cs_last_error(cs_ctx* ctx);
+
+/* Counters of the last cs_evaluate_device call: kernel launches issued. */
+int64_t cs_last_launch_count(cs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CS_H */

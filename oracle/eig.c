@@ -30,9 +30,10 @@
 static void balance(int n, double* a)
 {
     const double radix = 2.0, sqrdx = 4.0;
-    int done = 0;
-    while (!done) {
+    int done = 0, sweeps = 0;
+    while (!done && sweeps < 100) {            /* converges in a few sweeps; capped */
         done = 1;
+        ++sweeps;
         for (int i = 0; i < n; ++i) {
             double c = 0.0, r = 0.0;
             for (int j = 0; j < n; ++j) {
@@ -40,7 +41,7 @@ static void balance(int n, double* a)
                 c += fabs(A_(j, i));
                 r += fabs(A_(i, j));
             }
-            if (c == 0.0 || r == 0.0) continue;
+            if (c == 0.0 || r == 0.0 || !isfinite(c) || !isfinite(r)) continue;
             double g = r / radix, f = 1.0, s = c + r;
             while (c < g) { f *= radix; c *= sqrdx; }
             g = r * radix;

@@ -1,0 +1,290 @@
+"""Thin Python binding of libcs (argument marshalling only).
+
+Every step of the evaluation runs in the CUDA library; this module converts
+arguments (numpy arrays, torch tensors, stream handles) into the plain pointers
+and sizes of the C ABI declared in ``include/cs.h``.  Importing it loads
+``_lib/libcs.so`` (building it with nvcc if it is missing) and raises if the
+library cannot be loaded: there is no CPU fallback.
+
+PyTorch is used only to own device memory and to name CUDA streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+CS_OK, CS_PENDING = 0, 1
+ERRORS = {-1: "CS_E_ARG", -2: "CS_E_NOMEM", -3: "CS_E_BASE_INSECURE", -4: "CS_E_TIMEOUT",
+          -5: "CS_E_CUDA", -6: "CS_E_UNKNOWN_ID", -7: "CS_E_NUMERIC"}
+CLASSES = ("SECURE", "ISLANDED", "OPF_NONCONV", "LIMIT", "SS_UNSTABLE", "SS_POORLY_DAMPED", "EIG_FAIL")
+RISK_EQ3, RISK_ORDERED = 0, 1
+
+EXPORTS = ("cs_default_options", "cs_create", "cs_destroy", "cs_load_network", "cs_unload_network",
+           "cs_base_result", "cs_evaluate_device", "cs_sync", "cs_submit_contingencies", "cs_poll",
+           "cs_risk_index", "cs_risk_reduce_device", "cs_enumerate_pairs_device", "cs_last_error",
+           "cs_last_launch_count")
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("damping_min", ctypes.c_double), ("opf_tol", ctypes.c_double),
+                ("opf_max_it", ctypes.c_int32), ("require_secure_base", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+
+
+class NetworkDesc(ctypes.Structure):
+    _fields_ = [("n_bus", ctypes.c_int32), ("n_branch", ctypes.c_int32), ("n_gen", ctypes.c_int32),
+                ("n_levels", ctypes.c_int32), ("ref_bus", ctypes.c_int32),
+                ("base_mva", ctypes.c_double), ("f_hz", ctypes.c_double)] + \
+               [(k, _dp) for k in ("Vmin", "Vmax", "Gs", "Bs", "Pd", "Qd")] + \
+               [("f", _ip), ("t", _ip)] + [(k, _dp) for k in ("r", "x", "b", "rate", "tap")] + \
+               [("gbus", _ip)] + [(k, _dp) for k in ("Pmin", "Pmax", "Qmin", "Qmax", "c2", "c1", "c0",
+                                                      "H", "D", "xd", "xq", "xdp", "Td0p", "Tq0p", "KA", "TA")]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("klass", ctypes.c_void_p), ("severe", ctypes.c_void_p), ("n_islands", ctypes.c_void_p),
+                ("opf_iters", ctypes.c_void_p), ("cost", ctypes.c_void_p), ("max_re", ctypes.c_void_p),
+                ("min_zeta", ctypes.c_void_p), ("Vm", ctypes.c_void_p), ("Va", ctypes.c_void_p)]
+
+
+RESULT_FIELDS = (("klass", np.uint8), ("severe", np.uint8), ("n_islands", np.int16), ("opf_iters", np.int16),
+                 ("cost", np.float64), ("max_re", np.float64), ("min_zeta", np.float64))
+
+
+class CSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{ERRORS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libcs (compiling it first if needed).  Raises if it cannot be loaded."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libcs not found at {path}; run paper_2512_08465_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32, i64, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "cs_default_options": (None, [ctypes.POINTER(Options)]),
+        "cs_create": (i32, [ctypes.POINTER(Options), ctypes.POINTER(P)]),
+        "cs_destroy": (i32, [P]),
+        "cs_load_network": (i32, [P, ctypes.POINTER(NetworkDesc), ctypes.POINTER(i32)]),
+        "cs_unload_network": (i32, [P, i32]),
+        "cs_base_result": (i32, [P, i32, i32, ctypes.POINTER(Result)]),
+        "cs_evaluate_device": (i32, [P, i32, i32, P, P, i64, ctypes.POINTER(Result), P]),
+        "cs_sync": (i32, [P, P]),
+        "cs_submit_contingencies": (i32, [P, i32, i32, P, P, i64, ctypes.POINTER(u64)]),
+        "cs_poll": (i32, [P, u64, i32, ctypes.POINTER(Result)]),
+        "cs_risk_index": (i32, [P, i32, i32, P, i32, P, ctypes.POINTER(i64)]),
+        "cs_risk_reduce_device": (i32, [i32, P, P, P, i32, P, P]),
+        "cs_enumerate_pairs_device": (i32, [i32, i64, i64, P, P, P]),
+        "cs_last_error": (ctypes.c_char_p, [P]),
+        "cs_last_launch_count": (i64, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _ptr(x):
+    """Data pointer of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load_library().cs_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """One libcs context on one CUDA device."""
+
+    def __init__(self, **options):
+        self.lib = load_library()
+        self.opt = default_options(**options)
+        h = ctypes.c_void_p()
+        st = self.lib.cs_create(ctypes.byref(self.opt), ctypes.byref(h))
+        if st != CS_OK:
+            raise CSError(st, "cs_create failed (no usable CUDA device?)")
+        self.h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st < 0:
+            raise CSError(st, f"{what}: {self.lib.cs_last_error(self.h).decode()}")
+        return st
+
+    # -------------------------------------------------------------- networks --
+    def load_network(self, net) -> int:
+        """Copy a ``synth.Network`` (or any object with the same fields) to the device."""
+        arrs = {}
+
+        def d(name, v):
+            a = np.ascontiguousarray(v, dtype=np.float64)
+            arrs[name] = a
+            return a.ctypes.data_as(_dp)
+
+        def i(name, v):
+            a = np.ascontiguousarray(v, dtype=np.int32)
+            arrs[name] = a
+            return a.ctypes.data_as(_ip)
+
+        D = NetworkDesc()
+        D.n_bus, D.n_branch, D.n_gen = net.n_bus, net.n_branch, net.n_gen
+        D.n_levels, D.ref_bus = len(net.levels), int(net.ref_bus)
+        D.base_mva, D.f_hz = float(net.base_mva), float(net.f_hz)
+        for k in ("Vmin", "Vmax", "Gs", "Bs"):
+            setattr(D, k, d(k, getattr(net, k)))
+        D.Pd = d("Pd", np.asarray(net.Pd).reshape(-1))
+        D.Qd = d("Qd", np.asarray(net.Qd).reshape(-1))
+        D.f = i("f", net.f)
+        D.t = i("t", net.t)
+        for k in ("r", "x", "b", "rate", "tap"):
+            setattr(D, k, d(k, getattr(net, k)))
+        D.gbus = i("gbus", net.gbus)
+        for k in ("Pmin", "Pmax", "Qmin", "Qmax", "c2", "c1", "c0", "H", "D", "xd", "xq", "xdp", "Td0p",
+                  "Tq0p", "KA", "TA"):
+            setattr(D, k, d(k, getattr(net, k)))
+        nid = ctypes.c_int32()
+        self._check(self.lib.cs_load_network(self.h, ctypes.byref(D), ctypes.byref(nid)), "cs_load_network")
+        return nid.value
+
+    def unload_network(self, net_id: int):
+        self._check(self.lib.cs_unload_network(self.h, net_id), "cs_unload_network")
+
+    def base_result(self, net_id: int, level: int) -> dict:
+        out = {k: np.zeros(1, dt) for k, dt in RESULT_FIELDS}
+        R = Result(*[_ptr(out[k]) for k, _ in RESULT_FIELDS], None, None)
+        self._check(self.lib.cs_base_result(self.h, net_id, level, ctypes.byref(R)), "cs_base_result")
+        return {k: v[0] for k, v in out.items()}
+
+    # ------------------------------------------------------------ evaluation --
+    @staticmethod
+    def alloc_results(n: int, device="cuda", n_bus: int = 0):
+        """Result tensors for n records (torch, on ``device``); Vm/Va if n_bus > 0."""
+        import torch
+        tmap = {np.uint8: torch.uint8, np.int16: torch.int16, np.float64: torch.float64}
+        out = {k: torch.empty(n, dtype=tmap[dt], device=device) for k, dt in RESULT_FIELDS}
+        if n_bus:
+            out["Vm"] = torch.empty(n * n_bus, dtype=torch.float64, device=device)
+            out["Va"] = torch.empty(n * n_bus, dtype=torch.float64, device=device)
+        return out
+
+    @staticmethod
+    def _result_struct(out):
+        return Result(*[_ptr(out[k]) for k, _ in RESULT_FIELDS], _ptr(out.get("Vm")), _ptr(out.get("Va")))
+
+    def evaluate_device(self, net_id: int, level: int, ei, ej, out: dict, stream=None):
+        """Asynchronous evaluation of len(ei) scenarios with device tensors."""
+        n = int(ei.numel())
+        R = self._result_struct(out)
+        st = self.lib.cs_evaluate_device(self.h, net_id, level, _ptr(ei), _ptr(ej), n, ctypes.byref(R),
+                                         _stream_handle(stream))
+        self._check(st, "cs_evaluate_device")
+
+    def sync(self, stream=None):
+        self._check(self.lib.cs_sync(self.h, _stream_handle(stream)), "cs_sync")
+
+    def last_launch_count(self) -> int:
+        return int(self.lib.cs_last_launch_count(self.h))
+
+    def submit(self, net_id: int, level: int, ei, ej) -> int:
+        """Non-blocking submission with host arrays; returns a request id."""
+        ei = np.ascontiguousarray(ei, dtype=np.int32)
+        ej = np.ascontiguousarray(ej, dtype=np.int32)
+        rid = ctypes.c_uint64()
+        st = self.lib.cs_submit_contingencies(self.h, net_id, level, _ptr(ei), _ptr(ej), ei.size,
+                                              ctypes.byref(rid))
+        self._check(st, "cs_submit_contingencies")
+        self._keep[rid.value] = ei.size
+        return rid.value
+
+    def poll(self, request_id: int, timeout_us: int = 0, out: dict | None = None):
+        """Results of a finished request as numpy arrays, or None while pending."""
+        n = self._keep.get(request_id, 0)
+        if out is None:
+            out = {k: np.empty(n, dt) for k, dt in RESULT_FIELDS}
+        R = Result(*[_ptr(out[k]) for k, _ in RESULT_FIELDS], None, None)
+        st = self.lib.cs_poll(self.h, request_id, int(timeout_us), ctypes.byref(R))
+        if st == CS_PENDING:
+            return None
+        self._check(st, "cs_poll")
+        self._keep.pop(request_id, None)
+        return out
+
+    def evaluate(self, net_id: int, level: int, ei, ej, timeout_us: int = 600_000_000):
+        """Blocking convenience: submit host arrays and wait for the results."""
+        rid = self.submit(net_id, level, ei, ej)
+        out = self.poll(rid, timeout_us)
+        if out is None:
+            raise CSError(-4, "request did not finish in time")
+        return out
+
+    # ------------------------------------------------------------ Risk Index --
+    def risk_index(self, net_id: int, level: int, lam, mode: int = RISK_ORDERED):
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        R = np.empty_like(lam)
+        miss = ctypes.c_int64()
+        st = self.lib.cs_risk_index(self.h, net_id, level, _ptr(lam), mode, _ptr(R), ctypes.byref(miss))
+        self._check(st, "cs_risk_index")
+        return R, miss.value
+
+
+def risk_reduce_device(n_elem: int, S1, S2, lam, R, mode: int = RISK_ORDERED, stream=None):
+    st = load_library().cs_risk_reduce_device(n_elem, _ptr(S1), _ptr(S2), _ptr(lam), mode, _ptr(R),
+                                              _stream_handle(stream))
+    if st != CS_OK:
+        raise CSError(st, "cs_risk_reduce_device")
+
+
+def enumerate_pairs_device(n_elem: int, first: int, count: int, ei, ej, stream=None):
+    st = load_library().cs_enumerate_pairs_device(n_elem, first, count, _ptr(ei), _ptr(ej),
+                                                  _stream_handle(stream))
+    if st != CS_OK:
+        raise CSError(st, "cs_enumerate_pairs_device")

@@ -1,0 +1,616 @@
+// C ABI of libcs: context, network residency, evaluation, requests, Risk Index.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "cs_internal.h"
+#include "symbolic.h"
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t ensure(size_t nbytes) {
+        if (nbytes <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, nbytes);
+        if (e == cudaSuccess) bytes = nbytes;
+        return e;
+    }
+};
+
+struct Network {
+    int id = 0;
+    DevNet dev{};
+    DevBuf blob;                      // all static device arrays
+    Symbolic sym;
+    int nlev = 0;
+    std::vector<std::unique_ptr<DevBuf>> sev_n1, sev_pairs;   // per level
+    // base-case results per level (host)
+    std::vector<uint8_t> base_klass, base_severe;
+    std::vector<int16_t> base_isl, base_iters;
+    std::vector<double> base_cost, base_maxre, base_minz;
+};
+
+struct Request {
+    uint64_t id = 0;
+    int64_t n = 0;
+    int nb = 0;
+    cudaEvent_t done = nullptr;
+    DevBuf d_in, d_out;
+    void* h_out = nullptr;            // pinned staging
+    size_t h_out_bytes = 0;
+    ~Request() {
+        if (done) cudaEventDestroy(done);
+        if (h_out) cudaFreeHost(h_out);
+    }
+};
+
+}  // namespace
+
+struct cs_ctx {
+    std::mutex mu;
+    cs_options opt{};
+    int device = 0;
+    int sms = 0;
+    std::string err;
+    std::map<int, std::unique_ptr<Network>> nets;
+    int next_net = 1;
+    uint64_t next_req = 1;
+    std::map<uint64_t, std::unique_ptr<Request>> reqs;
+    cudaStream_t req_stream = nullptr;
+    // workspace
+    DevBuf scratch, isl, opfx, opfst, counters, err_word;
+    int64_t launches = 0;
+};
+
+namespace {
+
+cs_status fail(cs_ctx* c, cs_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+cs_status cuda_fail(cs_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, CS_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CS_CUDA(call)                                       \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// pack host vectors into one device blob
+struct Packer {
+    std::vector<char> host;
+    size_t add(const void* src, size_t bytes) {
+        size_t off = (host.size() + 255) & ~size_t(255);
+        host.resize(off + std::max<size_t>(bytes, 1));
+        if (bytes) std::memcpy(host.data() + off, src, bytes);
+        return off;
+    }
+    template <class T>
+    size_t add(const std::vector<T>& v) { return add(v.data(), v.size() * sizeof(T)); }
+};
+
+cs_status evaluate_impl(cs_ctx* ctx, Network* net, int level, const int32_t* ei, const int32_t* ej,
+                        int64_t n, const cs_result* out, cudaStream_t s, bool record) {
+    if (n <= 0) return CS_OK;
+    const DevNet& dn = net->dev;
+    const int nx = 2 * dn.nb + 2 * dn.ng;
+    const int64_t chunk = ctx->opt.chunk > 0 ? ctx->opt.chunk : 16384;
+    const int64_t cn = std::min<int64_t>(n, chunk);
+    // grids: persistent kernels sized from occupancy, capped per SM
+    const int cap_opf = ctx->opt.ctas_per_sm > 0 ? ctx->opt.ctas_per_sm : 3;
+    const int cap_dyn = ctx->opt.ctas_per_sm > 0 ? ctx->opt.ctas_per_sm : 2;
+    const int g_opf = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->sms * cap_opf, cn));
+    const int g_dyn = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->sms * cap_dyn, cn));
+    const size_t per_opf = opf_scratch_doubles(dn);
+    const size_t per_dyn = dyn_scratch_doubles(dn);
+    const size_t need = std::max(per_opf * g_opf, per_dyn * g_dyn) * sizeof(double);
+    CS_CUDA(ctx->scratch.ensure(need));
+    CS_CUDA(ctx->isl.ensure(sizeof(int) * cn));
+    CS_CUDA(ctx->opfx.ensure(sizeof(double) * nx * cn));
+    CS_CUDA(ctx->opfst.ensure(sizeof(int) * cn));
+    CS_CUDA(ctx->counters.ensure(sizeof(int) * 4));
+    CS_CUDA(ctx->err_word.ensure(sizeof(int)));
+    int* counters = (int*)ctx->counters.p;
+    for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+        const int64_t m = std::min(chunk, n - c0);
+        EvalArgs a{};
+        a.ei = ei + c0;
+        a.ej = ej + c0;
+        a.n = (int)m;
+        a.level = level;
+        a.out = *out;
+        a.out.klass = out->klass + c0;
+        a.out.severe = out->severe + c0;
+        a.out.n_islands = out->n_islands + c0;
+        a.out.opf_iters = out->opf_iters + c0;
+        a.out.cost = out->cost + c0;
+        a.out.max_re = out->max_re + c0;
+        a.out.min_zeta = out->min_zeta + c0;
+        a.out.Vm = out->Vm ? out->Vm + c0 * dn.nb : nullptr;
+        a.out.Va = out->Va ? out->Va + c0 * dn.nb : nullptr;
+        a.sev_n1 = record ? (uint8_t*)net->sev_n1[level]->p : nullptr;
+        a.sev_pairs = record ? (uint8_t*)net->sev_pairs[level]->p : nullptr;
+        a.err = (int*)ctx->err_word.p;
+        OpfOut o{(double*)ctx->opfx.p, (int*)ctx->opfst.p};
+        CS_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * 4, s));
+        CS_CUDA(launch_islands(dn, a, (int*)ctx->isl.p, s));
+        CS_CUDA(launch_opf(dn, a, (const int*)ctx->isl.p, o, ctx->opt.opf_tol, ctx->opt.opf_max_it,
+                           (double*)ctx->scratch.p, per_opf, std::min<int64_t>(g_opf, m), counters, s));
+        CS_CUDA(launch_dyn(dn, a, o, ctx->opt.damping_min, (double*)ctx->scratch.p, per_dyn,
+                           std::min<int64_t>(g_dyn, m), counters + 1, s));
+        ctx->launches += 3 + (a.sev_n1 ? 1 : 0);
+    }
+    return CS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cs_default_options(cs_options* o) {
+    if (!o) return;
+    o->device = 0;
+    o->damping_min = 0.05;
+    o->opf_tol = 1e-8;
+    o->opf_max_it = 50;
+    o->require_secure_base = 0;
+    o->ctas_per_sm = 0;
+    o->chunk = 0;
+}
+
+cs_status cs_create(const cs_options* opt, cs_ctx** out) {
+    if (!out) return CS_E_ARG;
+    *out = nullptr;
+    std::unique_ptr<cs_ctx> c(new cs_ctx());
+    if (opt) c->opt = *opt; else cs_default_options(&c->opt);
+    if (c->opt.opf_max_it < 0 || c->opt.opf_max_it > 10000 || !(c->opt.opf_tol > 0.0)) return CS_E_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return CS_E_CUDA;
+    if (c->opt.device < 0 || c->opt.device >= ndev) return CS_E_ARG;
+    c->device = c->opt.device;
+    if (cudaSetDevice(c->device) != cudaSuccess) return CS_E_CUDA;
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) return CS_E_CUDA;
+    if (cudaStreamCreateWithFlags(&c->req_stream, cudaStreamNonBlocking) != cudaSuccess) return CS_E_CUDA;
+    *out = c.release();
+    return CS_OK;
+}
+
+cs_status cs_destroy(cs_ctx* ctx) {
+    if (!ctx) return CS_E_ARG;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    ctx->reqs.clear();
+    ctx->nets.clear();
+    if (ctx->req_stream) cudaStreamDestroy(ctx->req_stream);
+    delete ctx;
+    return CS_OK;
+}
+
+const char* cs_last_error(cs_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int64_t cs_last_launch_count(cs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+cs_status cs_load_network(cs_ctx* ctx, const cs_network_desc* d, int32_t* net_id) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (!d || !net_id) return fail(ctx, CS_E_ARG, "NULL argument");
+    const int nb = d->n_bus, nbr = d->n_branch, ng = d->n_gen, nlev = d->n_levels;
+    if (nb <= 0 || nbr < 0 || ng <= 0 || nlev <= 0 || d->ref_bus < 0 || d->ref_bus >= nb || !(d->base_mva > 0) ||
+        !(d->f_hz > 0))
+        return fail(ctx, CS_E_ARG, "invalid sizes");
+    const void* req[] = {d->Vmin, d->Vmax, d->Gs, d->Bs, d->Pd, d->Qd, d->f, d->t, d->r, d->x, d->b, d->rate,
+                         d->tap, d->gbus, d->Pmin, d->Pmax, d->Qmin, d->Qmax, d->c2, d->c1, d->c0, d->H, d->D,
+                         d->xd, d->xq, d->xdp, d->Td0p, d->Tq0p, d->KA, d->TA};
+    for (const void* p : req)
+        if (!p) return fail(ctx, CS_E_ARG, "NULL array in network descriptor");
+    if ((long long)nbr + ng > 32767) return fail(ctx, CS_E_ARG, "too many outage elements");
+    for (int k = 0; k < nbr; ++k) {
+        if (d->f[k] < 0 || d->f[k] >= nb || d->t[k] < 0 || d->t[k] >= nb || d->f[k] == d->t[k])
+            return fail(ctx, CS_E_ARG, "branch end out of range or self loop");
+        if (!(d->rate[k] > 0) || !(d->tap[k] > 0) || !(std::fabs(d->r[k]) + std::fabs(d->x[k]) > 0))
+            return fail(ctx, CS_E_ARG, "branch rating, tap or impedance invalid");
+    }
+    for (int k = 0; k < ng; ++k) {
+        if (d->gbus[k] < 0 || d->gbus[k] >= nb) return fail(ctx, CS_E_ARG, "generator bus out of range");
+        if (!(d->Pmax[k] > 0) || !(d->xdp[k] > 0) || !(d->H[k] > 0) || !(d->Td0p[k] > 0) || !(d->Tq0p[k] > 0) ||
+            !(d->TA[k] > 0) || !(d->KA[k] > 0))
+            return fail(ctx, CS_E_ARG, "generator data invalid");
+    }
+    CS_CUDA(cudaSetDevice(ctx->device));
+    std::unique_ptr<Network> net(new Network());
+    std::vector<int> f(d->f, d->f + nbr), t(d->t, d->t + nbr);
+    std::string msg = symbolic_analysis(nb, f, t, net->sym);
+    if (!msg.empty()) return fail(ctx, CS_E_ARG, msg);
+    const Symbolic& S = net->sym;
+    const double B = d->base_mva;
+    // per-unit conversion and branch two-port admittances
+    std::vector<cplx> yff(nbr), yft(nbr), ytf(nbr), ytt(nbr);
+    std::vector<double> smax2(nbr);
+    for (int k = 0; k < nbr; ++k) {
+        const double r = d->r[k], x = d->x[k], den = r * r + x * x;
+        const cplx ys = cm(r / den, -x / den);
+        const cplx yt = ys + cm(0.0, 0.5 * d->b[k]);
+        const double tap = d->tap[k];
+        ytt[k] = yt;
+        yff[k] = (1.0 / (tap * tap)) * yt;
+        yft[k] = (-1.0 / tap) * ys;
+        ytf[k] = (-1.0 / tap) * ys;
+        smax2[k] = (d->rate[k] / B) * (d->rate[k] / B);
+    }
+    std::vector<double> gsh(nb), bsh(nb), Pd((size_t)nlev * nb), Qd((size_t)nlev * nb);
+    for (int i = 0; i < nb; ++i) {
+        gsh[i] = d->Gs[i] / B;
+        bsh[i] = d->Bs[i] / B;
+    }
+    for (size_t q = 0; q < (size_t)nlev * nb; ++q) {
+        Pd[q] = d->Pd[q] / B;
+        Qd[q] = d->Qd[q] / B;
+    }
+    std::vector<double> pmin(ng), pmax(ng), qmin(ng), qmax(ng), xd(ng), xq(ng), xp(ng), H2(ng), Dm(ng);
+    for (int k = 0; k < ng; ++k) {
+        pmin[k] = d->Pmin[k] / B;
+        pmax[k] = d->Pmax[k] / B;
+        qmin[k] = d->Qmin[k] / B;
+        qmax[k] = d->Qmax[k] / B;
+        const double zb = B / d->Pmax[k];       // machine base (MVA = Pmax) -> system base
+        xd[k] = d->xd[k] * zb;
+        xq[k] = d->xq[k] * zb;
+        xp[k] = d->xdp[k] * zb;
+        H2[k] = 2.0 * d->H[k] / zb;
+        Dm[k] = d->D[k] / zb;
+    }
+    // incidence
+    std::vector<int> bus_br_ptr(nb + 1, 0), bus_br(2 * nbr), bus_gen_ptr(nb + 1, 0), bus_gen(ng);
+    for (int k = 0; k < nbr; ++k) { bus_br_ptr[f[k] + 1]++; bus_br_ptr[t[k] + 1]++; }
+    for (int i = 0; i < nb; ++i) bus_br_ptr[i + 1] += bus_br_ptr[i];
+    {
+        std::vector<int> fill(bus_br_ptr.begin(), bus_br_ptr.end() - 1);
+        for (int k = 0; k < nbr; ++k) {
+            bus_br[fill[f[k]]++] = 2 * k;
+            bus_br[fill[t[k]]++] = 2 * k + 1;
+        }
+    }
+    for (int k = 0; k < ng; ++k) bus_gen_ptr[d->gbus[k] + 1]++;
+    for (int i = 0; i < nb; ++i) bus_gen_ptr[i + 1] += bus_gen_ptr[i];
+    {
+        std::vector<int> fill(bus_gen_ptr.begin(), bus_gen_ptr.end() - 1);
+        for (int k = 0; k < ng; ++k) bus_gen[fill[d->gbus[k]]++] = k;
+    }
+    auto vec = [](const double* p, int cnt) { return std::vector<double>(p, p + cnt); };
+    Packer P;
+    size_t o_f = P.add(f), o_t = P.add(t), o_yff = P.add(yff), o_yft = P.add(yft), o_ytf = P.add(ytf),
+           o_ytt = P.add(ytt), o_smax2 = P.add(smax2);
+    size_t o_vmin = P.add(vec(d->Vmin, nb)), o_vmax = P.add(vec(d->Vmax, nb)), o_gsh = P.add(gsh), o_bsh = P.add(bsh),
+           o_Pd = P.add(Pd), o_Qd = P.add(Qd);
+    std::vector<int> gbus(d->gbus, d->gbus + ng);
+    size_t o_gbus = P.add(gbus), o_pmin = P.add(pmin), o_pmax = P.add(pmax), o_qmin = P.add(qmin),
+           o_qmax = P.add(qmax), o_c2 = P.add(vec(d->c2, ng)), o_c1 = P.add(vec(d->c1, ng)), o_c0 = P.add(vec(d->c0, ng));
+    size_t o_xd = P.add(xd), o_xq = P.add(xq), o_xp = P.add(xp), o_Td0 = P.add(vec(d->Td0p, ng)),
+           o_Tq0 = P.add(vec(d->Tq0p, ng)), o_KA = P.add(vec(d->KA, ng)), o_TA = P.add(vec(d->TA, ng)),
+           o_H2 = P.add(H2), o_Dm = P.add(Dm);
+    size_t o_bbp = P.add(bus_br_ptr), o_bb = P.add(bus_br), o_bgp = P.add(bus_gen_ptr), o_bg = P.add(bus_gen);
+    size_t o_perm = P.add(S.perm), o_iperm = P.add(S.iperm), o_Lcp = P.add(S.Lcolptr), o_Lr = P.add(S.Lrow),
+           o_Lc = P.add(S.Lcol), o_Lrp = P.add(S.Lrowptr), o_Lrc = P.add(S.Lrowcol), o_Lrb = P.add(S.Lrowblk),
+           o_lp = P.add(S.lev_ptr), o_lc = P.add(S.lev_col), o_tp = P.add(S.tgt_ptr), o_tg = P.add(S.tgt),
+           o_up = P.add(S.upd_ptr), o_ua = P.add(S.upd_a), o_ub = P.add(S.upd_b), o_bbrp = P.add(S.blk_br_ptr),
+           o_bbr = P.add(S.blk_br);
+    CS_CUDA(net->blob.ensure(P.host.size()));
+    CS_CUDA(cudaMemcpy(net->blob.p, P.host.data(), P.host.size(), cudaMemcpyHostToDevice));
+    char* base = (char*)net->blob.p;
+    DevNet& dn = net->dev;
+    dn.nb = nb; dn.nbr = nbr; dn.ng = ng; dn.nlev = nlev; dn.ref = d->ref_bus;
+    dn.base = B; dn.ws = 2.0 * M_PI * d->f_hz; dn.nE = nbr + ng;
+#define P_(T, o) ((const T*)(base + (o)))
+    dn.f = P_(int, o_f); dn.t = P_(int, o_t);
+    dn.yff = P_(cplx, o_yff); dn.yft = P_(cplx, o_yft); dn.ytf = P_(cplx, o_ytf); dn.ytt = P_(cplx, o_ytt);
+    dn.smax2 = P_(double, o_smax2);
+    dn.vmin = P_(double, o_vmin); dn.vmax = P_(double, o_vmax); dn.gsh = P_(double, o_gsh); dn.bsh = P_(double, o_bsh);
+    dn.Pd = P_(double, o_Pd); dn.Qd = P_(double, o_Qd);
+    dn.gbus = P_(int, o_gbus); dn.pmin = P_(double, o_pmin); dn.pmax = P_(double, o_pmax);
+    dn.qmin = P_(double, o_qmin); dn.qmax = P_(double, o_qmax);
+    dn.c2 = P_(double, o_c2); dn.c1 = P_(double, o_c1); dn.c0 = P_(double, o_c0);
+    dn.xd = P_(double, o_xd); dn.xq = P_(double, o_xq); dn.xp = P_(double, o_xp); dn.Td0 = P_(double, o_Td0);
+    dn.Tq0 = P_(double, o_Tq0); dn.KA = P_(double, o_KA); dn.TA = P_(double, o_TA); dn.H2 = P_(double, o_H2);
+    dn.Dm = P_(double, o_Dm);
+    dn.bus_br_ptr = P_(int, o_bbp); dn.bus_br = P_(int, o_bb); dn.bus_gen_ptr = P_(int, o_bgp); dn.bus_gen = P_(int, o_bg);
+    dn.nL = (int)S.Lrow.size();
+    dn.perm = P_(int, o_perm); dn.iperm = P_(int, o_iperm); dn.Lcolptr = P_(int, o_Lcp); dn.Lrow = P_(int, o_Lr);
+    dn.Lcol = P_(int, o_Lc); dn.Lrowptr = P_(int, o_Lrp); dn.Lrowcol = P_(int, o_Lrc); dn.Lrowblk = P_(int, o_Lrb);
+    dn.nlevels = S.nlevels; dn.lev_ptr = P_(int, o_lp); dn.lev_col = P_(int, o_lc); dn.tgt_ptr = P_(int, o_tp);
+    dn.tgt = P_(int, o_tg); dn.upd_ptr = P_(int, o_up); dn.upd_a = P_(int, o_ua); dn.upd_b = P_(int, o_ub);
+    dn.blk_br_ptr = P_(int, o_bbrp); dn.blk_br = P_(int, o_bbr);
+#undef P_
+    // severity tables, one per level, 255 = not evaluated
+    const int64_t nE = nbr + ng;
+    const int64_t npairs = nE * (nE - 1) / 2;
+    net->nlev = nlev;
+    for (int l = 0; l < nlev; ++l) {
+        net->sev_n1.emplace_back(new DevBuf());
+        net->sev_pairs.emplace_back(new DevBuf());
+        CS_CUDA(net->sev_n1[l]->ensure(std::max<int64_t>(nE, 1)));
+        CS_CUDA(net->sev_pairs[l]->ensure(std::max<int64_t>(npairs, 1)));
+        CS_CUDA(cudaMemset(net->sev_n1[l]->p, 0xff, std::max<int64_t>(nE, 1)));
+        CS_CUDA(cudaMemset(net->sev_pairs[l]->p, 0xff, std::max<int64_t>(npairs, 1)));
+    }
+    // base case of every level (Section II-A step 1)
+    {
+        DevBuf din, dout;
+        CS_CUDA(din.ensure(2 * sizeof(int)));
+        const int m1[2] = {-1, -1};
+        CS_CUDA(cudaMemcpy(din.p, m1, sizeof(m1), cudaMemcpyHostToDevice));
+        const size_t rec = 1 + 1 + 2 + 2 + 8 * 3;
+        CS_CUDA(dout.ensure(64 + rec));
+        char* ob = (char*)dout.p;
+        cs_result r{};
+        r.cost = (double*)(ob + 0);
+        r.max_re = (double*)(ob + 8);
+        r.min_zeta = (double*)(ob + 16);
+        r.n_islands = (int16_t*)(ob + 24);
+        r.opf_iters = (int16_t*)(ob + 26);
+        r.klass = (uint8_t*)(ob + 28);
+        r.severe = (uint8_t*)(ob + 29);
+        for (int l = 0; l < nlev; ++l) {
+            cs_status st = evaluate_impl(ctx, net.get(), l, (const int*)din.p, (const int*)din.p + 1, 1, &r, 0, false);
+            if (st != CS_OK) return st;
+            CS_CUDA(cudaDeviceSynchronize());
+            char hb[32];
+            CS_CUDA(cudaMemcpy(hb, ob, 30, cudaMemcpyDeviceToHost));
+            double c, mr, mz;
+            int16_t isl, it;
+            std::memcpy(&c, hb, 8);
+            std::memcpy(&mr, hb + 8, 8);
+            std::memcpy(&mz, hb + 16, 8);
+            std::memcpy(&isl, hb + 24, 2);
+            std::memcpy(&it, hb + 26, 2);
+            net->base_cost.push_back(c);
+            net->base_maxre.push_back(mr);
+            net->base_minz.push_back(mz);
+            net->base_isl.push_back(isl);
+            net->base_iters.push_back(it);
+            net->base_klass.push_back((uint8_t)hb[28]);
+            net->base_severe.push_back((uint8_t)hb[29]);
+            if (ctx->opt.require_secure_base && hb[29])
+                return fail(ctx, CS_E_BASE_INSECURE, "base case of level " + std::to_string(l) + " is not secure");
+        }
+    }
+    const int id = ctx->next_net++;
+    net->id = id;
+    ctx->nets[id] = std::move(net);
+    *net_id = id;
+    return CS_OK;
+}
+
+cs_status cs_unload_network(cs_ctx* ctx, int32_t net_id) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    auto it = ctx->nets.find(net_id);
+    if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    ctx->nets.erase(it);
+    return CS_OK;
+}
+
+cs_status cs_base_result(cs_ctx* ctx, int32_t net_id, int32_t level, const cs_result* out) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    auto it = ctx->nets.find(net_id);
+    if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
+    Network* n = it->second.get();
+    if (!out || level < 0 || level >= n->nlev) return fail(ctx, CS_E_ARG, "bad level or NULL out");
+    if (out->klass) out->klass[0] = n->base_klass[level];
+    if (out->severe) out->severe[0] = n->base_severe[level];
+    if (out->n_islands) out->n_islands[0] = n->base_isl[level];
+    if (out->opf_iters) out->opf_iters[0] = n->base_iters[level];
+    if (out->cost) out->cost[0] = n->base_cost[level];
+    if (out->max_re) out->max_re[0] = n->base_maxre[level];
+    if (out->min_zeta) out->min_zeta[0] = n->base_minz[level];
+    return CS_OK;
+}
+
+cs_status cs_evaluate_device(cs_ctx* ctx, int32_t net_id, int32_t level, const int32_t* ei, const int32_t* ej,
+                             int64_t n, const cs_result* out, void* stream) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    auto it = ctx->nets.find(net_id);
+    if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
+    Network* net = it->second.get();
+    if (level < 0 || level >= net->nlev) return fail(ctx, CS_E_ARG, "level out of range");
+    if (n < 0 || n > (int64_t)1 << 31) return fail(ctx, CS_E_ARG, "n out of range");
+    if (n == 0) return CS_OK;
+    if (!ei || !ej || !out || !out->klass || !out->severe || !out->n_islands || !out->opf_iters || !out->cost ||
+        !out->max_re || !out->min_zeta)
+        return fail(ctx, CS_E_ARG, "NULL buffer");
+    CS_CUDA(cudaSetDevice(ctx->device));
+    ctx->launches = 0;
+    return evaluate_impl(ctx, net, level, ei, ej, n, out, (cudaStream_t)stream, true);
+}
+
+cs_status cs_sync(cs_ctx* ctx, void* stream) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    CS_CUDA(cudaSetDevice(ctx->device));
+    CS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (ctx->err_word.p) {
+        int e = 0;
+        CS_CUDA(cudaMemcpy(&e, ctx->err_word.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) {
+            CS_CUDA(cudaMemset(ctx->err_word.p, 0, sizeof(int)));
+            if (e & ERR_BAD_ELEMENT) return fail(ctx, CS_E_ARG, "element id out of range (record marked 255)");
+            return fail(ctx, CS_E_NUMERIC, "device error word " + std::to_string(e));
+        }
+    }
+    return CS_OK;
+}
+
+// ------------------------------------------------------------ requests ----
+static size_t result_bytes(int64_t n, int nb, bool volt) {
+    size_t b = (size_t)n * (1 + 1 + 2 + 2 + 8 * 3);
+    if (volt) b += (size_t)n * nb * 16;
+    return b;
+}
+
+static void carve(char* base, int64_t n, int nb, cs_result* r) {
+    // doubles first for alignment
+    r->cost = (double*)base;
+    r->max_re = r->cost + n;
+    r->min_zeta = r->max_re + n;
+    r->n_islands = (int16_t*)(r->min_zeta + n);
+    r->opf_iters = r->n_islands + n;
+    r->klass = (uint8_t*)(r->opf_iters + n);
+    r->severe = r->klass + n;
+    r->Vm = nullptr;
+    r->Va = nullptr;
+    (void)nb;
+}
+
+cs_status cs_submit_contingencies(cs_ctx* ctx, int32_t net_id, int32_t level, const int32_t* ei, const int32_t* ej,
+                                  int64_t n, uint64_t* request_id) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (!request_id || (n > 0 && (!ei || !ej))) return fail(ctx, CS_E_ARG, "NULL argument");
+    auto it = ctx->nets.find(net_id);
+    if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
+    Network* net = it->second.get();
+    if (level < 0 || level >= net->nlev) return fail(ctx, CS_E_ARG, "level out of range");
+    if (n < 0 || n > (int64_t)1 << 31) return fail(ctx, CS_E_ARG, "n out of range");
+    const int nE = net->dev.nE;
+    for (int64_t q = 0; q < n; ++q) {
+        const int a = ei[q], b = ej[q];
+        if (a < -1 || a >= nE || b < -1 || b >= nE || (a < 0 && b >= 0))
+            return fail(ctx, CS_E_ARG, "element id out of range at record " + std::to_string(q));
+    }
+    CS_CUDA(cudaSetDevice(ctx->device));
+    std::unique_ptr<Request> r(new Request());
+    r->id = ctx->next_req++;
+    r->n = n;
+    r->nb = net->dev.nb;
+    const size_t ob = result_bytes(std::max<int64_t>(n, 1), net->dev.nb, false);
+    CS_CUDA(r->d_in.ensure(sizeof(int) * 2 * std::max<int64_t>(n, 1)));
+    CS_CUDA(r->d_out.ensure(ob));
+    CS_CUDA(cudaMallocHost(&r->h_out, ob));
+    r->h_out_bytes = ob;
+    CS_CUDA(cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming));
+    cudaStream_t s = ctx->req_stream;
+    int* din = (int*)r->d_in.p;
+    if (n > 0) {
+        CS_CUDA(cudaMemcpyAsync(din, ei, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+        CS_CUDA(cudaMemcpyAsync(din + n, ej, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+        cs_result dr{};
+        carve((char*)r->d_out.p, n, net->dev.nb, &dr);
+        ctx->launches = 0;
+        cs_status st = evaluate_impl(ctx, net, level, din, din + n, n, &dr, s, true);
+        if (st != CS_OK) return st;
+        CS_CUDA(cudaMemcpyAsync(r->h_out, r->d_out.p, result_bytes(n, net->dev.nb, false), cudaMemcpyDeviceToHost, s));
+    }
+    CS_CUDA(cudaEventRecord(r->done, s));
+    *request_id = r->id;
+    ctx->reqs[r->id] = std::move(r);
+    return CS_OK;
+}
+
+cs_status cs_poll(cs_ctx* ctx, uint64_t request_id, int32_t timeout_us, const cs_result* out) {
+    if (!ctx) return CS_E_ARG;
+    Request* r = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        auto it = ctx->reqs.find(request_id);
+        if (it == ctx->reqs.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown request");
+        r = it->second.get();
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaEventQuery(r->done);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return cuda_fail(ctx, q, "cudaEventQuery");
+        const auto us = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+        if (us >= timeout_us) return CS_PENDING;
+        std::this_thread::sleep_for(std::chrono::microseconds(std::min<long long>(50, timeout_us - us)));
+    }
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    const int64_t n = r->n;
+    if (n > 0) {
+        if (!out) return fail(ctx, CS_E_ARG, "NULL out");
+        cs_result h{};
+        carve((char*)r->h_out, n, r->nb, &h);
+        if (out->klass) std::memcpy(out->klass, h.klass, n);
+        if (out->severe) std::memcpy(out->severe, h.severe, n);
+        if (out->n_islands) std::memcpy(out->n_islands, h.n_islands, 2 * n);
+        if (out->opf_iters) std::memcpy(out->opf_iters, h.opf_iters, 2 * n);
+        if (out->cost) std::memcpy(out->cost, h.cost, 8 * n);
+        if (out->max_re) std::memcpy(out->max_re, h.max_re, 8 * n);
+        if (out->min_zeta) std::memcpy(out->min_zeta, h.min_zeta, 8 * n);
+    }
+    ctx->reqs.erase(request_id);
+    return CS_OK;
+}
+
+// ---------------------------------------------------------- Risk Index ----
+cs_status cs_risk_index(cs_ctx* ctx, int32_t net_id, int32_t level, const double* lambda, int32_t mode,
+                        double* R_out, int64_t* n_missing) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    auto it = ctx->nets.find(net_id);
+    if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
+    Network* net = it->second.get();
+    if (level < 0 || level >= net->nlev || !lambda || !R_out || (mode != CS_RISK_EQ3 && mode != CS_RISK_ORDERED))
+        return fail(ctx, CS_E_ARG, "bad level, mode or NULL");
+    const int nE = net->dev.nE;
+    for (int i = 0; i < nE; ++i)
+        if (!(lambda[i] >= std::ldexp(1.0, -30) && lambda[i] <= std::ldexp(1.0, 10)))
+            return fail(ctx, CS_E_ARG, "lambda outside [2^-30, 2^10]");
+    CS_CUDA(cudaSetDevice(ctx->device));
+    DevBuf dl, dr, dm;
+    CS_CUDA(dl.ensure(sizeof(double) * nE));
+    CS_CUDA(dr.ensure(sizeof(double) * nE));
+    CS_CUDA(dm.ensure(sizeof(int64_t)));
+    cudaStream_t s = ctx->req_stream;
+    CS_CUDA(cudaDeviceSynchronize());      // tables written by earlier evaluations on any stream
+    CS_CUDA(cudaMemcpyAsync(dl.p, lambda, sizeof(double) * nE, cudaMemcpyHostToDevice, s));
+    CS_CUDA(cudaMemsetAsync(dm.p, 0, sizeof(int64_t), s));
+    CS_CUDA(launch_risk(nE, (const uint8_t*)net->sev_n1[level]->p, (const uint8_t*)net->sev_pairs[level]->p,
+                        (const double*)dl.p, mode, (double*)dr.p, (int64_t*)dm.p, s));
+    CS_CUDA(cudaMemcpyAsync(R_out, dr.p, sizeof(double) * nE, cudaMemcpyDeviceToHost, s));
+    int64_t miss = 0;
+    CS_CUDA(cudaMemcpyAsync(&miss, dm.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CS_CUDA(cudaStreamSynchronize(s));
+    if (n_missing) *n_missing = miss;
+    return CS_OK;
+}
+
+cs_status cs_risk_reduce_device(int32_t n_elem, const uint8_t* S1, const uint8_t* S2, const double* lambda,
+                                int32_t mode, double* R, void* stream) {
+    if (n_elem < 0 || (n_elem > 0 && (!S1 || !S2 || !lambda || !R)) || (mode != CS_RISK_EQ3 && mode != CS_RISK_ORDERED))
+        return CS_E_ARG;
+    cudaError_t e = launch_risk(n_elem, S1, S2, lambda, mode, R, nullptr, (cudaStream_t)stream);
+    return e == cudaSuccess ? CS_OK : CS_E_CUDA;
+}
+
+cs_status cs_enumerate_pairs_device(int32_t n_elem, int64_t first, int64_t count, int32_t* ei, int32_t* ej,
+                                    void* stream) {
+    const int64_t total = (int64_t)n_elem * (n_elem - 1) / 2;
+    if (n_elem < 2 || first < 0 || count < 0 || first + count > total || (count > 0 && (!ei || !ej))) return CS_E_ARG;
+    cudaError_t e = launch_enumerate(n_elem, first, count, ei, ej, (cudaStream_t)stream);
+    return e == cudaSuccess ? CS_OK : CS_E_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,644 @@
+// Small-signal screen of converged OPF points, one scenario per CTA
+// (Section II-B-2: the system model is linearised at the OPF operating point
+// and a scenario is unstable when an eigenvalue has a non-negative real part;
+// the configuration adds a minimum damping ratio).
+//
+// Model (per in-service generator, machine data converted to the system base):
+// states delta, omega, e'q, e'd, Efd (index 5k + s); E' = (e'q - j e'd) e^{j delta}
+// behind j x' (x'd = x'q, Ra = 0); I = Y_red E' with Y_red the Kron reduction of
+// the network (loads as constant admittances at the OPF voltage, machines as
+// 1/(j x') to their internal nodes); i_d + j i_q = j I e^{-j delta};
+//   d delta/dt = ws (omega - 1)
+//   2H d omega/dt = Pm - (e'd i_d + e'q i_q) - D (omega - 1)
+//   T'd0 d e'q/dt = -e'q - (x_d - x') i_d + Efd
+//   T'q0 d e'd/dt = -e'd + (x_q - x') i_q
+//   T_A d Efd/dt = -Efd + K_A (V_ref - |E' - j x' I|)
+// The state matrix is written from hand-derived partial derivatives of these
+// equations (the CPU oracle differentiates them automatically instead).
+//
+// Steps inside one CTA:
+//  1. Y_bb = Ybus(outages masked) + loads + machine admittances, factorised as
+//     a complex symmetric LDL^T on the network's shared symbolic analysis
+//     (scalar complex blocks, same elimination-tree levels as the OPF kernel);
+//  2. one thread per in-service machine solves Y_bb x = e_{bus} to get the
+//     machine-bus entries of Y_bb^{-1}, hence Y_red;
+//  3. equilibrium from the OPF point; one thread per machine pair writes the
+//     5x5 block of A;
+//  4. balancing by powers of two, Householder Hessenberg reduction, Francis
+//     double-shift QR (eigenvalues only), with the same steps and thresholds
+//     as the textbook algorithm; A lives in the CTA's global scratch (the
+//     resident CTAs' matrices together fit in the 129 MB L2);
+//  5. drop the eigenvalue of smallest modulus (the common-rotation mode of the
+//     absolute rotor angles), take max Re and min damping ratio, classify.
+#include <cmath>
+
+#include "cs_internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr double kEps = 2.220446049250313e-16;
+
+struct DLay {
+    int Yu, Yl, Yd, Ydi;      // complex arrays (2 doubles per entry)
+    int Z;                    // [ng*ng] complex
+    int rhs;                  // [ng*nb] complex
+    int gen;                  // [ng * kGen]
+    int A;                    // [(5ng)^2]
+    int wr, wi;               // [5ng]
+    int total;
+};
+constexpr int kGen = 16;      // per-generator doubles: E(2) I(2) e^{jd}(2) Vt(2) |Vt| id iq eq ed ym(2)
+enum { G_E = 0, G_I = 2, G_ED = 4, G_VT = 6, G_VTM = 8, G_ID = 9, G_IQ = 10, G_EQ = 11, G_EDD = 12, G_YM = 13 };
+
+DLay make_dlayout(const DevNet& n) {
+    DLay L{};
+    int o = 0;
+    auto take = [&](long cnt) { int r = o; o += (int)cnt; return r; };
+    L.Yu = take(2L * n.nL); L.Yl = take(2L * n.nL); L.Yd = take(2L * n.nb); L.Ydi = take(2L * n.nb);
+    L.Z = take(2L * n.ng * n.ng);
+    L.rhs = take(2L * n.ng * n.nb);
+    L.gen = take((long)kGen * n.ng);
+    o = (o + 31) & ~31;
+    L.A = take(25L * n.ng * n.ng);
+    L.wr = take(5L * n.ng); L.wi = take(5L * n.ng);
+    L.total = (o + 31) & ~31;
+    return L;
+}
+
+__device__ __forceinline__ cplx ld(const double* p) { return cplx{p[0], p[1]}; }
+__device__ __forceinline__ void st(double* p, cplx v) { p[0] = v.re; p[1] = v.im; }
+
+struct DShared {
+    double red[2][kThreads];
+    int ired[kThreads];
+    double u[3];
+    double x[3];
+    int lo, hi, its, fail, scen, m, nn;
+    double hmax;
+    double f_bal;
+    int done;
+};
+
+// block reductions ---------------------------------------------------------
+__device__ double bsum(DShared& sh, double v) {
+    const int tid = threadIdx.x;
+    sh.red[0][tid] = v;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (tid < s) sh.red[0][tid] += sh.red[0][tid + s];
+        __syncthreads();
+    }
+    const double r = sh.red[0][0];
+    __syncthreads();
+    return r;
+}
+__device__ void bsum2(DShared& sh, double& a, double& b) {
+    const int tid = threadIdx.x;
+    sh.red[0][tid] = a;
+    sh.red[1][tid] = b;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (tid < s) {
+            sh.red[0][tid] += sh.red[0][tid + s];
+            sh.red[1][tid] += sh.red[1][tid + s];
+        }
+        __syncthreads();
+    }
+    a = sh.red[0][0];
+    b = sh.red[1][0];
+    __syncthreads();
+}
+__device__ int bmax_int(DShared& sh, int v) {
+    const int tid = threadIdx.x;
+    for (int off = 16; off; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if ((tid & 31) == 0) sh.ired[tid >> 5] = v;
+    __syncthreads();
+    int r = sh.ired[0];
+    for (int w = 1; w < kThreads / 32; ++w) r = max(r, sh.ired[w]);
+    __syncthreads();
+    return r;
+}
+__device__ double bmax(DShared& sh, double v) {
+    const int tid = threadIdx.x;
+    for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if ((tid & 31) == 0) sh.red[0][tid >> 5] = v;
+    __syncthreads();
+    double r = sh.red[0][0];
+    for (int w = 1; w < kThreads / 32; ++w) r = fmax(r, sh.red[0][w]);
+    __syncthreads();
+    return r;
+}
+
+// eigenvalues of [[p, q], [r, s]] (same formulas as the textbook closed form)
+__device__ void eig2(double p, double q, double r, double s, double* re, double* im) {
+    const double hm = 0.5 * (p - s);
+    const double disc = hm * hm + q * r;
+    const double mean = 0.5 * (p + s);
+    if (disc >= 0.0) {
+        const double root = sqrt(disc);
+        const double big = mean + (hm >= 0.0 ? root : -root);
+        const double det = p * s - q * r;
+        const double other = (big != 0.0) ? det / big : mean - (hm >= 0.0 ? root : -root);
+        re[0] = big; im[0] = 0.0;
+        re[1] = other; im[1] = 0.0;
+    } else {
+        const double root = sqrt(-disc);
+        re[0] = mean; im[0] = root;
+        re[1] = mean; im[1] = -root;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch, size_t per_cta,
+           DLay L, int* counter) {
+    __shared__ DShared sh;
+    extern __shared__ int gidx[];     // [ng] compact -> generator id
+    const int tid = threadIdx.x;
+    double* W = scratch + per_cta * blockIdx.x;
+    const int nb = net.nb, ng = net.ng, nbr = net.nbr;
+    const int nx = 2 * nb + 2 * ng;
+    const double* Pd = net.Pd + (size_t)a.level * nb;
+    const double* Qd = net.Qd + (size_t)a.level * nb;
+
+    for (;;) {
+        if (tid == 0) sh.scen = atomicAdd(counter, 1);
+        __syncthreads();
+        const int s = sh.scen;
+        if (s >= a.n) break;
+        if (o.status[s] != 1) {
+            __syncthreads();
+            continue;
+        }
+        const Outage out = decode_outage(nbr, ng, a.ei[s], a.ej[s]);
+        const double* xs = o.x + (size_t)s * nx;
+        if (tid == 0) {
+            int m = 0;
+            for (int k = 0; k < ng; ++k)
+                if (!gen_out(out, k)) gidx[m++] = k;
+            sh.m = m;
+            sh.nn = 5 * m;
+            sh.fail = 0;
+        }
+        __syncthreads();
+        const int m = sh.m, n = sh.nn;
+
+        // ---- 1. assemble Y_bb on the symbolic pattern ----
+        for (int tg = tid; tg < nb + net.nL; tg += kThreads) {
+            if (tg < nb) {
+                const int j = tg, i = net.perm[j];
+                const double Vm = xs[nb + i];
+                cplx y = cm(net.gsh[i], net.bsh[i]);
+                y = y + (1.0 / (Vm * Vm)) * cm(Pd[i], -Qd[i]);
+                for (int e = net.bus_br_ptr[i]; e < net.bus_br_ptr[i + 1]; ++e) {
+                    const int code = net.bus_br[e];
+                    const int b = code >> 1, side = code & 1;
+                    if (br_out(out, b)) continue;
+                    y = y + (side ? net.ytt[b] : net.yff[b]);
+                }
+                for (int e = net.bus_gen_ptr[i]; e < net.bus_gen_ptr[i + 1]; ++e) {
+                    const int k = net.bus_gen[e];
+                    if (gen_out(out, k)) continue;
+                    y = y + cm(0.0, -1.0 / net.xp[k]);
+                }
+                st(W + L.Yd + 2 * j, y);
+            } else {
+                const int q = tg - nb;
+                const int Rb = net.perm[net.Lrow[q]];
+                cplx y = cm(0.0, 0.0);
+                for (int e = net.blk_br_ptr[q]; e < net.blk_br_ptr[q + 1]; ++e) {
+                    const int b = net.blk_br[e];
+                    if (br_out(out, b)) continue;
+                    y = y + ((net.f[b] == Rb) ? net.yft[b] : net.ytf[b]);
+                }
+                st(W + L.Yu + 2 * q, y);
+            }
+        }
+        __syncthreads();
+        // ---- complex LDL^T, level by level ----
+        for (int lev = 0; lev < net.nlevels; ++lev) {
+            const int t0 = net.tgt_ptr[lev], t1 = net.tgt_ptr[lev + 1];
+            for (int w = tid; w < t1 - t0; w += kThreads) {
+                const int tg = net.tgt[t0 + w];
+                double* A = (tg < nb) ? (W + L.Yd + 2 * tg) : (W + L.Yu + 2 * (tg - nb));
+                cplx acc = ld(A);
+                for (int u = net.upd_ptr[tg]; u < net.upd_ptr[tg + 1]; ++u)
+                    acc = acc - ld(W + L.Yl + 2 * net.upd_a[u]) * ld(W + L.Yu + 2 * net.upd_b[u]);
+                st(A, acc);
+            }
+            __syncthreads();
+            for (int w = net.lev_ptr[lev] + tid; w < net.lev_ptr[lev + 1]; w += kThreads) {
+                const int j = net.lev_col[w];
+                const cplx d = ld(W + L.Yd + 2 * j);
+                if (!(abs2(d) > 0.0) || !isfinite(abs2(d))) sh.fail = 1;
+                st(W + L.Ydi + 2 * j, cdiv(cm(1.0, 0.0), d));
+            }
+            __syncthreads();
+            for (int w = tid; w < t1 - t0; w += kThreads) {
+                const int tg = net.tgt[t0 + w];
+                if (tg < nb) continue;
+                const int q = tg - nb;
+                st(W + L.Yl + 2 * q, ld(W + L.Yu + 2 * q) * ld(W + L.Ydi + 2 * net.Lcol[q]));
+            }
+            __syncthreads();
+        }
+        // ---- 2. machine-bus entries of Y_bb^{-1}: one sparse solve per machine ----
+        for (int kk = tid; kk < m; kk += kThreads) {
+            double* y = W + L.rhs + (size_t)2 * nb * kk;
+            for (int j = 0; j < nb; ++j) { y[2 * j] = 0.0; y[2 * j + 1] = 0.0; }
+            const int jb = net.iperm[net.gbus[gidx[kk]]];
+            y[2 * jb] = 1.0;
+            for (int j = 0; j < nb; ++j) {           // forward, elimination order
+                cplx acc = ld(y + 2 * j);
+                for (int e = net.Lrowptr[j]; e < net.Lrowptr[j + 1]; ++e)
+                    acc = acc - ld(W + L.Yl + 2 * net.Lrowblk[e]) * ld(y + 2 * net.Lrowcol[e]);
+                st(y + 2 * j, acc);
+            }
+            for (int j = 0; j < nb; ++j) st(y + 2 * j, ld(y + 2 * j) * ld(W + L.Ydi + 2 * j));
+            for (int j = nb - 1; j >= 0; --j) {       // backward
+                cplx acc = ld(y + 2 * j);
+                for (int e = net.Lcolptr[j]; e < net.Lcolptr[j + 1]; ++e)
+                    acc = acc - ld(W + L.Yl + 2 * e) * ld(y + 2 * net.Lrow[e]);
+                st(y + 2 * j, acc);
+            }
+        }
+        __syncthreads();
+        // Y_red[k][l] = ym_k delta_kl - ym_k ym_l (Ybb^-1)[b_k][b_l]
+        for (int w = tid; w < m * m; w += kThreads) {
+            const int k = w / m, l = w % m;
+            const cplx ymk = cm(0.0, -1.0 / net.xp[gidx[k]]), yml = cm(0.0, -1.0 / net.xp[gidx[l]]);
+            const int jl = net.iperm[net.gbus[gidx[l]]];
+            cplx z = ld(W + L.rhs + (size_t)2 * nb * k + 2 * jl);
+            cplx v = cm(0.0, 0.0) - ymk * yml * z;
+            if (k == l) v = v + ymk;
+            st(W + L.Z + 2 * (size_t)(k * m + l), v);
+        }
+        // ---- 3. equilibrium per machine ----
+        for (int kk = tid; kk < m; kk += kThreads) {
+            const int k = gidx[kk], i = net.gbus[k];
+            double sa, ca;
+            sincos(xs[i], &sa, &ca);
+            const cplx V = xs[nb + i] * cm(ca, sa);
+            const cplx S = cm(xs[2 * nb + k], xs[2 * nb + ng + k]);
+            const cplx I = conj(cdiv(S, V));
+            const cplx EQ = V + mulj(net.xq[k] * I);
+            const double delta = atan2(EQ.im, EQ.re);
+            double sd, cd;
+            sincos(delta, &sd, &cd);
+            const cplx ejd = cm(cd, sd);
+            const cplx rot = mulj(conj(ejd));            // j e^{-j delta}
+            const cplx Idq = I * rot, Vdq = V * rot;   // OPF current, used for the equilibrium only
+            const double xp = net.xp[k];
+            const double eq = Vdq.im + xp * Idq.re;
+            const double ed = Vdq.re - xp * Idq.im;
+            const cplx E = cm(eq, -ed) * ejd;
+            double* g = W + L.gen + kGen * kk;
+            st(g + G_E, E);
+            st(g + G_ED, ejd);
+            g[G_EQ] = eq;
+            g[G_EDD] = ed;
+        }
+        __syncthreads();
+        // network currents at the equilibrium state: I = Y_red E' (the OPF injection up
+        // to the OPF residual), and the dq currents and terminal voltage from them
+        for (int kk = tid; kk < m; kk += kThreads) {
+            double* g = W + L.gen + kGen * kk;
+            cplx I = cm(0.0, 0.0);
+            for (int ll = 0; ll < m; ++ll)
+                I = I + ld(W + L.Z + 2 * (size_t)(kk * m + ll)) * ld(W + L.gen + kGen * ll + G_E);
+            const cplx rot = mulj(conj(ld(g + G_ED)));
+            const cplx Idq = I * rot;
+            const cplx Vt = ld(g + G_E) - mulj(net.xp[gidx[kk]] * I);
+            st(g + G_I, I);
+            st(g + G_VT, Vt);
+            g[G_VTM] = sqrt(abs2(Vt));
+            g[G_ID] = Idq.re;
+            g[G_IQ] = Idq.im;
+        }
+        __syncthreads();
+        // ---- state matrix: one thread per 5x5 block (k, l) ----
+        double* A = W + L.A;
+        for (int w = tid; w < m * m; w += kThreads) {
+            const int kk = w / m, ll = w % m;
+            const int k = gidx[kk];
+            const double* gk = W + L.gen + kGen * kk;
+            const double* gl = W + L.gen + kGen * ll;
+            const cplx Y = ld(W + L.Z + 2 * (size_t)(kk * m + ll));
+            const cplx El = ld(gl + G_E), ejl = ld(gl + G_ED);
+            const cplx dE[3] = {mulj(El), ejl, cm(0.0, -1.0) * ejl};   // d E'_l / d(delta, e'q, e'd)
+            const cplx rotk = mulj(conj(ld(gk + G_ED)));
+            const cplx Ik = ld(gk + G_I), Vt = ld(gk + G_VT);
+            const double idk = gk[G_ID], iqk = gk[G_IQ], eqk = gk[G_EQ], edk = gk[G_EDD], Vtm = gk[G_VTM];
+            const double xp = net.xp[k];
+            double blk[5][5];
+            for (int r = 0; r < 5; ++r)
+                for (int c = 0; c < 5; ++c) blk[r][c] = 0.0;
+            const int colmap[3] = {0, 2, 3};
+            for (int th = 0; th < 3; ++th) {
+                const cplx dI = Y * dE[th];
+                cplx didq = rotk * dI;
+                if (kk == ll && th == 0) didq = didq + cm(0.0, -1.0) * cplx{idk, iqk};
+                double dPe = edk * didq.re + eqk * didq.im;
+                if (kk == ll && th == 1) dPe += iqk;
+                if (kk == ll && th == 2) dPe += idk;
+                cplx dVt = cm(0.0, -xp) * dI;
+                if (kk == ll) dVt = dVt + dE[th];
+                const double dVm = (Vt.re * dVt.re + Vt.im * dVt.im) / Vtm;
+                const int c = colmap[th];
+                blk[1][c] = -dPe / net.H2[k];
+                blk[2][c] = -(net.xd[k] - xp) * didq.re / net.Td0[k];
+                blk[3][c] = (net.xq[k] - xp) * didq.im / net.Tq0[k];
+                blk[4][c] = -net.KA[k] * dVm / net.TA[k];
+            }
+            if (kk == ll) {
+                blk[0][1] = net.ws;
+                blk[1][1] = -net.Dm[k] / net.H2[k];
+                blk[2][2] += -1.0 / net.Td0[k];
+                blk[2][4] = 1.0 / net.Td0[k];
+                blk[3][3] += -1.0 / net.Tq0[k];
+                blk[4][4] = -1.0 / net.TA[k];
+            }
+            for (int r = 0; r < 5; ++r)
+                for (int c = 0; c < 5; ++c) A[(size_t)(5 * kk + r) * n + 5 * ll + c] = blk[r][c];
+        }
+        __syncthreads();
+        // ---- 4a. balancing by powers of two ----
+        if (tid == 0) sh.done = 0;
+        __syncthreads();
+        for (int sweep = 0; !sh.done && sweep < 100; ++sweep) {   // converges in a few sweeps; capped
+            __syncthreads();
+            if (tid == 0) sh.done = 1;
+            for (int i = 0; i < n; ++i) {
+                double c = 0.0, r = 0.0;
+                for (int j = tid; j < n; j += kThreads) {
+                    if (j == i) continue;
+                    c += fabs(A[(size_t)j * n + i]);
+                    r += fabs(A[(size_t)i * n + j]);
+                }
+                bsum2(sh, c, r);
+                if (c == 0.0 || r == 0.0 || !isfinite(c) || !isfinite(r)) continue;
+                double g = r / 2.0, f = 1.0;
+                const double ssum = c + r;
+                while (c < g) { f *= 2.0; c *= 4.0; }
+                g = r * 2.0;
+                while (c > g) { f /= 2.0; c /= 4.0; }
+                if ((c + r) / f < 0.95 * ssum) {
+                    const double ginv = 1.0 / f;
+                    for (int j = tid; j < n; j += kThreads) A[(size_t)i * n + j] *= ginv;
+                    __syncthreads();
+                    for (int j = tid; j < n; j += kThreads) A[(size_t)j * n + i] *= f;
+                    if (tid == 0) sh.done = 0;
+                    __syncthreads();
+                }
+            }
+            __syncthreads();
+        }
+        // ---- 4b. Householder reduction to Hessenberg form ----
+        double* v = W + L.wr;      // reflector (length <= n) reuses the eigenvalue arrays
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int k = 0; k + 2 < n; ++k) {
+            double t = 0.0;
+            for (int i = k + 2 + tid; i < n; i += kThreads) {
+                const double q = A[(size_t)i * n + k];
+                t += q * q;
+            }
+            const double tail = bsum(sh, t);
+            if (tail == 0.0) continue;
+            const double x0 = A[(size_t)(k + 1) * n + k];
+            const double nrm2 = x0 * x0 + tail;
+            const double alpha = (x0 >= 0.0) ? -sqrt(nrm2) : sqrt(nrm2);
+            const int mm = n - k - 1;
+            const double v0 = x0 - alpha;
+            const double beta = 2.0 / (v0 * v0 + tail);
+            for (int i = tid; i < mm; i += kThreads) v[i] = (i == 0) ? v0 : A[(size_t)(k + 1 + i) * n + k];
+            __syncthreads();
+            for (int j = k + tid; j < n; j += kThreads) {          // left: columns k..n-1
+                double sacc = 0.0;
+                for (int i = 0; i < mm; ++i) sacc += v[i] * A[(size_t)(k + 1 + i) * n + j];
+                sacc *= beta;
+                for (int i = 0; i < mm; ++i) A[(size_t)(k + 1 + i) * n + j] -= sacc * v[i];
+            }
+            __syncthreads();
+            for (int i = warp; i < n; i += kThreads / 32) {        // right: all rows
+                double* row = A + (size_t)i * n + k + 1;
+                double sacc = 0.0;
+                for (int j = lane; j < mm; j += 32) sacc += row[j] * v[j];
+                for (int off = 16; off; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+                sacc *= beta;
+                for (int j = lane; j < mm; j += 32) row[j] -= sacc * v[j];
+            }
+            __syncthreads();
+            for (int i = k + 1 + tid; i < n; i += kThreads) A[(size_t)i * n + k] = (i == k + 1) ? alpha : 0.0;
+            __syncthreads();
+        }
+        // ---- 4c. Francis double-shift QR, eigenvalues only ----
+        double* wr = W + L.wr;
+        double* wi = W + L.wi;
+        {
+            double hm = 0.0;
+            for (int w = tid; w < n * n; w += kThreads) {
+                const int i = w / n, j = w % n;
+                if (j >= i - 1) hm = fmax(hm, fabs(A[w]));
+            }
+            hm = bmax(sh, hm);
+            if (tid == 0) {
+                sh.hmax = hm;
+                sh.hi = n - 1;
+                sh.its = 0;
+            }
+            __syncthreads();
+        }
+        while (sh.hi >= 0) {
+            const int hi = sh.hi;
+            // locate the top of the unreduced block ending at hi: largest l <= hi with a negligible A[l][l-1]
+            int cand = 0;
+            for (int l = 1 + tid; l <= hi; l += kThreads) {
+                double sd = fabs(A[(size_t)(l - 1) * n + l - 1]) + fabs(A[(size_t)l * n + l]);
+                if (sd == 0.0) sd = sh.hmax;
+                if (fabs(A[(size_t)l * n + l - 1]) <= kEps * sd) cand = max(cand, l);
+            }
+            const int lo = bmax_int(sh, cand);
+            if (tid == 0 && lo > 0) A[(size_t)lo * n + lo - 1] = 0.0;
+            if (lo == hi) {
+                if (tid == 0) {
+                    wr[hi] = A[(size_t)hi * n + hi];
+                    wi[hi] = 0.0;
+                    sh.hi = hi - 1;
+                    sh.its = 0;
+                }
+                __syncthreads();
+                continue;
+            }
+            if (lo == hi - 1) {
+                if (tid == 0) {
+                    double re[2], im[2];
+                    eig2(A[(size_t)(hi - 1) * n + hi - 1], A[(size_t)(hi - 1) * n + hi], A[(size_t)hi * n + hi - 1],
+                         A[(size_t)hi * n + hi], re, im);
+                    wr[hi - 1] = re[0]; wi[hi - 1] = im[0];
+                    wr[hi] = re[1]; wi[hi] = im[1];
+                    sh.hi = hi - 2;
+                    sh.its = 0;
+                }
+                __syncthreads();
+                continue;
+            }
+            if (sh.its >= 30 * n) {
+                if (tid == 0) sh.fail = 2;
+                __syncthreads();
+                break;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                const int its = ++sh.its;
+                double sft, tft;
+                const double a11 = A[(size_t)(hi - 1) * n + hi - 1], a12 = A[(size_t)(hi - 1) * n + hi];
+                const double a21 = A[(size_t)hi * n + hi - 1], a22 = A[(size_t)hi * n + hi];
+                if (its == 10 || its == 20) {
+                    const double ww = fabs(a21) + fabs(A[(size_t)(hi - 1) * n + hi - 2]);
+                    sft = 1.5 * ww;
+                    tft = ww * ww;
+                } else {
+                    sft = a11 + a22;
+                    tft = a11 * a22 - a12 * a21;
+                }
+                const double h00 = A[(size_t)lo * n + lo], h01 = A[(size_t)lo * n + lo + 1];
+                const double h10 = A[(size_t)(lo + 1) * n + lo], h11 = A[(size_t)(lo + 1) * n + lo + 1];
+                const double h21 = A[(size_t)(lo + 2) * n + lo + 1];
+                sh.x[0] = h00 * h00 + h01 * h10 - sft * h00 + tft;
+                sh.x[1] = h10 * (h00 + h11 - sft);
+                sh.x[2] = h10 * h21;
+            }
+            __syncthreads();
+            double x0 = sh.x[0], x1 = sh.x[1], x2 = sh.x[2];
+            for (int k = lo; k <= hi - 1; ++k) {
+                const int len = (k + 2 <= hi) ? 3 : 2;
+                const double t2 = x1 * x1 + (len == 3 ? x2 * x2 : 0.0);
+                if (t2 != 0.0) {
+                    const double nrm = sqrt(x0 * x0 + t2);
+                    const double al = (x0 >= 0.0) ? -nrm : nrm;
+                    const double u0 = x0 - al, u1 = x1, u2 = (len == 3) ? x2 : 0.0;
+                    const double bt = 2.0 / (u0 * u0 + t2);
+                    const int c0 = (k > lo) ? k - 1 : lo;
+                    for (int j = c0 + tid; j <= hi; j += kThreads) {   // rows k..k+len-1
+                        double* p0 = A + (size_t)k * n + j;
+                        double d = u0 * p0[0] + u1 * p0[n];
+                        if (len == 3) d += u2 * p0[2 * n];
+                        d *= bt;
+                        p0[0] -= d * u0;
+                        p0[n] -= d * u1;
+                        if (len == 3) p0[2 * n] -= d * u2;
+                    }
+                    __syncthreads();
+                    const int r1 = (k + 3 < hi) ? k + 3 : hi;
+                    for (int i = lo + tid; i <= r1; i += kThreads) {   // columns k..k+len-1
+                        double* p0 = A + (size_t)i * n + k;
+                        double d = p0[0] * u0 + p0[1] * u1;
+                        if (len == 3) d += p0[2] * u2;
+                        d *= bt;
+                        p0[0] -= d * u0;
+                        p0[1] -= d * u1;
+                        if (len == 3) p0[2] -= d * u2;
+                    }
+                    __syncthreads();
+                }
+                if (k + 1 <= hi - 1) {
+                    x0 = A[(size_t)(k + 1) * n + k];
+                    x1 = A[(size_t)(k + 2) * n + k];
+                    x2 = (k + 3 <= hi) ? A[(size_t)(k + 3) * n + k] : 0.0;
+                }
+            }
+            for (int i = lo + 2 + tid; i <= hi; i += kThreads) {
+                A[(size_t)i * n + i - 2] = 0.0;
+                if (i >= lo + 3) A[(size_t)i * n + i - 3] = 0.0;
+            }
+            __syncthreads();
+        }
+        // ---- 5. statistics and class ----
+        {
+            // index of the smallest modulus (ties: smallest index)
+            double best = INFINITY;
+            int bi = 0x7fffffff;
+            if (!sh.fail) {
+                for (int i = tid; i < n; i += kThreads) {
+                    const double mg = wr[i] * wr[i] + wi[i] * wi[i];
+                    if (mg < best || (mg == best && i < bi)) { best = mg; bi = i; }
+                }
+            }
+            sh.red[0][tid] = best;
+            sh.ired[tid] = bi;
+            __syncthreads();
+            for (int st2 = kThreads / 2; st2 > 0; st2 >>= 1) {
+                if (tid < st2) {
+                    const double ob = sh.red[0][tid + st2];
+                    const int oi = sh.ired[tid + st2];
+                    if (ob < sh.red[0][tid] || (ob == sh.red[0][tid] && oi < sh.ired[tid])) {
+                        sh.red[0][tid] = ob;
+                        sh.ired[tid] = oi;
+                    }
+                }
+                __syncthreads();
+            }
+            const int drop = sh.ired[0];
+            __syncthreads();
+            double mr = -INFINITY, mz = INFINITY;
+            for (int i = tid; i < n; i += kThreads) {
+                if (i == drop) continue;
+                mr = fmax(mr, wr[i]);
+                const double mg = sqrt(wr[i] * wr[i] + wi[i] * wi[i]);
+                mz = fmin(mz, mg > 0.0 ? -wr[i] / mg : 1.0);
+            }
+            const double maxre = bmax(sh, mr);
+            const double minz = -bmax(sh, -mz);
+            if (tid == 0) {
+                uint8_t k;
+                if (sh.fail) k = CS_EIG_FAIL;
+                else if (maxre >= 0.0) k = CS_SS_UNSTABLE;
+                else if (minz < damping_min) k = CS_SS_POORLY_DAMPED;
+                else k = CS_SECURE;
+                a.out.klass[s] = k;
+                a.out.severe[s] = (k != CS_SECURE);
+                const double nan = __longlong_as_double(0x7ff8000000000000ll);
+                a.out.max_re[s] = sh.fail ? nan : maxre;
+                a.out.min_zeta[s] = sh.fail ? nan : minz;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void record_kernel(int nbr, int nE, EvalArgs a) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.n; s += gridDim.x * blockDim.x) {
+        const int ei = a.ei[s], ej = a.ej[s];
+        if (ei < 0 || ei >= nE || ej >= nE || ej < -1) continue;
+        const uint8_t S = a.out.severe[s] ? 1 : 0;
+        if (ej < 0 || ej == ei) {
+            a.sev_n1[ei] = S;
+        } else {
+            const long long i = min(ei, ej), j = max(ei, ej);
+            const long long k = i * nE - (i * (i + 1)) / 2 + (j - i - 1);
+            a.sev_pairs[k] = S;
+        }
+    }
+}
+
+}  // namespace
+
+size_t dyn_scratch_doubles(const DevNet& net) { return (size_t)make_dlayout(net).total; }
+
+cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double damping_min, double* scratch,
+                       size_t scratch_per_cta, int grid, int* counter, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    const DLay L = make_dlayout(net);
+    if ((size_t)L.total > scratch_per_cta) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(int) * (size_t)net.ng;
+    dyn_kernel<<<grid, kThreads, smem, s>>>(net, a, o, damping_min, scratch, scratch_per_cta, L, counter);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.sev_n1 && a.sev_pairs) {
+        int blocks = (a.n + 255) / 256;
+        if (blocks > 4096) blocks = 4096;
+        record_kernel<<<blocks, 256, 0, s>>>(net.nbr, net.nE, a);
+        e = cudaGetLastError();
+    }
+    return e;
+}

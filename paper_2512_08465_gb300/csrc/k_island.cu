@@ -1,0 +1,114 @@
+// Scenario decode (Section II-A) and islanding (Section II-B-3).
+//
+// Islanding: one warp per scenario.  The lanes initialise a parent array of
+// the bus graph in shared memory; lane 0 unions the end buses of every
+// in-service branch (union by smaller index, path halving); the lanes then
+// count the roots.  Generator outages do not change the topology.  Every bus
+// counts, so an isolated bus is an island of its own.
+#include "cs_internal.h"
+
+namespace {
+
+constexpr int kWarpsPerBlock = 8;
+
+__device__ int uf_find(int* p, int u) {
+    while (p[u] != u) {
+        p[u] = p[p[u]];
+        u = p[u];
+    }
+    return u;
+}
+
+__global__ void islands_kernel(DevNet net, EvalArgs a, int* islanded) {
+    extern __shared__ int sh_parent[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* parent = sh_parent + warp * net.nb;
+    const int nwarps_total = gridDim.x * kWarpsPerBlock;
+    for (int s = blockIdx.x * kWarpsPerBlock + warp; s < a.n; s += nwarps_total) {
+        const int ei = a.ei[s], ej = a.ej[s];
+        const bool bad = ei < -1 || ej < -1 || ei >= net.nE || ej >= net.nE || (ei < 0 && ej >= 0);
+        if (bad) {
+            if (lane == 0) {
+                atomicOr(a.err, ERR_BAD_ELEMENT);
+                islanded[s] = 2;
+                a.out.klass[s] = 255;
+                a.out.severe[s] = 1;
+                a.out.n_islands[s] = 0;
+                a.out.opf_iters[s] = 0;
+                a.out.cost[s] = __longlong_as_double(0x7ff8000000000000ll);
+                a.out.max_re[s] = __longlong_as_double(0x7ff8000000000000ll);
+                a.out.min_zeta[s] = __longlong_as_double(0x7ff8000000000000ll);
+            }
+            continue;
+        }
+        const Outage o = decode_outage(net.nbr, net.ng, ei, ej);
+        for (int u = lane; u < net.nb; u += 32) parent[u] = u;
+        __syncwarp();
+        if (lane == 0) {
+            for (int b = 0; b < net.nbr; ++b) {
+                if (br_out(o, b)) continue;
+                int x = uf_find(parent, net.f[b]);
+                int y = uf_find(parent, net.t[b]);
+                if (x != y) {
+                    if (x < y) parent[y] = x; else parent[x] = y;
+                }
+            }
+        }
+        __syncwarp();
+        int cnt = 0;
+        for (int u = lane; u < net.nb; u += 32) cnt += (parent[u] == u);
+        for (int off = 16; off; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+        if (lane == 0) {
+            islanded[s] = cnt > 1 ? 1 : 0;
+            a.out.n_islands[s] = (int16_t)(cnt > 32767 ? 32767 : cnt);
+            if (cnt > 1) {
+                a.out.klass[s] = CS_ISLANDED;
+                a.out.severe[s] = 1;
+                a.out.opf_iters[s] = 0;
+                const double nan = __longlong_as_double(0x7ff8000000000000ll);
+                a.out.cost[s] = nan;
+                a.out.max_re[s] = nan;
+                a.out.min_zeta[s] = nan;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// k -> (i, j), i < j, lexicographic: start(i) = i*E - i*(i+1)/2.
+__device__ __forceinline__ long long pair_start(long long i, long long E) {
+    return i * E - (i * (i + 1)) / 2;
+}
+
+__global__ void enumerate_kernel(int E, long long first, long long count, int* ei, int* ej) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long k = first + q;
+        long long lo = 0, hi = E - 2;          // largest i with start(i) <= k
+        while (lo < hi) {
+            long long mid = (lo + hi + 1) >> 1;
+            if (pair_start(mid, E) <= k) lo = mid; else hi = mid - 1;
+        }
+        ei[q] = (int)lo;
+        ej[q] = (int)(k - pair_start(lo, E) + lo + 1);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_islands(const DevNet& net, const EvalArgs& a, int* islanded, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    const size_t smem = sizeof(int) * (size_t)net.nb * kWarpsPerBlock;
+    int blocks = (a.n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (blocks > 4096) blocks = 4096;
+    islands_kernel<<<blocks, 32 * kWarpsPerBlock, smem, s>>>(net, a, islanded);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_enumerate(int nE, int64_t first, int64_t count, int* ei, int* ej, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    long long blocks = (count + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    enumerate_kernel<<<(int)blocks, 256, 0, s>>>(nE, (long long)first, (long long)count, ei, ej);
+    return cudaGetLastError();
+}

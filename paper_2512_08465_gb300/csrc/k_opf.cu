@@ -1,0 +1,771 @@
+// Primal-dual interior-point AC optimal power flow, one scenario per CTA
+// (Section II-B-1: a contingency is severe when the OPF does not converge or
+// its solution violates an operational limit).
+//
+// Algorithm: the MIPS primal-dual interior-point method (Wang, Murillo-Sanchez,
+// Zimmerman, Thomas 2007) in polar coordinates, x = [Va, Vm, Pg, Qg], cost
+// sum c2 (B Pg)^2 + c1 B Pg + c0, equalities = bus power balance and the
+// reference angle, inequalities = |S|^2 flow limits at both branch ends and
+// box bounds on Vm, Pg, Qg.  Start Va = 0, Vm = 1, Pg = (Pmin + Pmax)/2,
+// Qg = 0, z = max(-h, 1), mu = 1/z, lam = 0; step factor 0.99995, centring
+// sigma = 0.1; stop when the feasibility, gradient, complementarity and cost
+// conditions are all below tol, at most max_it iterations.
+//
+// GB300 design:
+//  * persistent grid: each CTA pulls scenarios from an atomic counter, so
+//    scenarios with uneven iteration counts never idle a CTA;
+//  * outaged elements are masked, the network pattern is kept: an outaged
+//    branch contributes numeric zeros and its flow rows are inactive, an
+//    outaged generator's variables are decoupled and its bound rows inactive;
+//  * the Newton system is reduced exactly before factorisation: the generator
+//    variables (diagonal in the Hessian) are eliminated into the multiplier
+//    diagonal, and the reference-angle row is replaced by dVa_ref = 0 (its
+//    multiplier step is recovered from its own Newton row afterwards).  What
+//    remains has one 4x4 block [dVa, dVm, dlamP, dlamQ] per bus and the bus
+//    graph as block pattern;
+//  * that matrix is factorised as a block LDL^T on ONE symbolic analysis per
+//    network (minimum-degree order, elimination tree, fill pattern and
+//    left-looking update lists, built on the host at load time), with the
+//    4x4 pivot blocks inverted by Gauss-Jordan with partial pivoting.  Columns
+//    of one elimination-tree level are independent, so a level is one
+//    parallel step of the CTA (16 threads per target block);
+//  * every branch quantity (flows, first and second derivatives of both end
+//    powers, the weighted 4x4 Hessian) is computed once per iteration by one
+//    thread from the branch's own four voltage variables and gathered by
+//    buses and blocks, deterministically (no atomics).
+#include <cmath>
+
+#include "cs_internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRec = 46;     // doubles per branch record
+constexpr double kXi = 0.99995;
+constexpr double kSigma = 0.1;
+constexpr double kLimitTol = 1e-6;
+
+// record layout
+constexpr int R_DSF = 0, R_DST = 8, R_GF = 16, R_GT = 20, R_H = 24, R_LG = 34, R_NG = 38, R_SF = 42, R_ST = 44;
+
+__device__ __forceinline__ int hidx(int p, int q) {
+    if (p > q) { int t = p; p = q; q = t; }
+    // (0,0)0 (0,1)1 (0,2)2 (0,3)3 (1,1)4 (1,2)5 (1,3)6 (2,2)7 (2,3)8 (3,3)9
+    const int base[4] = {0, 4, 7, 9};
+    return base[p] + (q - p);
+}
+
+struct Lay {
+    // bus
+    int Va, Vm, lP, lQ, zu, zl, muu, mul, gP, gQ, LxVa, LxVm, NVa, NVm, DP, DQ, rP, rQ, dzu, dzl, dmuu, dmul;
+    // gen
+    int Pg, Qg, gz, gmu, gdz, gdmu, MP, MQ, NP, NQ, LxP, LxQ, dPg, dQg;
+    // branch
+    int zf, zt, muf, mut, hf, ht, dzf, dzt, dmuf, dmut, rec;
+    // KKT
+    int Ub, Lb, Db, Di, x;
+    int total;
+};
+
+Lay make_layout(const DevNet& n) {
+    Lay L{};
+    int o = 0;
+    auto take = [&](int cnt) { int r = o; o += cnt; return r; };
+    int nb = n.nb, ng = n.ng, nbr = n.nbr;
+    L.Va = take(nb); L.Vm = take(nb); L.lP = take(nb); L.lQ = take(nb); L.zu = take(nb); L.zl = take(nb);
+    L.muu = take(nb); L.mul = take(nb); L.gP = take(nb); L.gQ = take(nb); L.LxVa = take(nb); L.LxVm = take(nb);
+    L.NVa = take(nb); L.NVm = take(nb); L.DP = take(nb); L.DQ = take(nb); L.rP = take(nb); L.rQ = take(nb);
+    L.dzu = take(nb); L.dzl = take(nb); L.dmuu = take(nb); L.dmul = take(nb);
+    L.Pg = take(ng); L.Qg = take(ng); L.gz = take(4 * ng); L.gmu = take(4 * ng); L.gdz = take(4 * ng);
+    L.gdmu = take(4 * ng); L.MP = take(ng); L.MQ = take(ng); L.NP = take(ng); L.NQ = take(ng);
+    L.LxP = take(ng); L.LxQ = take(ng); L.dPg = take(ng); L.dQg = take(ng);
+    L.zf = take(nbr); L.zt = take(nbr); L.muf = take(nbr); L.mut = take(nbr); L.hf = take(nbr); L.ht = take(nbr);
+    L.dzf = take(nbr); L.dzt = take(nbr); L.dmuf = take(nbr); L.dmut = take(nbr);
+    L.rec = take(kRec * nbr);
+    o = (o + 15) & ~15;
+    L.Ub = take(16 * n.nL); L.Lb = take(16 * n.nL); L.Db = take(16 * nb); L.Di = take(16 * nb);
+    L.x = take(4 * nb);
+    L.total = (o + 31) & ~31;
+    return L;
+}
+
+// ------------------------------------------------------------------ helpers --
+struct RedBuf {
+    double v[10][kThreads];
+};
+
+// reduce K values per thread: ops[k] = 0 max, 1 sum, 2 min.  Result broadcast in out[].
+template <int K>
+__device__ void block_reduce(RedBuf& rb, double (&val)[K], const int (&ops)[K], double* out) {
+    const int tid = threadIdx.x;
+    for (int k = 0; k < K; ++k) rb.v[k][tid] = val[k];
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (tid < s) {
+            for (int k = 0; k < K; ++k) {
+                double a = rb.v[k][tid], b = rb.v[k][tid + s];
+                rb.v[k][tid] = ops[k] == 1 ? a + b : (ops[k] == 0 ? fmax(a, b) : fmin(a, b));
+            }
+        }
+        __syncthreads();
+    }
+    if (tid < K) out[tid] = rb.v[tid][0];
+    __syncthreads();
+}
+
+// Gauss-Jordan inverse of a 4x4 block with partial pivoting; returns false if singular.
+__device__ bool inv4(const double* A, double* Ainv) {
+    double a[4][8];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            a[r][c] = A[4 * r + c];
+            a[r][4 + c] = (r == c) ? 1.0 : 0.0;
+        }
+    for (int c = 0; c < 4; ++c) {
+        int p = c;
+        double best = fabs(a[c][c]);
+        for (int r = c + 1; r < 4; ++r)
+            if (fabs(a[r][c]) > best) { best = fabs(a[r][c]); p = r; }
+        if (!(best > 0.0) || !isfinite(best)) return false;
+        if (p != c)
+            for (int q = 0; q < 8; ++q) { double t = a[c][q]; a[c][q] = a[p][q]; a[p][q] = t; }
+        const double piv = 1.0 / a[c][c];
+        for (int q = 0; q < 8; ++q) a[c][q] *= piv;
+        for (int r = 0; r < 4; ++r) {
+            if (r == c) continue;
+            const double m = a[r][c];
+            if (m != 0.0)
+                for (int q = 0; q < 8; ++q) a[r][q] -= m * a[c][q];
+        }
+    }
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) Ainv[4 * r + c] = a[r][4 + c];
+    return true;
+}
+
+// One branch at the current iterate: flows, derivatives, weighted Hessian,
+// Lagrangian-gradient and N contributions.  If init, also sets z, mu of the
+// two flow rows from h (z = max(-h, 1), mu = gamma / z).
+__device__ void eval_branch(const DevNet& net, int b, double* W, const Lay& L, double gamma,
+                            bool init) {
+    const int f = net.f[b], t = net.t[b];
+    double* rec = W + L.rec + (size_t)kRec * b;
+    const double vf = W[L.Vm + f], vt = W[L.Vm + t];
+    double sf, cf, st, ct;
+    sincos(W[L.Va + f], &sf, &cf);
+    sincos(W[L.Va + t], &st, &ct);
+    const cplx ef = cm(cf, sf), et = cm(ct, st);
+    const cplx Vf = vf * ef, Vt = vt * et;
+    const cplx yff = net.yff[b], yft = net.yft[b], ytf = net.ytf[b], ytt = net.ytt[b];
+    const cplx zero = cm(0.0, 0.0);
+    const cplx dVf[4] = {mulj(Vf), ef, zero, zero};
+    const cplx dVt[4] = {zero, zero, mulj(Vt), et};
+    const cplx If = yff * Vf + yft * Vt;
+    const cplx It = ytf * Vf + ytt * Vt;
+    cplx dIf[4], dIt[4], dSf[4], dSt[4];
+    for (int p = 0; p < 4; ++p) {
+        dIf[p] = yff * dVf[p] + yft * dVt[p];
+        dIt[p] = ytf * dVf[p] + ytt * dVt[p];
+    }
+    const cplx Sf = Vf * conj(If), St = Vt * conj(It);
+    for (int p = 0; p < 4; ++p) {
+        dSf[p] = dVf[p] * conj(If) + Vf * conj(dIf[p]);
+        dSt[p] = dVt[p] * conj(It) + Vt * conj(dIt[p]);
+    }
+    const double smax2 = net.smax2[b];
+    const double hf = abs2(Sf) - smax2, ht = abs2(St) - smax2;
+    double zf, zt, muf, mut;
+    if (init) {
+        zf = fmax(-hf, 1.0);
+        zt = fmax(-ht, 1.0);
+        muf = gamma / zf;
+        mut = gamma / zt;
+        W[L.zf + b] = zf; W[L.zt + b] = zt; W[L.muf + b] = muf; W[L.mut + b] = mut;
+    } else {
+        zf = W[L.zf + b]; zt = W[L.zt + b]; muf = W[L.muf + b]; mut = W[L.mut + b];
+    }
+    W[L.hf + b] = hf;
+    W[L.ht + b] = ht;
+    double gf[4], gt[4];
+    for (int p = 0; p < 4; ++p) {
+        gf[p] = 2.0 * (Sf.re * dSf[p].re + Sf.im * dSf[p].im);
+        gt[p] = 2.0 * (St.re * dSt[p].re + St.im * dSt[p].im);
+    }
+    const double lPf = W[L.lP + f], lQf = W[L.lQ + f], lPt = W[L.lP + t], lQt = W[L.lQ + t];
+    // weights: Re(c * d2S) = lamP Re d2S + lamQ Im d2S + 2 mu Re(conj(S) d2S)
+    const cplx wf = cm(lPf, -lQf) + (2.0 * muf) * conj(Sf);
+    const cplx wt = cm(lPt, -lQt) + (2.0 * mut) * conj(St);
+    const double bf = muf / zf, bt = mut / zt;
+    // second derivatives of V: f end (0,0) -V_f, (0,1) j e_f ; t end (2,2) -V_t, (2,3) j e_t
+    for (int p = 0; p < 4; ++p) {
+        for (int q = p; q < 4; ++q) {
+            cplx d2Vf = zero, d2Vt = zero;
+            if (p == 0 && q == 0) d2Vf = -Vf;
+            if (p == 0 && q == 1) d2Vf = mulj(ef);
+            if (p == 2 && q == 2) d2Vt = -Vt;
+            if (p == 2 && q == 3) d2Vt = mulj(et);
+            const cplx d2If = yff * d2Vf + yft * d2Vt;
+            const cplx d2It = ytf * d2Vf + ytt * d2Vt;
+            const cplx d2Sf = d2Vf * conj(If) + dVf[p] * conj(dIf[q]) + dVf[q] * conj(dIf[p]) + Vf * conj(d2If);
+            const cplx d2St = d2Vt * conj(It) + dVt[p] * conj(dIt[q]) + dVt[q] * conj(dIt[p]) + Vt * conj(d2It);
+            double h = (wf * d2Sf).re + (wt * d2St).re;
+            h += 2.0 * muf * (dSf[q].re * dSf[p].re + dSf[q].im * dSf[p].im);
+            h += 2.0 * mut * (dSt[q].re * dSt[p].re + dSt[q].im * dSt[p].im);
+            h += bf * gf[p] * gf[q] + bt * gt[p] * gt[q];
+            rec[R_H + hidx(p, q)] = h;
+        }
+    }
+    const double nf = (muf * hf + gamma) / zf, nt = (mut * ht + gamma) / zt;
+    for (int p = 0; p < 4; ++p) {
+        rec[R_DSF + 2 * p] = dSf[p].re;
+        rec[R_DSF + 2 * p + 1] = dSf[p].im;
+        rec[R_DST + 2 * p] = dSt[p].re;
+        rec[R_DST + 2 * p + 1] = dSt[p].im;
+        rec[R_GF + p] = gf[p];
+        rec[R_GT + p] = gt[p];
+        rec[R_LG + p] = lPf * dSf[p].re + lQf * dSf[p].im + lPt * dSt[p].re + lQt * dSt[p].im +
+                        muf * gf[p] + mut * gt[p];
+        rec[R_NG + p] = nf * gf[p] + nt * gt[p];
+    }
+    rec[R_SF] = Sf.re;
+    rec[R_SF + 1] = Sf.im;
+    rec[R_ST] = St.re;
+    rec[R_ST + 1] = St.im;
+}
+
+struct Scal {          // per-scenario scalars in shared memory
+    double gamma, f, f_prev, lref, dlref, ap, ad;
+    double red[10];
+    int fail;
+    int conv;
+    int scen;
+};
+
+__global__ void __launch_bounds__(kThreads)
+opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, int max_it,
+           double* scratch, size_t per_cta, Lay L, int* counter) {
+    __shared__ RedBuf rb;
+    __shared__ Scal sc;
+    const int tid = threadIdx.x;
+    double* W = scratch + per_cta * blockIdx.x;
+    const int nb = net.nb, ng = net.ng, nbr = net.nbr;
+    const double B = net.base;
+    const double* Pd = net.Pd + (size_t)a.level * nb;
+    const double* Qd = net.Qd + (size_t)a.level * nb;
+    const int nx = 2 * nb + 2 * ng;
+
+    for (;;) {
+        if (tid == 0) sc.scen = atomicAdd(counter, 1);
+        __syncthreads();
+        const int s = sc.scen;
+        if (s >= a.n) break;
+        if (islanded[s] != 0) {                // islanded or invalid: nothing to do here
+            if (tid == 0) o.status[s] = 3;
+            __syncthreads();
+            continue;
+        }
+        const Outage out = decode_outage(nbr, ng, a.ei[s], a.ej[s]);
+        const int nbr_act = nbr - (out.br0 >= 0) - (out.br1 >= 0);
+        const int ng_act = ng - (out.g0 >= 0) - (out.g1 >= 0);
+        const double niq = 2.0 * nbr_act + 2.0 * nb + 4.0 * ng_act;
+
+        // ---------------- initial point ----------------
+        if (tid == 0) {
+            sc.gamma = 1.0;
+            sc.lref = 0.0;
+            sc.fail = 0;
+            sc.conv = 0;
+        }
+        for (int i = tid; i < nb; i += kThreads) {
+            W[L.Va + i] = 0.0;
+            W[L.Vm + i] = 1.0;
+            W[L.lP + i] = 0.0;
+            W[L.lQ + i] = 0.0;
+        }
+        for (int k = tid; k < ng; k += kThreads) {
+            const bool off = gen_out(out, k);
+            W[L.Pg + k] = off ? 0.0 : 0.5 * (net.pmin[k] + net.pmax[k]);
+            W[L.Qg + k] = 0.0;
+        }
+        __syncthreads();
+        const int ops10[10] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 0};
+        int it = 0;
+        // evaluate(x) then the convergence quantities; init = first call
+        auto evaluate = [&](bool init) {
+            const double gamma = init ? 1.0 : sc.gamma;
+            for (int b = tid; b < nbr; b += kThreads) {
+                if (br_out(out, b)) {
+                    double* rec = W + L.rec + (size_t)kRec * b;
+                    for (int q = 0; q < kRec; ++q) rec[q] = 0.0;
+                    W[L.zf + b] = 1.0; W[L.zt + b] = 1.0; W[L.muf + b] = 0.0; W[L.mut + b] = 0.0;
+                    W[L.hf + b] = -1.0; W[L.ht + b] = -1.0;
+                    continue;
+                }
+                eval_branch(net, b, W, L, gamma, init);
+            }
+            __syncthreads();
+            // per-thread partial reductions: maxg, maxh, maxx, maxz, maxmu, maxLx, maxlam, sumzmu, cost, nonfinite
+            double v[10] = {0.0, -INFINITY, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int b = tid; b < nbr; b += kThreads) {
+                if (br_out(out, b)) continue;
+                const double zf = W[L.zf + b], zt = W[L.zt + b], mf = W[L.muf + b], mt = W[L.mut + b];
+                v[1] = fmax(v[1], fmax(W[L.hf + b], W[L.ht + b]));
+                v[3] = fmax(v[3], fmax(zf, zt));
+                v[4] = fmax(v[4], fmax(mf, mt));
+                v[7] += zf * mf + zt * mt;
+            }
+            for (int i = tid; i < nb; i += kThreads) {
+                const double Vm = W[L.Vm + i], Va = W[L.Va + i];
+                const double hu = Vm - net.vmax[i], hl = net.vmin[i] - Vm;
+                double zu, zl, muu, mul;
+                if (init) {
+                    zu = fmax(-hu, 1.0); zl = fmax(-hl, 1.0);
+                    muu = gamma / zu; mul = gamma / zl;
+                    W[L.zu + i] = zu; W[L.zl + i] = zl; W[L.muu + i] = muu; W[L.mul + i] = mul;
+                } else {
+                    zu = W[L.zu + i]; zl = W[L.zl + i]; muu = W[L.muu + i]; mul = W[L.mul + i];
+                }
+                const double lP = W[L.lP + i], lQ = W[L.lQ + i];
+                double Sre = Vm * Vm * net.gsh[i], Sim = -Vm * Vm * net.bsh[i];
+                double LxVa = 0.0, LxVm = 2.0 * Vm * (lP * net.gsh[i] - lQ * net.bsh[i]) + muu - mul;
+                double NVa = 0.0, NVm = (muu * hu + gamma) / zu - (mul * hl + gamma) / zl;
+                for (int e = net.bus_br_ptr[i]; e < net.bus_br_ptr[i + 1]; ++e) {
+                    const int code = net.bus_br[e];
+                    const int b = code >> 1, side = code & 1;
+                    if (br_out(out, b)) continue;
+                    const double* rec = W + L.rec + (size_t)kRec * b;
+                    Sre += rec[side ? R_ST : R_SF];
+                    Sim += rec[(side ? R_ST : R_SF) + 1];
+                    const int p0 = 2 * side;
+                    LxVa += rec[R_LG + p0];
+                    LxVm += rec[R_LG + p0 + 1];
+                    NVa += rec[R_NG + p0];
+                    NVm += rec[R_NG + p0 + 1];
+                }
+                if (i == net.ref) LxVa += sc.lref;
+                double Pgen = 0.0, Qgen = 0.0, DP = 0.0, DQ = 0.0, rP = 0.0, rQ = 0.0;
+                for (int e = net.bus_gen_ptr[i]; e < net.bus_gen_ptr[i + 1]; ++e) {
+                    const int k = net.bus_gen[e];
+                    if (gen_out(out, k)) continue;
+                    const double Pg = W[L.Pg + k], Qg = W[L.Qg + k];
+                    const double h4[4] = {Pg - net.pmax[k], net.pmin[k] - Pg, Qg - net.qmax[k], net.qmin[k] - Qg};
+                    double z4[4], m4[4];
+                    for (int q = 0; q < 4; ++q) {
+                        if (init) {
+                            z4[q] = fmax(-h4[q], 1.0);
+                            m4[q] = gamma / z4[q];
+                            W[L.gz + 4 * k + q] = z4[q];
+                            W[L.gmu + 4 * k + q] = m4[q];
+                        } else {
+                            z4[q] = W[L.gz + 4 * k + q];
+                            m4[q] = W[L.gmu + 4 * k + q];
+                        }
+                        v[1] = fmax(v[1], h4[q]);
+                        v[3] = fmax(v[3], z4[q]);
+                        v[4] = fmax(v[4], m4[q]);
+                        v[7] += z4[q] * m4[q];
+                    }
+                    const double PgMW = B * Pg;
+                    const double LxP = B * (2.0 * net.c2[k] * PgMW + net.c1[k]) - lP + m4[0] - m4[1];
+                    const double LxQ = -lQ + m4[2] - m4[3];
+                    const double NP = LxP + (m4[0] * h4[0] + gamma) / z4[0] - (m4[1] * h4[1] + gamma) / z4[1];
+                    const double NQ = LxQ + (m4[2] * h4[2] + gamma) / z4[2] - (m4[3] * h4[3] + gamma) / z4[3];
+                    const double MP = 2.0 * net.c2[k] * B * B + m4[0] / z4[0] + m4[1] / z4[1];
+                    const double MQ = m4[2] / z4[2] + m4[3] / z4[3];
+                    W[L.LxP + k] = LxP; W[L.LxQ + k] = LxQ; W[L.NP + k] = NP; W[L.NQ + k] = NQ;
+                    W[L.MP + k] = MP; W[L.MQ + k] = MQ;
+                    DP += 1.0 / MP;
+                    DQ += 1.0 / MQ;
+                    rP += NP / MP;
+                    rQ += NQ / MQ;
+                    Pgen += Pg;
+                    Qgen += Qg;
+                    v[2] = fmax(v[2], fmax(fabs(Pg), fabs(Qg)));
+                    v[5] = fmax(v[5], fmax(fabs(LxP), fabs(LxQ)));
+                    v[8] += net.c2[k] * PgMW * PgMW + net.c1[k] * PgMW + net.c0[k];
+                }
+                NVa += LxVa;
+                NVm += LxVm;
+                const double gP = Sre - Pgen + Pd[i], gQ = Sim - Qgen + Qd[i];
+                W[L.gP + i] = gP; W[L.gQ + i] = gQ;
+                W[L.LxVa + i] = LxVa; W[L.LxVm + i] = LxVm; W[L.NVa + i] = NVa; W[L.NVm + i] = NVm;
+                W[L.DP + i] = DP; W[L.DQ + i] = DQ; W[L.rP + i] = rP; W[L.rQ + i] = rQ;
+                v[0] = fmax(v[0], fmax(fabs(gP), fabs(gQ)));
+                v[1] = fmax(v[1], fmax(hu, hl));
+                v[2] = fmax(v[2], fmax(fabs(Va), fabs(Vm)));
+                v[3] = fmax(v[3], fmax(zu, zl));
+                v[4] = fmax(v[4], fmax(muu, mul));
+                v[5] = fmax(v[5], fmax(fabs(LxVa), fabs(LxVm)));
+                v[6] = fmax(v[6], fmax(fabs(lP), fabs(lQ)));
+                v[7] += zu * muu + zl * mul;
+                if (!isfinite(gP) || !isfinite(gQ) || !isfinite(NVa) || !isfinite(NVm)) v[9] = 1.0;
+            }
+            if (tid == 0) v[6] = fmax(v[6], fabs(sc.lref));
+            block_reduce<10>(rb, v, ops10, sc.red);
+            if (tid == 0) {
+                const double maxg = sc.red[0], maxh = sc.red[1], maxx = sc.red[2], maxz = sc.red[3];
+                const double maxmu = sc.red[4], maxLx = sc.red[5], maxlam = sc.red[6], zmu = sc.red[7];
+                sc.f = sc.red[8];
+                if (init) sc.f_prev = sc.f;
+                const double feas = fmax(maxg, maxh) / (1.0 + fmax(maxx, maxz));
+                const double grad = maxLx / (1.0 + fmax(maxlam, maxmu));
+                const double comp = zmu / (1.0 + maxx);
+                const double cost = fabs(sc.f - sc.f_prev) / (1.0 + fabs(sc.f_prev));
+                if (sc.red[9] != 0.0 || !isfinite(sc.f) || !isfinite(feas) || !isfinite(grad) || !isfinite(comp))
+                    sc.fail = 1;
+                sc.conv = (feas < tol && grad < tol && comp < tol && cost < tol) ? 1 : 0;
+            }
+            __syncthreads();
+        };
+
+        evaluate(true);
+
+        while (!sc.conv && !sc.fail && it < max_it) {
+            ++it;
+            const double gamma = sc.gamma;
+            // ---------------- assemble the reduced KKT blocks ----------------
+            for (int tg = tid; tg < nb + net.nL; tg += kThreads) {
+                double blk[16];
+                for (int q = 0; q < 16; ++q) blk[q] = 0.0;
+                if (tg < nb) {
+                    const int j = tg, i = net.perm[j];
+                    const double Vm = W[L.Vm + i];
+                    double J[2][2] = {{0.0, 2.0 * net.gsh[i] * Vm}, {0.0, -2.0 * net.bsh[i] * Vm}};
+                    blk[5] = 2.0 * (W[L.lP + i] * net.gsh[i] - W[L.lQ + i] * net.bsh[i]) +
+                             W[L.muu + i] / W[L.zu + i] + W[L.mul + i] / W[L.zl + i];
+                    for (int e = net.bus_br_ptr[i]; e < net.bus_br_ptr[i + 1]; ++e) {
+                        const int code = net.bus_br[e];
+                        const int b = code >> 1, side = code & 1;
+                        if (br_out(out, b)) continue;
+                        const double* rec = W + L.rec + (size_t)kRec * b;
+                        const int p0 = 2 * side;
+                        const double* dS = rec + (side ? R_DST : R_DSF);
+                        for (int r = 0; r < 2; ++r)
+                            for (int c = 0; c < 2; ++c) blk[4 * r + c] += rec[R_H + hidx(p0 + r, p0 + c)];
+                        for (int c = 0; c < 2; ++c) {
+                            J[0][c] += dS[2 * (p0 + c)];
+                            J[1][c] += dS[2 * (p0 + c) + 1];
+                        }
+                    }
+                    for (int q = 0; q < 2; ++q)
+                        for (int r = 0; r < 2; ++r) {
+                            blk[4 * r + 2 + q] = J[q][r];
+                            blk[4 * (2 + q) + r] = J[q][r];
+                        }
+                    blk[10] = -W[L.DP + i];
+                    blk[15] = -W[L.DQ + i];
+                    if (i == net.ref) {
+                        for (int q = 0; q < 4; ++q) { blk[q] = 0.0; blk[4 * q] = 0.0; }
+                        blk[0] = 1.0;
+                    }
+                    double* D = W + L.Db + 16 * j;
+                    for (int q = 0; q < 16; ++q) D[q] = blk[q];
+                    double* x = W + L.x + 4 * j;
+                    x[0] = (i == net.ref) ? 0.0 : -W[L.NVa + i];
+                    x[1] = -W[L.NVm + i];
+                    x[2] = -W[L.gP + i] - W[L.rP + i];
+                    x[3] = -W[L.gQ + i] - W[L.rQ + i];
+                } else {
+                    const int q = tg - nb;
+                    const int Rn = net.Lrow[q], Cn = net.Lcol[q];
+                    const int Rb = net.perm[Rn], Cb = net.perm[Cn];
+                    for (int e = net.blk_br_ptr[q]; e < net.blk_br_ptr[q + 1]; ++e) {
+                        const int b = net.blk_br[e];
+                        if (br_out(out, b)) continue;
+                        const double* rec = W + L.rec + (size_t)kRec * b;
+                        const bool flip = (net.f[b] != Rb);     // stored block is (t row, f col)
+                        double K[16];
+                        for (int r = 0; r < 4; ++r)
+                            for (int c = 0; c < 4; ++c) {
+                                double v;
+                                if (r < 2 && c < 2) v = rec[R_H + hidx(r, 2 + c)];
+                                else if (r < 2) v = rec[R_DST + 2 * r + (c - 2)];          // J(t,f)^T
+                                else if (c < 2) v = rec[R_DSF + 2 * (2 + c) + (r - 2)];    // J(f,t)
+                                else v = 0.0;
+                                K[4 * r + c] = v;
+                            }
+                        for (int r = 0; r < 4; ++r)
+                            for (int c = 0; c < 4; ++c) blk[4 * r + c] += flip ? K[4 * c + r] : K[4 * r + c];
+                    }
+                    if (Rb == net.ref) for (int c = 0; c < 4; ++c) blk[c] = 0.0;
+                    if (Cb == net.ref) for (int r = 0; r < 4; ++r) blk[4 * r] = 0.0;
+                    double* U = W + L.Ub + 16 * q;
+                    for (int c = 0; c < 16; ++c) U[c] = blk[c];
+                }
+            }
+            __syncthreads();
+            // ---------------- block LDL^T, level by level ----------------
+            for (int lev = 0; lev < net.nlevels; ++lev) {
+                const int t0 = net.tgt_ptr[lev], t1 = net.tgt_ptr[lev + 1];
+                for (int w = tid; w < 16 * (t1 - t0); w += kThreads) {
+                    const int tg = net.tgt[t0 + (w >> 4)];
+                    const int r = (w & 15) >> 2, c = w & 3;
+                    double* A = (tg < nb) ? (W + L.Db + 16 * tg) : (W + L.Ub + 16 * (tg - nb));
+                    double acc = A[4 * r + c];
+                    for (int u = net.upd_ptr[tg]; u < net.upd_ptr[tg + 1]; ++u) {
+                        const double* La = W + L.Lb + 16 * net.upd_a[u] + 4 * r;
+                        const double* Ubb = W + L.Ub + 16 * net.upd_b[u] + 4 * c;
+                        acc -= La[0] * Ubb[0] + La[1] * Ubb[1] + La[2] * Ubb[2] + La[3] * Ubb[3];
+                    }
+                    A[4 * r + c] = acc;
+                }
+                __syncthreads();
+                for (int w = net.lev_ptr[lev] + tid; w < net.lev_ptr[lev + 1]; w += kThreads) {
+                    const int j = net.lev_col[w];
+                    if (!inv4(W + L.Db + 16 * j, W + L.Di + 16 * j)) sc.fail = 1;
+                }
+                __syncthreads();
+                for (int w = tid; w < 16 * (t1 - t0); w += kThreads) {
+                    const int tg = net.tgt[t0 + (w >> 4)];
+                    if (tg < nb) continue;
+                    const int q = tg - nb;
+                    const int r = (w & 15) >> 2, c = w & 3;
+                    const double* U = W + L.Ub + 16 * q + 4 * r;
+                    const double* Di = W + L.Di + 16 * net.Lcol[q] + c;
+                    W[L.Lb + 16 * q + 4 * r + c] = U[0] * Di[0] + U[1] * Di[4] + U[2] * Di[8] + U[3] * Di[12];
+                }
+                __syncthreads();
+            }
+            if (sc.fail) break;
+            // ---------------- solve: L y = b, D w = y, L^T x = w ----------------
+            for (int lev = 0; lev < net.nlevels; ++lev) {
+                const int c0 = net.lev_ptr[lev], c1 = net.lev_ptr[lev + 1];
+                for (int w = tid; w < 4 * (c1 - c0); w += kThreads) {
+                    const int j = net.lev_col[c0 + (w >> 2)], r = w & 3;
+                    double acc = W[L.x + 4 * j + r];
+                    for (int e = net.Lrowptr[j]; e < net.Lrowptr[j + 1]; ++e) {
+                        const double* Lq = W + L.Lb + 16 * net.Lrowblk[e] + 4 * r;
+                        const double* y = W + L.x + 4 * net.Lrowcol[e];
+                        acc -= Lq[0] * y[0] + Lq[1] * y[1] + Lq[2] * y[2] + Lq[3] * y[3];
+                    }
+                    W[L.x + 4 * j + r] = acc;
+                }
+                __syncthreads();
+            }
+            for (int j = tid; j < nb; j += kThreads) {
+                const double* Di = W + L.Di + 16 * j;
+                double* y = W + L.x + 4 * j;
+                const double y0 = y[0], y1 = y[1], y2 = y[2], y3 = y[3];
+                for (int r = 0; r < 4; ++r)
+                    y[r] = Di[4 * r] * y0 + Di[4 * r + 1] * y1 + Di[4 * r + 2] * y2 + Di[4 * r + 3] * y3;
+            }
+            __syncthreads();
+            for (int lev = net.nlevels - 1; lev >= 0; --lev) {
+                const int c0 = net.lev_ptr[lev], c1 = net.lev_ptr[lev + 1];
+                for (int w = tid; w < 4 * (c1 - c0); w += kThreads) {
+                    const int j = net.lev_col[c0 + (w >> 2)], r = w & 3;
+                    double acc = W[L.x + 4 * j + r];
+                    for (int e = net.Lcolptr[j]; e < net.Lcolptr[j + 1]; ++e) {
+                        const double* Lq = W + L.Lb + 16 * e + r;
+                        const double* xi = W + L.x + 4 * net.Lrow[e];
+                        acc -= Lq[0] * xi[0] + Lq[4] * xi[1] + Lq[8] * xi[2] + Lq[12] * xi[3];
+                    }
+                    W[L.x + 4 * j + r] = acc;
+                }
+                __syncthreads();
+            }
+            // ---------------- recover the eliminated steps, dz, dmu, ratios ----------------
+            double rp = INFINITY, rd = INFINITY, bad = 0.0;
+            for (int k = tid; k < ng; k += kThreads) {
+                if (gen_out(out, k)) continue;
+                const int jn = net.iperm[net.gbus[k]];
+                const double dlP = W[L.x + 4 * jn + 2], dlQ = W[L.x + 4 * jn + 3];
+                const double dPg = (-W[L.NP + k] + dlP) / W[L.MP + k];
+                const double dQg = (-W[L.NQ + k] + dlQ) / W[L.MQ + k];
+                W[L.dPg + k] = dPg;
+                W[L.dQg + k] = dQg;
+                const double Pg = W[L.Pg + k], Qg = W[L.Qg + k];
+                const double h4[4] = {Pg - net.pmax[k], net.pmin[k] - Pg, Qg - net.qmax[k], net.qmin[k] - Qg};
+                const double dh4[4] = {dPg, -dPg, dQg, -dQg};
+                for (int q = 0; q < 4; ++q) {
+                    const double z = W[L.gz + 4 * k + q], m = W[L.gmu + 4 * k + q];
+                    const double dz = -h4[q] - z - dh4[q];
+                    const double dm = -m + (gamma - m * dz) / z;
+                    W[L.gdz + 4 * k + q] = dz;
+                    W[L.gdmu + 4 * k + q] = dm;
+                    if (dz < 0.0) rp = fmin(rp, -z / dz);
+                    if (dm < 0.0) rd = fmin(rd, -m / dm);
+                    if (!isfinite(dz) || !isfinite(dm)) bad = 1.0;
+                }
+            }
+            for (int b = tid; b < nbr; b += kThreads) {
+                if (br_out(out, b)) continue;
+                const double* rec = W + L.rec + (size_t)kRec * b;
+                const int fn = net.iperm[net.f[b]], tn = net.iperm[net.t[b]];
+                const double dx[4] = {W[L.x + 4 * fn], W[L.x + 4 * fn + 1], W[L.x + 4 * tn], W[L.x + 4 * tn + 1]};
+                double gdf = 0.0, gdt = 0.0;
+                for (int p = 0; p < 4; ++p) {
+                    gdf += rec[R_GF + p] * dx[p];
+                    gdt += rec[R_GT + p] * dx[p];
+                }
+                const double zf = W[L.zf + b], zt = W[L.zt + b], mf = W[L.muf + b], mt = W[L.mut + b];
+                const double dzf = -W[L.hf + b] - zf - gdf, dzt = -W[L.ht + b] - zt - gdt;
+                const double dmf = -mf + (gamma - mf * dzf) / zf, dmt = -mt + (gamma - mt * dzt) / zt;
+                W[L.dzf + b] = dzf; W[L.dzt + b] = dzt; W[L.dmuf + b] = dmf; W[L.dmut + b] = dmt;
+                if (dzf < 0.0) rp = fmin(rp, -zf / dzf);
+                if (dzt < 0.0) rp = fmin(rp, -zt / dzt);
+                if (dmf < 0.0) rd = fmin(rd, -mf / dmf);
+                if (dmt < 0.0) rd = fmin(rd, -mt / dmt);
+                if (!isfinite(dzf) || !isfinite(dzt) || !isfinite(dmf) || !isfinite(dmt)) bad = 1.0;
+            }
+            for (int i = tid; i < nb; i += kThreads) {
+                const int jn = net.iperm[i];
+                const double dVm = W[L.x + 4 * jn + 1];
+                const double Vm = W[L.Vm + i];
+                const double hu = Vm - net.vmax[i], hl = net.vmin[i] - Vm;
+                const double zu = W[L.zu + i], zl = W[L.zl + i], mu_ = W[L.muu + i], ml = W[L.mul + i];
+                const double dzu = -hu - zu - dVm, dzl = -hl - zl + dVm;
+                const double dmu = -mu_ + (gamma - mu_ * dzu) / zu, dml = -ml + (gamma - ml * dzl) / zl;
+                W[L.dzu + i] = dzu; W[L.dzl + i] = dzl; W[L.dmuu + i] = dmu; W[L.dmul + i] = dml;
+                if (dzu < 0.0) rp = fmin(rp, -zu / dzu);
+                if (dzl < 0.0) rp = fmin(rp, -zl / dzl);
+                if (dmu < 0.0) rd = fmin(rd, -mu_ / dmu);
+                if (dml < 0.0) rd = fmin(rd, -ml / dml);
+                for (int r = 0; r < 4; ++r)
+                    if (!isfinite(W[L.x + 4 * jn + r])) bad = 1.0;
+            }
+            if (tid == 0) {
+                // multiplier step of the reference-angle row from its Newton row
+                const int i = net.ref;
+                double row = 0.0;
+                for (int e = net.bus_br_ptr[i]; e < net.bus_br_ptr[i + 1]; ++e) {
+                    const int code = net.bus_br[e];
+                    const int b = code >> 1, side = code & 1;
+                    if (br_out(out, b)) continue;
+                    const double* rec = W + L.rec + (size_t)kRec * b;
+                    const int fn = net.iperm[net.f[b]], tn = net.iperm[net.t[b]];
+                    const double dx[4] = {W[L.x + 4 * fn], W[L.x + 4 * fn + 1], W[L.x + 4 * tn], W[L.x + 4 * tn + 1]};
+                    const int p = 2 * side;
+                    for (int q = 0; q < 4; ++q) row += rec[R_H + hidx(p, q)] * dx[q];
+                    row += rec[R_DSF + 2 * p] * W[L.x + 4 * fn + 2] + rec[R_DSF + 2 * p + 1] * W[L.x + 4 * fn + 3];
+                    row += rec[R_DST + 2 * p] * W[L.x + 4 * tn + 2] + rec[R_DST + 2 * p + 1] * W[L.x + 4 * tn + 3];
+                }
+                sc.dlref = -W[L.NVa + i] - row;
+            }
+            {
+                double v3[3] = {rp, rd, bad};
+                const int ops3[3] = {2, 2, 0};
+                block_reduce<3>(rb, v3, ops3, sc.red);
+            }
+            if (tid == 0) {
+                sc.ap = fmin(kXi * sc.red[0], 1.0);
+                sc.ad = fmin(kXi * sc.red[1], 1.0);
+                if (sc.red[2] != 0.0 || !isfinite(sc.dlref)) sc.fail = 1;
+            }
+            __syncthreads();
+            if (sc.fail) break;
+            // ---------------- update ----------------
+            const double ap = sc.ap, ad = sc.ad;
+            double zmu = 0.0;
+            for (int i = tid; i < nb; i += kThreads) {
+                const int jn = net.iperm[i];
+                W[L.Va + i] += ap * W[L.x + 4 * jn];
+                W[L.Vm + i] += ap * W[L.x + 4 * jn + 1];
+                W[L.lP + i] += ad * W[L.x + 4 * jn + 2];
+                W[L.lQ + i] += ad * W[L.x + 4 * jn + 3];
+                const double zu = W[L.zu + i] + ap * W[L.dzu + i], zl = W[L.zl + i] + ap * W[L.dzl + i];
+                const double mu_ = W[L.muu + i] + ad * W[L.dmuu + i], ml = W[L.mul + i] + ad * W[L.dmul + i];
+                W[L.zu + i] = zu; W[L.zl + i] = zl; W[L.muu + i] = mu_; W[L.mul + i] = ml;
+                zmu += zu * mu_ + zl * ml;
+            }
+            for (int k = tid; k < ng; k += kThreads) {
+                if (gen_out(out, k)) continue;
+                W[L.Pg + k] += ap * W[L.dPg + k];
+                W[L.Qg + k] += ap * W[L.dQg + k];
+                for (int q = 0; q < 4; ++q) {
+                    const double z = W[L.gz + 4 * k + q] + ap * W[L.gdz + 4 * k + q];
+                    const double m = W[L.gmu + 4 * k + q] + ad * W[L.gdmu + 4 * k + q];
+                    W[L.gz + 4 * k + q] = z;
+                    W[L.gmu + 4 * k + q] = m;
+                    zmu += z * m;
+                }
+            }
+            for (int b = tid; b < nbr; b += kThreads) {
+                if (br_out(out, b)) continue;
+                const double zf = W[L.zf + b] + ap * W[L.dzf + b], zt = W[L.zt + b] + ap * W[L.dzt + b];
+                const double mf = W[L.muf + b] + ad * W[L.dmuf + b], mt = W[L.mut + b] + ad * W[L.dmut + b];
+                W[L.zf + b] = zf; W[L.zt + b] = zt; W[L.muf + b] = mf; W[L.mut + b] = mt;
+                zmu += zf * mf + zt * mt;
+            }
+            {
+                double v1[1] = {zmu};
+                const int ops1[1] = {1};
+                block_reduce<1>(rb, v1, ops1, sc.red);
+            }
+            if (tid == 0) {
+                sc.lref += ad * sc.dlref;
+                sc.gamma = kSigma * sc.red[0] / niq;
+                sc.f_prev = sc.f;
+            }
+            __syncthreads();
+            evaluate(false);
+        }
+        // ---------------- outputs ----------------
+        double viol = 0.0;
+        const bool converged = sc.conv && !sc.fail;
+        if (converged) {
+            for (int b = tid; b < nbr; b += kThreads) {
+                if (br_out(out, b)) continue;
+                const double sm = sqrt(net.smax2[b]);
+                const double sf = sqrt(fmax(W[L.hf + b] + net.smax2[b], 0.0));
+                const double st = sqrt(fmax(W[L.ht + b] + net.smax2[b], 0.0));
+                if (sf - sm > kLimitTol || st - sm > kLimitTol) viol = 1.0;
+            }
+            for (int i = tid; i < nb; i += kThreads) {
+                const double Vm = W[L.Vm + i];
+                if (Vm - net.vmax[i] > kLimitTol || net.vmin[i] - Vm > kLimitTol) viol = 1.0;
+            }
+            for (int k = tid; k < ng; k += kThreads) {
+                if (gen_out(out, k)) continue;
+                const double Pg = W[L.Pg + k], Qg = W[L.Qg + k];
+                if (Pg - net.pmax[k] > kLimitTol || net.pmin[k] - Pg > kLimitTol ||
+                    Qg - net.qmax[k] > kLimitTol || net.qmin[k] - Qg > kLimitTol) viol = 1.0;
+            }
+        }
+        {
+            double v1[1] = {viol};
+            const int ops1[1] = {0};
+            block_reduce<1>(rb, v1, ops1, sc.red);
+        }
+        double* xs = o.x + (size_t)s * nx;
+        for (int i = tid; i < nb; i += kThreads) {
+            xs[i] = W[L.Va + i];
+            xs[nb + i] = W[L.Vm + i];
+            if (a.out.Va) a.out.Va[(size_t)s * nb + i] = W[L.Va + i];
+            if (a.out.Vm) a.out.Vm[(size_t)s * nb + i] = W[L.Vm + i];
+        }
+        for (int k = tid; k < ng; k += kThreads) {
+            xs[2 * nb + k] = W[L.Pg + k];
+            xs[2 * nb + ng + k] = W[L.Qg + k];
+        }
+        if (tid == 0) {
+            const double nan = __longlong_as_double(0x7ff8000000000000ll);
+            a.out.opf_iters[s] = (int16_t)it;
+            a.out.cost[s] = converged ? sc.f : nan;
+            if (!converged || sc.red[0] != 0.0) {
+                o.status[s] = 2;
+                a.out.klass[s] = converged ? CS_LIMIT : CS_OPF_NONCONV;
+                a.out.severe[s] = 1;
+                a.out.max_re[s] = nan;
+                a.out.min_zeta[s] = nan;
+            } else {
+                o.status[s] = 1;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t opf_scratch_doubles(const DevNet& net) { return (size_t)make_layout(net).total; }
+
+cudaError_t launch_opf(const DevNet& net, const EvalArgs& a, const int* islanded, OpfOut o, double tol,
+                       int max_it, double* scratch, size_t scratch_per_cta, int grid, int* counter,
+                       cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    const Lay L = make_layout(net);
+    if ((size_t)L.total > scratch_per_cta) return cudaErrorInvalidValue;
+    opf_kernel<<<grid, kThreads, 0, s>>>(net, a, islanded, o, tol, max_it, scratch, scratch_per_cta, L, counter);
+    return cudaGetLastError();
+}
