@@ -185,8 +185,16 @@ cs_status cs_enumerate_pairs_device(int32_t n_elem, int64_t first, int64_t count
 /* Message of the last failing call on ctx (never NULL; "" if none). */
 const char* cs_last_error(cs_ctx* ctx);
 
-/* Counters of the last cs_evaluate_device call: kernel launches issued. */
+/* Kernel launches issued by the last cs_evaluate_device / cs_submit call. */
 int64_t cs_last_launch_count(cs_ctx* ctx);
+
+/* Per-kernel device timing (off by default).  When enabled, every evaluation
+ * records CUDA events on its stream around the islanding, OPF and small-signal
+ * launches.  cs_kernel_times waits for those events and returns the summed
+ * milliseconds per kernel (ms[3]: islanding, OPF, small-signal + recording) and
+ * the launch counts (launches[3], may be NULL) since cs_set_timing was called. */
+cs_status cs_set_timing(cs_ctx* ctx, int32_t enable);
+cs_status cs_kernel_times(cs_ctx* ctx, double* ms, int64_t* launches);
 
 #ifdef __cplusplus
 }

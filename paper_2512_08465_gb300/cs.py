@@ -28,7 +28,7 @@ RISK_EQ3, RISK_ORDERED = 0, 1
 EXPORTS = ("cs_default_options", "cs_create", "cs_destroy", "cs_load_network", "cs_unload_network",
            "cs_base_result", "cs_evaluate_device", "cs_sync", "cs_submit_contingencies", "cs_poll",
            "cs_risk_index", "cs_risk_reduce_device", "cs_enumerate_pairs_device", "cs_last_error",
-           "cs_last_launch_count")
+           "cs_last_launch_count", "cs_set_timing", "cs_kernel_times")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -97,6 +97,8 @@ def load_library(build_if_missing: bool = True):
         "cs_enumerate_pairs_device": (i32, [i32, i64, i64, P, P, P]),
         "cs_last_error": (ctypes.c_char_p, [P]),
         "cs_last_launch_count": (i64, [P]),
+        "cs_set_timing": (i32, [P, i32]),
+        "cs_kernel_times": (i32, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -233,6 +235,16 @@ class Context:
 
     def last_launch_count(self) -> int:
         return int(self.lib.cs_last_launch_count(self.h))
+
+    def set_timing(self, enable: bool = True):
+        self._check(self.lib.cs_set_timing(self.h, int(enable)), "cs_set_timing")
+
+    def kernel_times(self):
+        """(ms per kernel, launches per kernel) for islanding, OPF, small-signal."""
+        ms = np.zeros(3)
+        cnt = np.zeros(3, np.int64)
+        self._check(self.lib.cs_kernel_times(self.h, _ptr(ms), _ptr(cnt)), "cs_kernel_times")
+        return dict(zip(("islands", "opf", "dyn"), ms.tolist())), dict(zip(("islands", "opf", "dyn"), cnt.tolist()))
 
     def submit(self, net_id: int, level: int, ei, ej) -> int:
         """Non-blocking submission with host arrays; returns a request id."""

@@ -76,6 +76,13 @@ struct cs_ctx {
     // workspace
     DevBuf scratch, isl, opfx, opfst, counters, err_word;
     int64_t launches = 0;
+    // optional per-kernel timing (cs_set_timing): events around each launch
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;      // pairs (start, stop) per kernel launch, reused
+    std::vector<int> ev_kind;         // 0 islands, 1 opf, 2 dyn (+record)
+    size_t ev_used = 0;
+    double kernel_ms[3] = {0.0, 0.0, 0.0};
+    int64_t kernel_launches[3] = {0, 0, 0};
 };
 
 namespace {
@@ -152,11 +159,35 @@ cs_status evaluate_impl(cs_ctx* ctx, Network* net, int level, const int32_t* ei,
         a.err = (int*)ctx->err_word.p;
         OpfOut o{(double*)ctx->opfx.p, (int*)ctx->opfst.p};
         CS_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * 4, s));
+        auto mark = [&](int kind) -> cudaError_t {     // start event of a timed launch
+            if (!ctx->timing) return cudaSuccess;
+            while (ctx->ev.size() < 2 * (ctx->ev_used + 1)) {
+                cudaEvent_t e;
+                cudaError_t r = cudaEventCreate(&e);
+                if (r != cudaSuccess) return r;
+                ctx->ev.push_back(e);
+            }
+            if ((int)ctx->ev_kind.size() <= (int)ctx->ev_used) ctx->ev_kind.resize(ctx->ev_used + 1);
+            ctx->ev_kind[ctx->ev_used] = kind;
+            return cudaEventRecord(ctx->ev[2 * ctx->ev_used], s);
+        };
+        auto done = [&]() -> cudaError_t {
+            if (!ctx->timing) return cudaSuccess;
+            cudaError_t r = cudaEventRecord(ctx->ev[2 * ctx->ev_used + 1], s);
+            ctx->ev_used++;
+            return r;
+        };
+        CS_CUDA(mark(0));
         CS_CUDA(launch_islands(dn, a, (int*)ctx->isl.p, s));
+        CS_CUDA(done());
+        CS_CUDA(mark(1));
         CS_CUDA(launch_opf(dn, a, (const int*)ctx->isl.p, o, ctx->opt.opf_tol, ctx->opt.opf_max_it,
                            (double*)ctx->scratch.p, per_opf, std::min<int64_t>(g_opf, m), counters, s));
+        CS_CUDA(done());
+        CS_CUDA(mark(2));
         CS_CUDA(launch_dyn(dn, a, o, ctx->opt.damping_min, (double*)ctx->scratch.p, per_dyn,
                            std::min<int64_t>(g_dyn, m), counters + 1, s));
+        CS_CUDA(done());
         ctx->launches += 3 + (a.sev_n1 ? 1 : 0);
     }
     return CS_OK;
@@ -200,6 +231,7 @@ cs_status cs_destroy(cs_ctx* ctx) {
     cudaDeviceSynchronize();
     ctx->reqs.clear();
     ctx->nets.clear();
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     if (ctx->req_stream) cudaStreamDestroy(ctx->req_stream);
     delete ctx;
     return CS_OK;
@@ -208,6 +240,33 @@ cs_status cs_destroy(cs_ctx* ctx) {
 const char* cs_last_error(cs_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
 int64_t cs_last_launch_count(cs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+cs_status cs_set_timing(cs_ctx* ctx, int32_t enable) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->timing = enable != 0;
+    ctx->ev_used = 0;
+    for (int k = 0; k < 3; ++k) { ctx->kernel_ms[k] = 0.0; ctx->kernel_launches[k] = 0; }
+    return CS_OK;
+}
+
+cs_status cs_kernel_times(cs_ctx* ctx, double* ms, int64_t* launches) {
+    if (!ctx || !ms) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    for (size_t q = 0; q < ctx->ev_used; ++q) {
+        CS_CUDA(cudaEventSynchronize(ctx->ev[2 * q + 1]));
+        float t = 0.f;
+        CS_CUDA(cudaEventElapsedTime(&t, ctx->ev[2 * q], ctx->ev[2 * q + 1]));
+        ctx->kernel_ms[ctx->ev_kind[q]] += t;
+        ctx->kernel_launches[ctx->ev_kind[q]] += 1;
+    }
+    ctx->ev_used = 0;
+    for (int k = 0; k < 3; ++k) {
+        ms[k] = ctx->kernel_ms[k];
+        if (launches) launches[k] = ctx->kernel_launches[k];
+    }
+    return CS_OK;
+}
 
 cs_status cs_load_network(cs_ctx* ctx, const cs_network_desc* d, int32_t* net_id) {
     if (!ctx) return CS_E_ARG;
@@ -238,7 +297,7 @@ cs_status cs_load_network(cs_ctx* ctx, const cs_network_desc* d, int32_t* net_id
     CS_CUDA(cudaSetDevice(ctx->device));
     std::unique_ptr<Network> net(new Network());
     std::vector<int> f(d->f, d->f + nbr), t(d->t, d->t + nbr);
-    std::string msg = symbolic_analysis(nb, f, t, net->sym);
+    std::string msg = symbolic_analysis(nb, f, t, d->ref_bus, net->sym);
     if (!msg.empty()) return fail(ctx, CS_E_ARG, msg);
     const Symbolic& S = net->sym;
     const double B = d->base_mva;

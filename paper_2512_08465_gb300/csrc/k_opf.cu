@@ -44,6 +44,8 @@ constexpr int kRec = 46;     // doubles per branch record
 constexpr double kXi = 0.99995;
 constexpr double kSigma = 0.1;
 constexpr double kLimitTol = 1e-6;
+constexpr int kRefineSteps = 3;              // FP64 iterative refinement steps per Newton solve (at most)
+constexpr double kRefineStop = 0x1p-50;      // stop when the correction is below 2^-50 of the solution
 
 // record layout
 constexpr int R_DSF = 0, R_DST = 8, R_GF = 16, R_GT = 20, R_H = 24, R_LG = 34, R_NG = 38, R_SF = 42, R_ST = 44;
@@ -62,8 +64,8 @@ struct Lay {
     int Pg, Qg, gz, gmu, gdz, gdmu, MP, MQ, NP, NQ, LxP, LxQ, dPg, dQg;
     // branch
     int zf, zt, muf, mut, hf, ht, dzf, dzt, dmuf, dmut, rec;
-    // KKT
-    int Ub, Lb, Db, Di, x;
+    // KKT: assembled blocks (Kb, Kd) kept for refinement, factor (Ub, Lb, Db, Di), vectors
+    int Kb, Kd, Ub, Lb, Db, Di, x, bv, rv;
     int total;
 };
 
@@ -83,8 +85,9 @@ Lay make_layout(const DevNet& n) {
     L.dzf = take(nbr); L.dzt = take(nbr); L.dmuf = take(nbr); L.dmut = take(nbr);
     L.rec = take(kRec * nbr);
     o = (o + 15) & ~15;
+    L.Kb = take(16 * n.nL); L.Kd = take(16 * nb);
     L.Ub = take(16 * n.nL); L.Lb = take(16 * n.nL); L.Db = take(16 * nb); L.Di = take(16 * nb);
-    L.x = take(4 * nb);
+    L.x = take(4 * nb); L.bv = take(4 * nb); L.rv = take(4 * nb);
     L.total = (o + 31) & ~31;
     return L;
 }
@@ -231,6 +234,71 @@ __device__ void eval_branch(const DevNet& net, int b, double* W, const Lay& L, d
     rec[R_SF + 1] = Sf.im;
     rec[R_ST] = St.re;
     rec[R_ST + 1] = St.im;
+}
+
+// Solve (L D L^T) v = v in place for the 4-vector-per-bus array v (new order):
+// forward by elimination-tree levels, block diagonal, backward by levels.
+__device__ void ldl_solve(const DevNet& net, const double* W, const Lay& L, double* v) {
+    const int tid = threadIdx.x, nb = net.nb;
+    for (int lev = 0; lev < net.nlevels; ++lev) {
+        const int c0 = net.lev_ptr[lev], c1 = net.lev_ptr[lev + 1];
+        for (int w = tid; w < 4 * (c1 - c0); w += kThreads) {
+            const int j = net.lev_col[c0 + (w >> 2)], r = w & 3;
+            double acc = v[4 * j + r];
+            for (int e = net.Lrowptr[j]; e < net.Lrowptr[j + 1]; ++e) {
+                const double* Lq = W + L.Lb + 16 * net.Lrowblk[e] + 4 * r;
+                const double* y = v + 4 * net.Lrowcol[e];
+                acc -= Lq[0] * y[0] + Lq[1] * y[1] + Lq[2] * y[2] + Lq[3] * y[3];
+            }
+            v[4 * j + r] = acc;
+        }
+        __syncthreads();
+    }
+    for (int j = tid; j < nb; j += kThreads) {
+        const double* Di = W + L.Di + 16 * j;
+        double* y = v + 4 * j;
+        const double y0 = y[0], y1 = y[1], y2 = y[2], y3 = y[3];
+        for (int r = 0; r < 4; ++r)
+            y[r] = Di[4 * r] * y0 + Di[4 * r + 1] * y1 + Di[4 * r + 2] * y2 + Di[4 * r + 3] * y3;
+    }
+    __syncthreads();
+    for (int lev = net.nlevels - 1; lev >= 0; --lev) {
+        const int c0 = net.lev_ptr[lev], c1 = net.lev_ptr[lev + 1];
+        for (int w = tid; w < 4 * (c1 - c0); w += kThreads) {
+            const int j = net.lev_col[c0 + (w >> 2)], r = w & 3;
+            double acc = v[4 * j + r];
+            for (int e = net.Lcolptr[j]; e < net.Lcolptr[j + 1]; ++e) {
+                const double* Lq = W + L.Lb + 16 * e + r;
+                const double* xi = v + 4 * net.Lrow[e];
+                acc -= Lq[0] * xi[0] + Lq[4] * xi[1] + Lq[8] * xi[2] + Lq[12] * xi[3];
+            }
+            v[4 * j + r] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// r = b - K x with the assembled (unfactored) blocks, one thread per (bus, row).
+__device__ void kkt_residual(const DevNet& net, const double* W, const Lay& L, const double* x, double* r) {
+    const int tid = threadIdx.x, nb = net.nb;
+    for (int w = tid; w < 4 * nb; w += kThreads) {
+        const int i = w >> 2, rr = w & 3;
+        const double* Kd = W + L.Kd + 16 * i + 4 * rr;
+        const double* xi = x + 4 * i;
+        double acc = W[L.bv + w] - (Kd[0] * xi[0] + Kd[1] * xi[1] + Kd[2] * xi[2] + Kd[3] * xi[3]);
+        for (int e = net.Lrowptr[i]; e < net.Lrowptr[i + 1]; ++e) {        // blocks (i, k), k < i
+            const double* Kq = W + L.Kb + 16 * net.Lrowblk[e] + 4 * rr;
+            const double* xk = x + 4 * net.Lrowcol[e];
+            acc -= Kq[0] * xk[0] + Kq[1] * xk[1] + Kq[2] * xk[2] + Kq[3] * xk[3];
+        }
+        for (int e = net.Lcolptr[i]; e < net.Lcolptr[i + 1]; ++e) {        // blocks (j, i)^T, j > i
+            const double* Kq = W + L.Kb + 16 * e + rr;
+            const double* xj = x + 4 * net.Lrow[e];
+            acc -= Kq[0] * xj[0] + Kq[4] * xj[1] + Kq[8] * xj[2] + Kq[12] * xj[3];
+        }
+        r[w] = acc;
+    }
+    __syncthreads();
 }
 
 struct Scal {          // per-scenario scalars in shared memory
@@ -458,13 +526,15 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                         for (int q = 0; q < 4; ++q) { blk[q] = 0.0; blk[4 * q] = 0.0; }
                         blk[0] = 1.0;
                     }
-                    double* D = W + L.Db + 16 * j;
-                    for (int q = 0; q < 16; ++q) D[q] = blk[q];
-                    double* x = W + L.x + 4 * j;
-                    x[0] = (i == net.ref) ? 0.0 : -W[L.NVa + i];
-                    x[1] = -W[L.NVm + i];
-                    x[2] = -W[L.gP + i] - W[L.rP + i];
-                    x[3] = -W[L.gQ + i] - W[L.rQ + i];
+                    double* D = W + L.Kd + 16 * j;
+                    double* Dc = W + L.Db + 16 * j;
+                    for (int q = 0; q < 16; ++q) { D[q] = blk[q]; Dc[q] = blk[q]; }
+                    double bq[4];
+                    bq[0] = (i == net.ref) ? 0.0 : -W[L.NVa + i];
+                    bq[1] = -W[L.NVm + i];
+                    bq[2] = -W[L.gP + i] - W[L.rP + i];
+                    bq[3] = -W[L.gQ + i] - W[L.rQ + i];
+                    for (int q = 0; q < 4; ++q) { W[L.bv + 4 * j + q] = bq[q]; W[L.x + 4 * j + q] = bq[q]; }
                 } else {
                     const int q = tg - nb;
                     const int Rn = net.Lrow[q], Cn = net.Lcol[q];
@@ -490,7 +560,8 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                     if (Rb == net.ref) for (int c = 0; c < 4; ++c) blk[c] = 0.0;
                     if (Cb == net.ref) for (int r = 0; r < 4; ++r) blk[4 * r] = 0.0;
                     double* U = W + L.Ub + 16 * q;
-                    for (int c = 0; c < 16; ++c) U[c] = blk[c];
+                    double* Kq = W + L.Kb + 16 * q;
+                    for (int c = 0; c < 16; ++c) { U[c] = blk[c]; Kq[c] = blk[c]; }
                 }
             }
             __syncthreads();
@@ -527,42 +598,27 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                 __syncthreads();
             }
             if (sc.fail) break;
-            // ---------------- solve: L y = b, D w = y, L^T x = w ----------------
-            for (int lev = 0; lev < net.nlevels; ++lev) {
-                const int c0 = net.lev_ptr[lev], c1 = net.lev_ptr[lev + 1];
-                for (int w = tid; w < 4 * (c1 - c0); w += kThreads) {
-                    const int j = net.lev_col[c0 + (w >> 2)], r = w & 3;
-                    double acc = W[L.x + 4 * j + r];
-                    for (int e = net.Lrowptr[j]; e < net.Lrowptr[j + 1]; ++e) {
-                        const double* Lq = W + L.Lb + 16 * net.Lrowblk[e] + 4 * r;
-                        const double* y = W + L.x + 4 * net.Lrowcol[e];
-                        acc -= Lq[0] * y[0] + Lq[1] * y[1] + Lq[2] * y[2] + Lq[3] * y[3];
-                    }
-                    W[L.x + 4 * j + r] = acc;
+            // ---------------- solve, then FP64 iterative refinement against the assembled K ----------------
+            // The blocks are eliminated in a fixed order without pivoting between blocks;
+            // near convergence some pivot blocks become nearly singular (a load bus whose
+            // voltage sits at a bound has one free local variable for two balance rows),
+            // which leaves a low-rank error in the first solve that refinement removes.
+            ldl_solve(net, W, L, W + L.x);
+            for (int ref_step = 0; ref_step < kRefineSteps; ++ref_step) {
+                kkt_residual(net, W, L, W + L.x, W + L.rv);
+                ldl_solve(net, W, L, W + L.rv);
+                double dmax = 0.0, xmax = 0.0;
+                for (int w = tid; w < 4 * nb; w += kThreads) {
+                    const double d = W[L.rv + w];
+                    const double xn = W[L.x + w] + d;
+                    W[L.x + w] = xn;
+                    dmax = fmax(dmax, fabs(d));
+                    xmax = fmax(xmax, fabs(xn));
                 }
-                __syncthreads();
-            }
-            for (int j = tid; j < nb; j += kThreads) {
-                const double* Di = W + L.Di + 16 * j;
-                double* y = W + L.x + 4 * j;
-                const double y0 = y[0], y1 = y[1], y2 = y[2], y3 = y[3];
-                for (int r = 0; r < 4; ++r)
-                    y[r] = Di[4 * r] * y0 + Di[4 * r + 1] * y1 + Di[4 * r + 2] * y2 + Di[4 * r + 3] * y3;
-            }
-            __syncthreads();
-            for (int lev = net.nlevels - 1; lev >= 0; --lev) {
-                const int c0 = net.lev_ptr[lev], c1 = net.lev_ptr[lev + 1];
-                for (int w = tid; w < 4 * (c1 - c0); w += kThreads) {
-                    const int j = net.lev_col[c0 + (w >> 2)], r = w & 3;
-                    double acc = W[L.x + 4 * j + r];
-                    for (int e = net.Lcolptr[j]; e < net.Lcolptr[j + 1]; ++e) {
-                        const double* Lq = W + L.Lb + 16 * e + r;
-                        const double* xi = W + L.x + 4 * net.Lrow[e];
-                        acc -= Lq[0] * xi[0] + Lq[4] * xi[1] + Lq[8] * xi[2] + Lq[12] * xi[3];
-                    }
-                    W[L.x + 4 * j + r] = acc;
-                }
-                __syncthreads();
+                double v2[2] = {dmax, xmax};
+                const int ops2[2] = {0, 0};
+                block_reduce<2>(rb, v2, ops2, sc.red);
+                if (!(sc.red[0] > kRefineStop * sc.red[1])) break;     // correction negligible (or NaN: caught below)
             }
             // ---------------- recover the eliminated steps, dz, dmu, ratios ----------------
             double rp = INFINITY, rd = INFINITY, bad = 0.0;

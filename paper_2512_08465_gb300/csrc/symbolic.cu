@@ -6,7 +6,11 @@
 // outaged branch only zeroes values).  One ordering and one fill pattern
 // therefore serve all contingencies:
 //  * ordering: exact minimum degree on the elimination graph (ties broken by
-//    the smaller bus index), computed on explicit adjacency sets;
+//    the smaller bus index), computed on explicit adjacency sets, with the
+//    reference bus eliminated last.  Its reduced-KKT block has the angle row
+//    replaced by the identity, so without a generator at that bus the block
+//    alone is singular; as the last pivot it is the Schur complement of the
+//    whole system, which is nonsingular whenever the system is;
 //  * pattern: the neighbours of each bus when it is eliminated are the rows of
 //    its column of L;
 //  * elimination tree (parent = first row of the column) and its heights; the
@@ -20,8 +24,10 @@
 #include <map>
 #include <set>
 
-std::string symbolic_analysis(int n, const std::vector<int>& f, const std::vector<int>& t, Symbolic& S) {
+std::string symbolic_analysis(int n, const std::vector<int>& f, const std::vector<int>& t, int last,
+                              Symbolic& S) {
     if (n <= 0) return "network has no bus";
+    if (last >= n) return "reference bus out of range";
     std::vector<std::set<int>> adj(n);
     for (size_t k = 0; k < f.size(); ++k) {
         const int a = f[k], b = t[k];
@@ -39,7 +45,7 @@ std::string symbolic_analysis(int n, const std::vector<int>& f, const std::vecto
         int best = -1;
         size_t bdeg = 0;
         for (int v = 0; v < n; ++v) {
-            if (!alive[v]) continue;
+            if (!alive[v] || (v == last && step < n - 1)) continue;
             if (best < 0 || adj[v].size() < bdeg) {
                 best = v;
                 bdeg = adj[v].size();

@@ -18,7 +18,9 @@ struct Symbolic {
 };
 
 // Minimum-degree elimination of the graph (n nodes, undirected edges f[k]-t[k],
-// self loops and parallel edges allowed in the input), symbolic block
-// factorisation, elimination-tree levels and left-looking update lists.
-// Returns an empty string on success, an error message otherwise.
-std::string symbolic_analysis(int n, const std::vector<int>& f, const std::vector<int>& t, Symbolic& S);
+// parallel edges allowed, self loops rejected) with node `last` (the reference
+// bus, -1 for none) held back to the end, symbolic block factorisation,
+// elimination-tree levels and left-looking update lists.  Returns an empty
+// string on success, an error message otherwise.
+std::string symbolic_analysis(int n, const std::vector<int>& f, const std::vector<int>& t, int last,
+                              Symbolic& S);

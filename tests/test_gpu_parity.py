@@ -1,0 +1,297 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (from the method's accuracy targets): severity classes, island
+counts and the Risk Index are compared exactly; bus voltage magnitudes and
+angles within 1e-8 (p.u., rad); OPF cost within 1e-6 relative; max Re(lambda)
+and the minimum damping ratio within 1e-6.  A class may differ only inside the
+guard band where floating-point rounding legitimately decides it: an oracle
+OPF that needed >= 48 of its 50 iterations, or a decisive eigen statistic
+within 1e-6 of its threshold; such cases are counted and must stay rare.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2512_08465_gb300 import cs, synth  # noqa: E402
+from oracle import pipeline, risk  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEV = "cuda:0"
+TOL_V, TOL_COST, TOL_EIG = 1e-8, 1e-6, 1e-6
+
+
+def _gold(name):
+    return json.load(open(os.path.join(HERE, "golden", name)))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = cs.Context()
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def net118(ctx):
+    net = synth.case118()
+    return net, ctx.load_network(net)
+
+
+def _run(ctx, nid, level, ei, ej, n_bus=0):
+    ei = torch.as_tensor(np.asarray(ei, np.int32), device=DEV)
+    ej = torch.as_tensor(np.asarray(ej, np.int32), device=DEV)
+    out = ctx.alloc_results(ei.numel(), DEV, n_bus)
+    ctx.evaluate_device(nid, level, ei, ej, out)
+    ctx.sync()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _guard(ref, dmin=pipeline.DAMPING_MIN):
+    if ref.get("opf_iters", 0) >= 48:
+        return True
+    mr, mz = ref.get("max_re"), ref.get("min_zeta")
+    if mr is not None and np.isfinite(mr) and abs(mr) < TOL_EIG:
+        return True
+    if mz is not None and np.isfinite(mz) and abs(mz - dmin) < TOL_EIG:
+        return True
+    return False
+
+
+def _compare(got, refs, nb=None, max_guard=0):
+    guard = 0
+    for q, r in enumerate(refs):
+        k = int(got["klass"][q])
+        if k != r["klass"]:
+            assert _guard(r), f"class mismatch at {q}: gpu {k} oracle {r['klass']} ({r['level']},{r['i']},{r['j']})"
+            guard += 1
+            continue
+        assert int(got["n_islands"][q]) == r["n_islands"]
+        assert int(got["severe"][q]) == int(r["severe"])
+        if r["klass"] in (0, 3, 4, 5):
+            c = r["cost"]
+            assert abs(got["cost"][q] - c) <= TOL_COST * abs(c), (q, got["cost"][q], c)
+        if r["klass"] in (0, 4, 5):
+            assert abs(got["max_re"][q] - r["max_re"]) <= TOL_EIG, (q, got["max_re"][q], r["max_re"])
+            assert abs(got["min_zeta"][q] - r["min_zeta"]) <= TOL_EIG, (q, got["min_zeta"][q], r["min_zeta"])
+        if nb and r.get("Vm") is not None and r["klass"] in (0, 3, 4, 5):
+            vm = got["Vm"][q * nb:(q + 1) * nb]
+            va = got["Va"][q * nb:(q + 1) * nb]
+            assert np.abs(vm - np.asarray(r["Vm"])).max() <= TOL_V
+            assert np.abs(va - np.asarray(r["Va"])).max() <= TOL_V
+    assert guard <= max_guard, f"{guard} guard-band class differences"
+    return guard
+
+
+# ------------------------------------------------------------ building blocks --
+def test_enumerate_pairs_bitexact():
+    for E in (2, 3, 25, 240):
+        n = E * (E - 1) // 2
+        ei = torch.empty(n, dtype=torch.int32, device=DEV)
+        ej = torch.empty(n, dtype=torch.int32, device=DEV)
+        cs.enumerate_pairs_device(E, 0, n, ei, ej)
+        torch.cuda.synchronize()
+        ii, jj = synth.all_pairs(E)
+        np.testing.assert_array_equal(ei.cpu().numpy(), ii)
+        np.testing.assert_array_equal(ej.cpu().numpy(), jj)
+    # a ragged window in the middle
+    E, first, cnt = 240, 1000, 777
+    ei = torch.empty(cnt, dtype=torch.int32, device=DEV)
+    ej = torch.empty(cnt, dtype=torch.int32, device=DEV)
+    cs.enumerate_pairs_device(E, first, cnt, ei, ej)
+    ii, jj = synth.all_pairs(E)
+    np.testing.assert_array_equal(ei.cpu().numpy(), ii[first:first + cnt])
+    np.testing.assert_array_equal(ej.cpu().numpy(), jj[first:first + cnt])
+
+
+def _pair_table(S2):
+    E = S2.shape[0]
+    ii, jj = np.triu_indices(E, 1)
+    return S2[ii, jj].astype(np.uint8)
+
+
+@pytest.mark.parametrize("E,seed", [(1, 0), (2, 1), (33, 2), (240, 3), (700, 4)])
+def test_risk_reduce_bitexact_random(E, seed):
+    rng = np.random.default_rng(seed)
+    lam = rng.uniform(0.01, 1.0, E)
+    lam[::7] = 2.0 ** rng.integers(-30, 10, size=lam[::7].size)       # range edges
+    S1 = rng.integers(0, 2, E).astype(np.uint8)
+    U = np.triu(rng.integers(0, 2, (E, E)), 1)
+    S2 = U + U.T
+    for mode in (cs.RISK_EQ3, cs.RISK_ORDERED):
+        R = torch.empty(E, dtype=torch.float64, device=DEV)
+        pairs = _pair_table(S2) if E > 1 else np.zeros(1, np.uint8)
+        cs.risk_reduce_device(E, torch.from_numpy(S1).to(DEV), torch.from_numpy(pairs).to(DEV),
+                              torch.from_numpy(lam).to(DEV), R, mode)
+        torch.cuda.synchronize()
+        ref = risk.risk_index(lam, S1, S2, risk.ORDERED if mode == cs.RISK_ORDERED else risk.EQ3)
+        np.testing.assert_array_equal(R.cpu().numpy(), ref)
+
+
+def test_risk_reduce_printed_values():
+    """Section V worked values (Table I rates, every scenario severe): 1.472 / 0.590."""
+    lam = np.array([0.05] * 175 + [0.02] * 11 + [0.10] * 53)
+    E = lam.size
+    S1 = np.ones(E, np.uint8)
+    pairs = np.ones(E * (E - 1) // 2, np.uint8)
+    R = torch.empty(E, dtype=torch.float64, device=DEV)
+    cs.risk_reduce_device(E, torch.from_numpy(S1).to(DEV), torch.from_numpy(pairs).to(DEV),
+                          torch.from_numpy(lam).to(DEV), R, cs.RISK_ORDERED)
+    R = R.cpu().numpy()
+    assert abs(R[0] - 1.472) < 1e-12 and abs(R[175] - 0.590) < 1e-12
+    np.testing.assert_array_equal(R, risk.risk_index(lam, S1, np.ones((E, E)), risk.ORDERED))
+
+
+def test_islanding_bitexact_all_n1_and_pairs(ctx, net118):
+    net, nid = net118
+    from oracle import grid
+    E = net.n_elem
+    ii, jj = synth.all_pairs(E)
+    ei = np.concatenate([np.arange(E), ii[::7]]).astype(np.int32)
+    ej = np.concatenate([-np.ones(E, np.int32), jj[::7]]).astype(np.int32)
+    got = _run(ctx, nid, 0, ei, ej)
+    for q in range(len(ei)):
+        sc = grid.make_scenario(net, 0, int(ei[q]), int(ej[q]))
+        k = grid.count_islands(net.n_bus, net.f[sc.br], net.t[sc.br])
+        assert int(got["n_islands"][q]) == k
+        if k > 1:
+            assert int(got["klass"][q]) == 1
+
+
+# ------------------------------------------------------------ whole scenarios --
+def test_small_network_every_scenario_vs_oracle(ctx):
+    """14-bus network: base, every N-1 and every N-2 of its 25 elements, live oracle."""
+    net = synth.make_network(14, 20, 5, 11, 1, seed=3, levels=(0.5,))
+    nid = ctx.load_network(net)
+    E = net.n_elem
+    ii, jj = synth.all_pairs(E)
+    ei = np.concatenate([[-1], np.arange(E), ii]).astype(np.int32)
+    ej = np.concatenate([[-1], -np.ones(E, np.int32), jj]).astype(np.int32)
+    got = _run(ctx, nid, 0, ei, ej, n_bus=net.n_bus)
+    refs = pipeline.evaluate_many(net, [(0, int(a), int(b)) for a, b in zip(ei, ej)])
+    _compare(got, refs, nb=net.n_bus, max_guard=2)
+    ctx.unload_network(nid)
+
+
+def test_case118_n1_vs_golden(ctx, net118):
+    """The plain small configuration: all 186 branch N-1 scenarios at 70 % load."""
+    net, nid = net118
+    g = _gold("case118_n1.json")
+    refs = g["scenarios"]
+    got = _run(ctx, nid, 0, [r["i"] for r in refs], [r["j"] for r in refs], n_bus=net.n_bus)
+    _compare(got, refs, nb=net.n_bus, max_guard=1)
+
+
+def test_case118_pairs_vs_golden(ctx, net118):
+    net, nid = net118
+    refs = _gold("case118_pairs.json")["scenarios"]
+    for lv in (0, 1):
+        sub = [r for r in refs if r["level"] == lv]
+        got = _run(ctx, nid, lv, [r["i"] for r in sub], [r["j"] for r in sub])
+        _compare(got, sub, max_guard=2)
+
+
+def test_full_size_batch_sampled(ctx, net118):
+    """All 28,680 pairs of a level in one call (the benchmark's launch
+    configuration), checked at the golden sample and by invariants."""
+    net, nid = net118
+    E = net.n_elem
+    n = E * (E - 1) // 2
+    ei = torch.empty(n, dtype=torch.int32, device=DEV)
+    ej = torch.empty(n, dtype=torch.int32, device=DEV)
+    cs.enumerate_pairs_device(E, 0, n, ei, ej)
+    out = ctx.alloc_results(n, DEV)
+    ctx.evaluate_device(nid, 1, ei, ej, out)
+    ctx.sync()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    refs = [r for r in _gold("case118_pairs.json")["scenarios"] if r["level"] == 1]
+    ii, jj = synth.all_pairs(E)
+    index = {(int(a), int(b)): q for q, (a, b) in enumerate(zip(ii, jj))}
+    pos = [index[(r["i"], r["j"])] for r in refs]
+    sub = {k: v[pos] for k, v in got.items()}
+    _compare(sub, refs, max_guard=2)
+    k = got["klass"]
+    assert np.all(k <= 6)
+    assert np.all(got["severe"] == (k != 0))
+    assert np.all((k == 1) == (got["n_islands"] > 1))
+    assert np.all(np.isnan(got["cost"][k == 1]))
+    assert np.all(np.isfinite(got["cost"][(k == 0) | (k == 4) | (k == 5)]))
+
+
+def test_risk_index_from_gpu_severities_matches_oracle(ctx, net118):
+    """cs_risk_index over the context's severity table equals the exact oracle
+    reduction of the same severities (pairs never evaluated count as 0)."""
+    net, nid = net118
+    E = net.n_elem
+    lam = synth.failure_rates(E, 7)
+    nctx = cs.Context()
+    nid2 = nctx.load_network(net)
+    ii, jj = synth.all_pairs(E)
+    sel = np.arange(0, ii.size, 5)
+    ei = np.concatenate([np.arange(E), ii[sel]]).astype(np.int32)
+    ej = np.concatenate([-np.ones(E, np.int32), jj[sel]]).astype(np.int32)
+    got = _run(nctx, nid2, 0, ei, ej)
+    S1 = got["severe"][:E]
+    S2 = np.zeros((E, E), np.uint8)
+    S2[ii[sel], jj[sel]] = got["severe"][E:]
+    S2 = S2 + S2.T
+    for mode in (cs.RISK_EQ3, cs.RISK_ORDERED):
+        R, missing = nctx.risk_index(nid2, 0, lam, mode)
+        assert missing == ii.size - sel.size
+        np.testing.assert_array_equal(R, risk.risk_index(lam, S1, S2, risk.ORDERED if mode else risk.EQ3))
+    nctx.close()
+
+
+# ------------------------------------------------------------ properties / edges --
+def test_deterministic_and_alone_equals_mixed(ctx, net118):
+    net, nid = net118
+    E = net.n_elem
+    ii, jj = synth.all_pairs(E)
+    rng = np.random.default_rng(5)
+    sel = rng.choice(ii.size, 400, replace=False)
+    a = _run(ctx, nid, 0, ii[sel], jj[sel], n_bus=net.n_bus)
+    b = _run(ctx, nid, 0, ii[sel], jj[sel], n_bus=net.n_bus)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
+    few = sel[:17]
+    c = _run(ctx, nid, 0, ii[few], jj[few], n_bus=net.n_bus)
+    for k in ("klass", "cost", "max_re", "min_zeta", "opf_iters"):
+        np.testing.assert_array_equal(c[k], a[k][:17])
+
+
+def test_host_request_path_equals_device_path(ctx, net118):
+    net, nid = net118
+    ei = np.array([-1, 0, 5, 17, 100, 200, 3], np.int32)
+    ej = np.array([-1, -1, 9, -1, 230, 201, 239], np.int32)
+    dev = _run(ctx, nid, 1, ei, ej)
+    host = ctx.evaluate(nid, 1, ei, ej)
+    for k in ("klass", "severe", "n_islands", "opf_iters", "cost", "max_re", "min_zeta"):
+        np.testing.assert_array_equal(dev[k], host[k])
+
+
+def test_base_case_secure_and_edges(ctx, net118):
+    net, nid = net118
+    for lv in (0, 1):
+        b = ctx.base_result(nid, lv)
+        assert int(b["klass"]) == 0 and int(b["n_islands"]) == 1
+    # empty batch
+    _run(ctx, nid, 0, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    # invalid ids are rejected on the host path and flagged on the device path
+    with pytest.raises(cs.CSError):
+        ctx.evaluate(nid, 0, np.array([net.n_elem], np.int32), np.array([-1], np.int32))
+    with pytest.raises(cs.CSError):
+        _run(ctx, nid, 0, np.array([0, net.n_elem + 5], np.int32), np.array([-1, -1], np.int32))
+    with pytest.raises(cs.CSError):
+        ctx.risk_index(nid, 0, np.full(net.n_elem, 1e-12))
+    with pytest.raises(cs.CSError):
+        ctx.base_result(nid + 99, 0)
+    # the same element twice is the N-1 scenario of that element
+    a = _run(ctx, nid, 0, [7, 7], [7, -1])
+    assert a["klass"][0] == a["klass"][1] and a["cost"][0] == a["cost"][1]
