@@ -72,6 +72,7 @@ struct cs_ctx {
     int next_net = 1;
     uint64_t next_req = 1;
     std::map<uint64_t, std::unique_ptr<Request>> reqs;
+    std::vector<std::unique_ptr<Request>> pool;     // finished requests kept for buffer reuse
     cudaStream_t req_stream = nullptr;
     // workspace
     DevBuf scratch, isl, opfx, opfst, counters, err_word;
@@ -230,6 +231,7 @@ cs_status cs_destroy(cs_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     ctx->reqs.clear();
+    ctx->pool.clear();
     ctx->nets.clear();
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     if (ctx->req_stream) cudaStreamDestroy(ctx->req_stream);
@@ -559,16 +561,27 @@ cs_status cs_submit_contingencies(cs_ctx* ctx, int32_t net_id, int32_t level, co
             return fail(ctx, CS_E_ARG, "element id out of range at record " + std::to_string(q));
     }
     CS_CUDA(cudaSetDevice(ctx->device));
-    std::unique_ptr<Request> r(new Request());
+    const size_t ob = result_bytes(std::max<int64_t>(n, 1), net->dev.nb, false);
+    const size_t ib = sizeof(int) * 2 * std::max<int64_t>(n, 1);
+    std::unique_ptr<Request> r;
+    for (size_t q = 0; q < ctx->pool.size(); ++q) {          // reuse buffers of a finished request
+        if (ctx->pool[q]->h_out_bytes >= ob && ctx->pool[q]->d_in.bytes >= ib) {
+            r = std::move(ctx->pool[q]);
+            ctx->pool.erase(ctx->pool.begin() + q);
+            break;
+        }
+    }
+    if (!r) {
+        r.reset(new Request());
+        CS_CUDA(r->d_in.ensure(ib));
+        CS_CUDA(r->d_out.ensure(ob));
+        CS_CUDA(cudaMallocHost(&r->h_out, ob));
+        r->h_out_bytes = ob;
+        CS_CUDA(cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming));
+    }
     r->id = ctx->next_req++;
     r->n = n;
     r->nb = net->dev.nb;
-    const size_t ob = result_bytes(std::max<int64_t>(n, 1), net->dev.nb, false);
-    CS_CUDA(r->d_in.ensure(sizeof(int) * 2 * std::max<int64_t>(n, 1)));
-    CS_CUDA(r->d_out.ensure(ob));
-    CS_CUDA(cudaMallocHost(&r->h_out, ob));
-    r->h_out_bytes = ob;
-    CS_CUDA(cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming));
     cudaStream_t s = ctx->req_stream;
     int* din = (int*)r->d_in.p;
     if (n > 0) {
@@ -619,7 +632,9 @@ cs_status cs_poll(cs_ctx* ctx, uint64_t request_id, int32_t timeout_us, const cs
         if (out->max_re) std::memcpy(out->max_re, h.max_re, 8 * n);
         if (out->min_zeta) std::memcpy(out->min_zeta, h.min_zeta, 8 * n);
     }
-    ctx->reqs.erase(request_id);
+    auto it2 = ctx->reqs.find(request_id);
+    if (ctx->pool.size() < 64) ctx->pool.push_back(std::move(it2->second));
+    ctx->reqs.erase(it2);
     return CS_OK;
 }
 

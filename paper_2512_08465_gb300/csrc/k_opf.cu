@@ -116,33 +116,47 @@ __device__ void block_reduce(RedBuf& rb, double (&val)[K], const int (&ops)[K], 
     __syncthreads();
 }
 
-// Gauss-Jordan inverse of a 4x4 block with partial pivoting; returns false if singular.
+// Inverse of a 4x4 pivot block: LU factorisation with partial pivoting, then
+// forward/back substitution for each column of the identity.  (Near the end of
+// the interior-point iteration some pivot blocks are nearly singular; the
+// LU-based inverse keeps the error low-rank, which the iterative refinement
+// removes, where a Gauss-Jordan inverse did not.)  Returns false if a pivot
+// is exactly zero or not finite.
 __device__ bool inv4(const double* A, double* Ainv) {
-    double a[4][8];
+    double a[4][4];
+    int piv[4] = {0, 1, 2, 3};
     for (int r = 0; r < 4; ++r)
-        for (int c = 0; c < 4; ++c) {
-            a[r][c] = A[4 * r + c];
-            a[r][4 + c] = (r == c) ? 1.0 : 0.0;
-        }
+        for (int c = 0; c < 4; ++c) a[r][c] = A[4 * r + c];
     for (int c = 0; c < 4; ++c) {
         int p = c;
         double best = fabs(a[c][c]);
         for (int r = c + 1; r < 4; ++r)
             if (fabs(a[r][c]) > best) { best = fabs(a[r][c]); p = r; }
         if (!(best > 0.0) || !isfinite(best)) return false;
-        if (p != c)
-            for (int q = 0; q < 8; ++q) { double t = a[c][q]; a[c][q] = a[p][q]; a[p][q] = t; }
-        const double piv = 1.0 / a[c][c];
-        for (int q = 0; q < 8; ++q) a[c][q] *= piv;
-        for (int r = 0; r < 4; ++r) {
-            if (r == c) continue;
+        if (p != c) {
+            for (int q = 0; q < 4; ++q) { double t = a[c][q]; a[c][q] = a[p][q]; a[p][q] = t; }
+            int t = piv[c]; piv[c] = piv[p]; piv[p] = t;
+        }
+        for (int r = c + 1; r < 4; ++r) {
+            a[r][c] /= a[c][c];
             const double m = a[r][c];
-            if (m != 0.0)
-                for (int q = 0; q < 8; ++q) a[r][q] -= m * a[c][q];
+            for (int q = c + 1; q < 4; ++q) a[r][q] -= m * a[c][q];
         }
     }
-    for (int r = 0; r < 4; ++r)
-        for (int c = 0; c < 4; ++c) Ainv[4 * r + c] = a[r][4 + c];
+    for (int j = 0; j < 4; ++j) {
+        double y[4];
+        for (int i = 0; i < 4; ++i) {
+            double v = (piv[i] == j) ? 1.0 : 0.0;
+            for (int q = 0; q < i; ++q) v -= a[i][q] * y[q];
+            y[i] = v;
+        }
+        for (int i = 3; i >= 0; --i) {
+            double v = y[i];
+            for (int q = i + 1; q < 4; ++q) v -= a[i][q] * y[q];
+            y[i] = v / a[i][i];
+        }
+        for (int i = 0; i < 4; ++i) Ainv[4 * i + j] = y[i];
+    }
     return true;
 }
 
