@@ -116,8 +116,9 @@ __device__ void block_reduce(RedBuf& rb, double (&val)[K], const int (&ops)[K], 
     __syncthreads();
 }
 
-// Inverse of a 4x4 pivot block: LU factorisation with partial pivoting, then
-// forward/back substitution for each column of the identity.  (Near the end of
+// Inverse of the symmetric part of a 4x4 pivot block: LU factorisation with
+// partial pivoting, forward/back substitution for each column of the identity,
+// then symmetrisation of the result.  (Near the end of
 // the interior-point iteration some pivot blocks are nearly singular; the
 // LU-based inverse keeps the error low-rank, which the iterative refinement
 // removes, where a Gauss-Jordan inverse did not.)  Returns false if a pivot
@@ -125,8 +126,8 @@ __device__ void block_reduce(RedBuf& rb, double (&val)[K], const int (&ops)[K], 
 __device__ bool inv4(const double* A, double* Ainv) {
     double a[4][4];
     int piv[4] = {0, 1, 2, 3};
-    for (int r = 0; r < 4; ++r)
-        for (int c = 0; c < 4; ++c) a[r][c] = A[4 * r + c];
+    for (int r = 0; r < 4; ++r)                  // symmetric part of the updated pivot
+        for (int c = 0; c < 4; ++c) a[r][c] = 0.5 * (A[4 * r + c] + A[4 * c + r]);
     for (int c = 0; c < 4; ++c) {
         int p = c;
         double best = fabs(a[c][c]);
@@ -157,6 +158,16 @@ __device__ bool inv4(const double* A, double* Ainv) {
         }
         for (int i = 0; i < 4; ++i) Ainv[4 * i + j] = y[i];
     }
+    // Symmetrise the inverse.  Only the lower blocks are stored and updated with
+    // L(i,k) U(j,k)^T, which assumes a symmetric pivot inverse; an LU-based inverse of
+    // a nearly singular symmetric block is far from symmetric in rounding, and the
+    // factorisation would then not be a consistent L D L^T (refinement stalls).
+    for (int r = 0; r < 4; ++r)
+        for (int c = r + 1; c < 4; ++c) {
+            const double m = 0.5 * (Ainv[4 * r + c] + Ainv[4 * c + r]);
+            Ainv[4 * r + c] = m;
+            Ainv[4 * c + r] = m;
+        }
     return true;
 }
 
