@@ -182,6 +182,11 @@ cs_status cs_risk_reduce_device(int32_t n_elem, const uint8_t* S1, const uint8_t
 cs_status cs_enumerate_pairs_device(int32_t n_elem, int64_t first, int64_t count,
                                     int32_t* elem_i, int32_t* elem_j, void* stream);
 
+/* Measured ALU peaks of `device` for roofline reporting: independent fused
+ * multiply-add chains in FP64 and FP32 timed with CUDA events, in TFLOP/s
+ * (2 flops per FMA).  Host outputs.  Runs ~10 ms of GPU work. */
+cs_status cs_alu_peak(int32_t device, double* fp64_tflops, double* fp32_tflops);
+
 /* Message of the last failing call on ctx (never NULL; "" if none). */
 const char* cs_last_error(cs_ctx* ctx);
 

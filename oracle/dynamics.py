@@ -27,13 +27,23 @@ Per in-service generator (machine base S_m = Pmax, converted to system base):
                  e'q = v_q + x' i_d, e'd = v_d - x' i_q, Efd = e'q + (x_d - x') i_d,
                  V_ref = |V| + Efd/K_A, Pm = Pg, omega = 1.
 
+Angle reference.  With absolute rotor angles and constant-impedance loads a
+common rotation of every angle is an equilibrium direction (A v0 = 0 for
+v0 = delta-all-ones), so A has one exact zero eigenvalue that carries no
+stability information, and the slow common-frequency mode is nearly parallel
+to it (eigenvalue condition number ~ w_s / sigma ~ 4e3).  The paper is silent;
+the reading used refers every angle to the first in-service machine r:
+delta'_k = delta_k - delta_r (k != r) with d delta'_k/dt = w_s (omega_k - omega_r),
+and delta_r is dropped.  The reduced matrix A' (5m - 1 states) has exactly the
+eigenvalues of A less one zero, and its decisive slow mode is well conditioned.
+
 A = df/dx is obtained by forward-mode automatic differentiation of the state
 equations above (a value plus a tangent for every state), so the oracle never
 writes a derivative by hand; the CUDA path uses hand-derived derivatives
-instead.  Pinned in ``tests/test_oracle_dynamics.py``: A against central
+instead.  Pinned in ``tests/test_oracle_dynamics.py``: A and A' against central
 differences with Richardson extrapolation, f(x0) = 0 at the equilibrium,
-A v0 = 0 for the common-rotation vector, Y_red against the definition on a
-two-bus case, and the single-machine infinite-bus swing mode closed form.
+A v0 = 0 for the common-rotation vector, eig(A') = eig(A) less one zero, and
+Y_red against a full nodal solve of the augmented network.
 """
 from __future__ import annotations
 
@@ -207,5 +217,24 @@ class Model:
         return self.f(Dual(xv, np.zeros((xv.size, 1)))).v
 
     def state_matrix(self):
+        """A = df/dx over the absolute states (5m)."""
         n = 5 * self.m
         return self.f(Dual(self.x0, np.eye(n))).d
+
+    def reduced_state_matrix(self):
+        """A' over the states with angles referred to machine 0 (5m - 1):
+        reduced index 5k + s - 1 for every state but delta_0."""
+        m = self.m
+        nf, nr = 5 * m, 5 * m - 1
+        val = self.x0.copy()
+        tan = np.zeros((nf, nr))
+        for i in range(1, nf):
+            tan[i, i - 1] = 1.0
+        for k in range(1, m):
+            tan[5 * k, :] = 0.0
+            tan[5 * k, 5 * k - 1] = 1.0     # delta_k = delta_0 (constant) + delta'_k
+        f = self.f(Dual(val, tan)).d
+        out = f[1:].copy()                  # drop the delta_0 row
+        for k in range(1, m):
+            out[5 * k - 1] = f[5 * k] - f[0]   # d delta'_k / dt = f_delta_k - f_delta_0
+        return out

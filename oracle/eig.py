@@ -7,11 +7,9 @@ non-negative real part.  The arithmetic is in ``eig.c`` (balancing, Householder
 Hessenberg, Francis double-shift QR); this module loads it (compiling it with
 gcc on first use) and computes the decision statistics.
 
-Structural zero mode.  The generator rotor angles are absolute states and the
-loads are constant impedances, so a common rotation of every angle is an
-equilibrium direction: A v0 = 0 for v0 = (delta = 1, other states 0), and A has
-one exact zero eigenvalue that carries no stability information (the paper is
-silent on it).  The statistics drop the single eigenvalue of smallest modulus.
+The state matrix handed in is the one with rotor angles referred to one machine
+(see ``oracle/dynamics``), which has no structural zero mode, so the statistics
+run over every eigenvalue.
 """
 from __future__ import annotations
 
@@ -72,15 +70,11 @@ def hessenberg(A, balance: bool = True):
 
 
 def stability_stats(lam):
-    """(max real part, minimum damping ratio) over the eigenvalues with the one of
-    smallest modulus (the structural zero mode) removed.  Damping ratio of an
-    eigenvalue s is -Re(s)/|s|."""
+    """(max real part, minimum damping ratio) over all eigenvalues; the damping
+    ratio of s is -Re(s)/|s| (1 for s = 0)."""
     lam = np.asarray(lam)
-    if lam.size <= 1:
+    if lam.size == 0:
         return -np.inf, np.inf
-    k = int(np.argmin(np.abs(lam)))
-    rest = np.delete(lam, k)
-    max_re = float(np.max(rest.real))
-    mag = np.abs(rest)
-    zeta = np.where(mag > 0, -rest.real / np.where(mag > 0, mag, 1.0), 1.0)
-    return max_re, float(np.min(zeta))
+    mag = np.abs(lam)
+    zeta = np.where(mag > 0, -lam.real / np.where(mag > 0, mag, 1.0), 1.0)
+    return float(np.max(lam.real)), float(np.min(zeta))

@@ -10,7 +10,7 @@ then the eigenvalue screen of the linearised model.  The class records the
 first criterion that failed; S_c = 1 for every class but SECURE.
 
 Classes: SECURE 0, ISLANDED 1, OPF_NONCONV 2, LIMIT 3, SS_UNSTABLE 4
-(max Re >= 0 after dropping the structural zero mode), SS_POORLY_DAMPED 5
+(max Re >= 0 of the angle-referenced state matrix), SS_POORLY_DAMPED 5
 (minimum damping ratio below ``damping_min``; 0 gives the paper's literal rule,
 the study configuration uses 0.05), EIG_FAIL 6 (QR did not converge).
 """
@@ -49,7 +49,7 @@ def evaluate(net, level: int, i: int = -1, j: int = -1, damping_min: float = DAM
         out["severe"] = 1
         return out
     model = dynamics.Model(net, sc, r["Va"], r["Vm"], r["Pg"], r["Qg"])
-    A = model.state_matrix()
+    A = model.reduced_state_matrix()
     lam, ok, sweeps = eig.eigvals(A)
     out["eig_sweeps"] = sweeps
     if keep_state:

@@ -28,7 +28,7 @@ RISK_EQ3, RISK_ORDERED = 0, 1
 EXPORTS = ("cs_default_options", "cs_create", "cs_destroy", "cs_load_network", "cs_unload_network",
            "cs_base_result", "cs_evaluate_device", "cs_sync", "cs_submit_contingencies", "cs_poll",
            "cs_risk_index", "cs_risk_reduce_device", "cs_enumerate_pairs_device", "cs_last_error",
-           "cs_last_launch_count", "cs_set_timing", "cs_kernel_times")
+           "cs_last_launch_count", "cs_set_timing", "cs_kernel_times", "cs_alu_peak")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -99,6 +99,7 @@ def load_library(build_if_missing: bool = True):
         "cs_last_launch_count": (i64, [P]),
         "cs_set_timing": (i32, [P, i32]),
         "cs_kernel_times": (i32, [P, P, P]),
+        "cs_alu_peak": (i32, [i32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -293,6 +294,15 @@ def risk_reduce_device(n_elem: int, S1, S2, lam, R, mode: int = RISK_ORDERED, st
                                               _stream_handle(stream))
     if st != CS_OK:
         raise CSError(st, "cs_risk_reduce_device")
+
+
+def alu_peak(device: int = 0):
+    """Measured (fp64, fp32) FMA-pipe peaks in TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    st = load_library().cs_alu_peak(device, ctypes.byref(a), ctypes.byref(b))
+    if st != CS_OK:
+        raise CSError(st, "cs_alu_peak")
+    return a.value, b.value
 
 
 def enumerate_pairs_device(n_elem: int, first: int, count: int, ei, ej, stream=None):

@@ -28,8 +28,13 @@
 //     double-shift QR (eigenvalues only), with the same steps and thresholds
 //     as the textbook algorithm; A lives in the CTA's global scratch (the
 //     resident CTAs' matrices together fit in the 129 MB L2);
-//  5. drop the eigenvalue of smallest modulus (the common-rotation mode of the
-//     absolute rotor angles), take max Re and min damping ratio, classify.
+//  5. max Re and min damping ratio over all eigenvalues, classify.
+// Angle reference: every rotor angle is referred to the first in-service
+// machine (delta'_k = delta_k - delta_0, d delta'_k/dt = ws (omega_k - omega_0),
+// delta_0 dropped).  The absolute-angle matrix has an exact zero eigenvalue
+// (common rotation) to which the slow common-frequency mode is nearly parallel;
+// the referred matrix (5m - 1 states) has the same eigenvalues less that zero
+// and a well-conditioned slow mode.
 #include <cmath>
 
 #include "cs_internal.h"
@@ -177,7 +182,7 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
             for (int k = 0; k < ng; ++k)
                 if (!gen_out(out, k)) gidx[m++] = k;
             sh.m = m;
-            sh.nn = 5 * m;
+            sh.nn = 5 * m - 1;           // angles referred to the first in-service machine
             sh.fail = 0;
         }
         __syncthreads();
@@ -350,16 +355,24 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
                 blk[3][c] = (net.xq[k] - xp) * didq.im / net.Tq0[k];
                 blk[4][c] = -net.KA[k] * dVm / net.TA[k];
             }
+            // angle rows: d delta'_k/dt = ws (omega_k - omega_0) for k != 0 (row of delta_0 dropped)
+            if (kk == ll && kk != 0) blk[0][1] = net.ws;
+            if (ll == 0 && kk != 0) blk[0][1] = -net.ws;
             if (kk == ll) {
-                blk[0][1] = net.ws;
                 blk[1][1] = -net.Dm[k] / net.H2[k];
                 blk[2][2] += -1.0 / net.Td0[k];
                 blk[2][4] = 1.0 / net.Td0[k];
                 blk[3][3] += -1.0 / net.Tq0[k];
                 blk[4][4] = -1.0 / net.TA[k];
             }
-            for (int r = 0; r < 5; ++r)
-                for (int c = 0; c < 5; ++c) A[(size_t)(5 * kk + r) * n + 5 * ll + c] = blk[r][c];
+            // reduced indexing: full index 5k + s -> 5k + s - 1, the angle of machine 0 dropped
+            for (int r = 0; r < 5; ++r) {
+                if (kk == 0 && r == 0) continue;
+                for (int c = 0; c < 5; ++c) {
+                    if (ll == 0 && c == 0) continue;
+                    A[(size_t)(5 * kk + r - 1) * n + 5 * ll + c - 1] = blk[r][c];
+                }
+            }
         }
         __syncthreads();
         // ---- 4a. balancing by powers of two ----
@@ -555,37 +568,13 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
         }
         // ---- 5. statistics and class ----
         {
-            // index of the smallest modulus (ties: smallest index)
-            double best = INFINITY;
-            int bi = 0x7fffffff;
+            double mr = -INFINITY, mz = INFINITY;
             if (!sh.fail) {
                 for (int i = tid; i < n; i += kThreads) {
-                    const double mg = wr[i] * wr[i] + wi[i] * wi[i];
-                    if (mg < best || (mg == best && i < bi)) { best = mg; bi = i; }
+                    mr = fmax(mr, wr[i]);
+                    const double mg = sqrt(wr[i] * wr[i] + wi[i] * wi[i]);
+                    mz = fmin(mz, mg > 0.0 ? -wr[i] / mg : 1.0);
                 }
-            }
-            sh.red[0][tid] = best;
-            sh.ired[tid] = bi;
-            __syncthreads();
-            for (int st2 = kThreads / 2; st2 > 0; st2 >>= 1) {
-                if (tid < st2) {
-                    const double ob = sh.red[0][tid + st2];
-                    const int oi = sh.ired[tid + st2];
-                    if (ob < sh.red[0][tid] || (ob == sh.red[0][tid] && oi < sh.ired[tid])) {
-                        sh.red[0][tid] = ob;
-                        sh.ired[tid] = oi;
-                    }
-                }
-                __syncthreads();
-            }
-            const int drop = sh.ired[0];
-            __syncthreads();
-            double mr = -INFINITY, mz = INFINITY;
-            for (int i = tid; i < n; i += kThreads) {
-                if (i == drop) continue;
-                mr = fmax(mr, wr[i]);
-                const double mg = sqrt(wr[i] * wr[i] + wi[i] * wi[i]);
-                mz = fmin(mz, mg > 0.0 ? -wr[i] / mg : 1.0);
             }
             const double maxre = bmax(sh, mr);
             const double minz = -bmax(sh, -mz);
