@@ -320,6 +320,32 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_profile(args):
+    """Small fixed case for profiler captures (kernels as in the benchmark)."""
+    import torch
+    from paper_2512_08465_gb300 import cs, synth
+    dev = torch.device("cuda", 0)
+    net = synth.case118()
+    ctx = cs.Context()
+    nid = ctx.load_network(net)
+    E = net.n_elem
+    n = min(args.profile, E * (E - 1) // 2)
+    ei = torch.empty(n, dtype=torch.int32, device=dev)
+    ej = torch.empty(n, dtype=torch.int32, device=dev)
+    cs.enumerate_pairs_device(E, 0, n, ei, ej)
+    out = ctx.alloc_results(n, dev)
+    for rep in range(2):
+        if rep == 1:
+            ctx.set_timing(True)
+        ctx.evaluate_device(nid, 0, ei, ej, out)
+        ctx.sync()
+    kms, kcnt = ctx.kernel_times()
+    k = out["klass"].cpu().numpy()
+    print(json.dumps({"profile_pairs": n, "kernel_ms": kms, "launches": kcnt,
+                      "classes": {int(c): int((k == c).sum()) for c in set(k.tolist())}}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,7 +356,13 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--request", type=int, default=4096, help="scenarios per request in the e2e leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", type=int, default=0, metavar="N",
+                    help="profiling case for ncu: N pairs of the 70 %% level, one warm-up and one launch set, "
+                         "no baseline, no e2e, prints per-kernel times")
     args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

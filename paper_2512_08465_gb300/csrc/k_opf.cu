@@ -44,7 +44,7 @@ constexpr int kRec = 46;     // doubles per branch record
 constexpr double kXi = 0.99995;
 constexpr double kSigma = 0.1;
 constexpr double kLimitTol = 1e-6;
-constexpr int kRefineSteps = 3;              // FP64 iterative refinement steps per Newton solve (at most)
+constexpr int kRefineSteps = 12;             // FP64 iterative refinement steps per Newton solve (at most)
 constexpr double kRefineStop = 0x1p-50;      // stop when the correction is below 2^-50 of the solution
 
 // record layout
