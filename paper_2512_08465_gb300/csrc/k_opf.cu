@@ -44,8 +44,10 @@ constexpr int kRec = 46;     // doubles per branch record
 constexpr double kXi = 0.99995;
 constexpr double kSigma = 0.1;
 constexpr double kLimitTol = 1e-6;
-constexpr int kRefineSteps = 12;             // FP64 iterative refinement steps per Newton solve (at most)
+constexpr int kRefineSteps = 3;              // FP64 iterative refinement steps per Newton solve (at most)
 constexpr double kRefineStop = 0x1p-50;      // stop when the correction is below 2^-50 of the solution
+constexpr double kBackwardTol = 1e-13;       // componentwise backward error accepted from the block solve
+constexpr int kDenseMax = 1024;              // dense fallback for reduced systems up to this order
 
 // record layout
 constexpr int R_DSF = 0, R_DST = 8, R_GF = 16, R_GT = 20, R_H = 24, R_LG = 34, R_NG = 38, R_SF = 42, R_ST = 44;
@@ -66,7 +68,8 @@ struct Lay {
     int zf, zt, muf, mut, hf, ht, dzf, dzt, dmuf, dmut, rec;
     // KKT: assembled blocks (Kb, Kd) kept for refinement, factor (Ub, Lb, Db, Di), vectors
     int Kb, Kd, Ub, Lb, Db, Di, x, bv, rv;
-    int total;
+    long dense;                 // dense fallback matrix (4nb)^2, -1 if the network is too large
+    long total;
 };
 
 Lay make_layout(const DevNet& n) {
@@ -88,7 +91,15 @@ Lay make_layout(const DevNet& n) {
     L.Kb = take(16 * n.nL); L.Kd = take(16 * nb);
     L.Ub = take(16 * n.nL); L.Lb = take(16 * n.nL); L.Db = take(16 * nb); L.Di = take(16 * nb);
     L.x = take(4 * nb); L.bv = take(4 * nb); L.rv = take(4 * nb);
-    L.total = (o + 31) & ~31;
+    o = (o + 31) & ~31;
+    if (4 * nb <= kDenseMax) {
+        L.dense = o;
+        L.total = (long)o + (long)16 * nb * nb;
+    } else {
+        L.dense = -1;
+        L.total = o;
+    }
+    L.total = (L.total + 31) & ~31L;
     return L;
 }
 
@@ -324,6 +335,120 @@ __device__ void kkt_residual(const DevNet& net, const double* W, const Lay& L, c
         r[w] = acc;
     }
     __syncthreads();
+}
+
+// Componentwise backward error of x: max_i |b - K x|_i / (|K| |x| + |b|)_i (per thread,
+// to be max-reduced by the caller).
+__device__ double kkt_backward_error(const DevNet& net, const double* W, const Lay& L, const double* x) {
+    const int tid = threadIdx.x, nb = net.nb;
+    double worst = 0.0;
+    for (int w = tid; w < 4 * nb; w += kThreads) {
+        const int i = w >> 2, rr = w & 3;
+        const double* Kd = W + L.Kd + 16 * i + 4 * rr;
+        const double* xi = x + 4 * i;
+        const double bw = W[L.bv + w];
+        double r = bw, sc = fabs(bw);
+        for (int c = 0; c < 4; ++c) { r -= Kd[c] * xi[c]; sc += fabs(Kd[c] * xi[c]); }
+        for (int e = net.Lrowptr[i]; e < net.Lrowptr[i + 1]; ++e) {
+            const double* Kq = W + L.Kb + 16 * net.Lrowblk[e] + 4 * rr;
+            const double* xk = x + 4 * net.Lrowcol[e];
+            for (int c = 0; c < 4; ++c) { r -= Kq[c] * xk[c]; sc += fabs(Kq[c] * xk[c]); }
+        }
+        for (int e = net.Lcolptr[i]; e < net.Lcolptr[i + 1]; ++e) {
+            const double* Kq = W + L.Kb + 16 * e + rr;
+            const double* xj = x + 4 * net.Lrow[e];
+            for (int c = 0; c < 4; ++c) { r -= Kq[4 * c] * xj[c]; sc += fabs(Kq[4 * c] * xj[c]); }
+        }
+        const double be = (sc > 0.0) ? fabs(r) / sc : (r == 0.0 ? 0.0 : INFINITY);
+        worst = fmax(worst, isfinite(be) ? be : INFINITY);
+    }
+    return worst;
+}
+
+struct DenseShared {
+    double val[kThreads / 32];
+    int idx[kThreads / 32];
+    int piv;
+    double pv;
+};
+
+// Dense LU with partial pivoting of the assembled reduced system (order 4 nb,
+// row-major in scratch), solving for b into x.  Backstop for the Newton steps
+// whose block solve did not reach the backward-error target.  Returns false
+// when a pivot column is exactly zero.
+__device__ bool dense_solve(const DevNet& net, double* W, const Lay& L, DenseShared& ds) {
+    const int tid = threadIdx.x, nb = net.nb, N = 4 * nb;
+    const int warp = tid >> 5, lane = tid & 31;
+    double* A = W + L.dense;
+    double* x = W + L.x;
+    for (long w = tid; w < (long)N * N; w += kThreads) A[w] = 0.0;
+    __syncthreads();
+    for (int w = tid; w < 16 * nb; w += kThreads) {
+        const int i = w >> 4, r = (w >> 2) & 3, c = w & 3;
+        A[(long)(4 * i + r) * N + 4 * i + c] = W[L.Kd + 16 * i + 4 * r + c];
+    }
+    for (int w = tid; w < 16 * net.nL; w += kThreads) {
+        const int q = w >> 4, r = (w >> 2) & 3, c = w & 3;
+        const int i = net.Lrow[q], j = net.Lcol[q];
+        const double v = W[L.Kb + 16 * q + 4 * r + c];
+        A[(long)(4 * i + r) * N + 4 * j + c] = v;
+        A[(long)(4 * j + c) * N + 4 * i + r] = v;
+    }
+    for (int w = tid; w < N; w += kThreads) x[w] = W[L.bv + w];
+    __syncthreads();
+    for (int k = 0; k < N; ++k) {
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + tid; i < N; i += kThreads) {
+            const double a = fabs(A[(long)i * N + k]);
+            if (a > best) { best = a; bi = i; }
+        }
+        for (int off = 16; off; off >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { ds.val[warp] = best; ds.idx[warp] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            double b0 = ds.val[0];
+            int i0 = ds.idx[0];
+            for (int q = 1; q < kThreads / 32; ++q)
+                if (ds.val[q] > b0 || (ds.val[q] == b0 && ds.idx[q] < i0)) { b0 = ds.val[q]; i0 = ds.idx[q]; }
+            ds.piv = i0;
+            ds.pv = b0;
+        }
+        __syncthreads();
+        if (!(ds.pv > 0.0) || !isfinite(ds.pv)) return false;
+        const int p = ds.piv;
+        if (p != k) {
+            for (int c = tid; c < N; c += kThreads) {
+                const double t = A[(long)k * N + c];
+                A[(long)k * N + c] = A[(long)p * N + c];
+                A[(long)p * N + c] = t;
+            }
+            if (tid == 0) { const double t = x[k]; x[k] = x[p]; x[p] = t; }
+            __syncthreads();
+        }
+        const double inv = 1.0 / A[(long)k * N + k];
+        for (int i = k + 1 + tid; i < N; i += kThreads) A[(long)i * N + k] *= inv;
+        __syncthreads();
+        const int m = N - k - 1;
+        for (long w = tid; w < (long)m * m; w += kThreads) {
+            const int i = k + 1 + (int)(w / m), j = k + 1 + (int)(w % m);
+            A[(long)i * N + j] -= A[(long)i * N + k] * A[(long)k * N + j];
+        }
+        for (int i = k + 1 + tid; i < N; i += kThreads) x[i] -= A[(long)i * N + k] * x[k];
+        __syncthreads();
+    }
+    for (int k = N - 1; k >= 0; --k) {
+        if (tid == 0) x[k] /= A[(long)k * N + k];
+        __syncthreads();
+        const double xk = x[k];
+        for (int i = tid; i < k; i += kThreads) x[i] -= A[(long)i * N + k] * xk;
+        __syncthreads();
+    }
+    return true;
 }
 
 struct Scal {          // per-scenario scalars in shared memory
@@ -644,6 +769,17 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                 const int ops2[2] = {0, 0};
                 block_reduce<2>(rb, v2, ops2, sc.red);
                 if (!(sc.red[0] > kRefineStop * sc.red[1])) break;     // correction negligible (or NaN: caught below)
+            }
+            if (L.dense >= 0) {
+                double v1[1] = {kkt_backward_error(net, W, L, W + L.x)};
+                const int ops1[1] = {0};
+                block_reduce<1>(rb, v1, ops1, sc.red);
+                if (!(sc.red[0] <= kBackwardTol)) {
+                    __shared__ DenseShared ds;
+                    if (!dense_solve(net, W, L, ds)) sc.fail = 1;
+                    __syncthreads();
+                    if (sc.fail) break;
+                }
             }
             // ---------------- recover the eliminated steps, dz, dmu, ratios ----------------
             double rp = INFINITY, rd = INFINITY, bad = 0.0;
