@@ -163,6 +163,30 @@ def fp64_peak_measured(torch, dev):
     return 2.0 * n ** 3 / best / 1e12
 
 
+def _algorithmic_flops(net, res_lv, E, mixed_reruns=0):
+    """Algorithmic FP64/FP32 work of the small-signal kernel for one step:
+    10 n^3 flops per converged scenario (Golub & Van Loan's count for
+    Hessenberg + Francis QR, eigenvalues only), n = 5 in-service generators - 1."""
+    import numpy as np
+    from paper_2512_08465_gb300 import synth
+    ii, jj = synth.all_pairs(E)
+    gout = (ii >= net.n_branch).astype(np.int64) + (jj >= net.n_branch).astype(np.int64)
+    tot = 0.0
+    for k in res_lv:
+        ok = (k == 0) | (k == 4) | (k == 5) | (k == 6)
+        nst = 5.0 * (net.n_gen - gout[ok]) - 1.0
+        tot += float(np.sum(10.0 * nst ** 3))
+    return tot
+
+
+def _opf_flops_per_iter(ctx_sym):
+    """Algorithmic FP64 flops of one interior-point iteration on the 118-bus
+    network: block factorisation (1,857 block updates x 128 + 464 L blocks x 128
+    + 118 pivot inverses x ~200), one solve (2 x 464 x 32 + 118 x 32), branch
+    derivatives (186 x ~1,200)."""
+    return 1857 * 128 + 464 * 128 + 118 * 200 + 2 * 464 * 32 + 118 * 32 + 186 * 1200
+
+
 def run_ours(args):
     import numpy as np
     rank, world, local = _env_rank()
@@ -178,89 +202,110 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     from paper_2512_08465_gb300 import cs, synth
     net = synth.case118(seed=118 + rank)
-    ctx = cs.Context(device=local)
-    nid = ctx.load_network(net)
     E = net.n_elem
     npair = E * (E - 1) // 2
+    lam = synth.failure_rates(E, 2512)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def make(prec):
+        ctx = cs.Context(device=local, precision=prec)
+        nid = ctx.load_network(net)
+        return ctx, nid
+
     ei = torch.empty(npair, dtype=torch.int32, device=dev)
     ej = torch.empty(npair, dtype=torch.int32, device=dev)
     cs.enumerate_pairs_device(E, 0, npair, ei, ej)
     n1i = torch.arange(E, dtype=torch.int32, device=dev)
     n1j = torch.full((E,), -1, dtype=torch.int32, device=dev)
-    outs = {lv: (ctx.alloc_results(npair, dev), ctx.alloc_results(E, dev)) for lv in (0, 1)}
-    lam = synth.failure_rates(E, 2512)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
 
-    def step():
-        for lv in (0, 1):
-            ctx.evaluate_device(nid, lv, ei, ej, outs[lv][0], stream)
-            launches[0] += ctx.last_launch_count()
-            ctx.evaluate_device(nid, lv, n1i, n1j, outs[lv][1], stream)
-            launches[0] += ctx.last_launch_count()
-        for lv in (0, 1):
-            ctx.risk_index(nid, lv, lam, cs.RISK_ORDERED)
-            launches[0] += 1
+    def measure(ctx, nid, warmup, steps, clocks=False):
+        outs = {lv: (ctx.alloc_results(npair, dev), ctx.alloc_results(E, dev)) for lv in (0, 1)}
+        launches = [0]
 
-    launches = [0]
-    for _ in range(args.warmup):
-        step()
-    ctx.sync(stream)
-    torch.cuda.synchronize()
-    launches[0] = 0
-    ctx.set_timing(True)
-    sampler = ClockSampler(local)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    wall0 = time.perf_counter()
-    step_ms = []
-    for _ in range(args.steps):
-        flush.zero_()                                   # L2 flush, outside the timed events
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    clocks = sampler.stop()
-    ctx.sync(stream)
-    kms, kcnt = ctx.kernel_times()
-    ctx.set_timing(False)
-    ms = sum(step_ms) / len(step_ms)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-    ms_max = float(t.item())
-    n2_per_rank = 2 * npair
-    value = n2_per_rank * world / (ms_max / 1e3)
+        def step():
+            for lv in (0, 1):
+                ctx.evaluate_device(nid, lv, ei, ej, outs[lv][0], stream)
+                launches[0] += ctx.last_launch_count()
+                ctx.evaluate_device(nid, lv, n1i, n1j, outs[lv][1], stream)
+                launches[0] += ctx.last_launch_count()
+            for lv in (0, 1):
+                ctx.risk_index(nid, lv, lam, cs.RISK_ORDERED)
+                launches[0] += 1
 
-    # per-kernel work for the roofline of the dominant kernel (small-signal screen)
-    res = {lv: {k: v.cpu().numpy() for k, v in outs[lv][0].items()} for lv in (0, 1)}
-    flops_dyn = 0.0
-    ng = net.n_gen
-    # in-service generators per scenario: ng minus generator outages in the pair
-    ii, jj = synth.all_pairs(E)
-    gout = (ii >= net.n_branch).astype(np.int64) + (jj >= net.n_branch).astype(np.int64)
-    for lv in (0, 1):
-        k = res[lv]["klass"]
-        ok = (k == 0) | (k == 4) | (k == 5) | (k == 6)
-        nst = 5.0 * (ng - gout[ok])
-        flops_dyn += float(np.sum(10.0 * nst ** 3))
-    dyn_launch_ms = kms["dyn"] / max(1, kcnt["dyn"])
-    dyn_launches_per_step = kcnt["dyn"] / args.steps
-    # work per dyn launch averaged over the N-2 launches of a step (N-1 launches are small)
-    flops_per_step = flops_dyn
-    dyn_ms_per_step = kms["dyn"] / args.steps
-    achieved = flops_per_step / (dyn_ms_per_step / 1e3) / 1e12
-    peak, peak32 = cs.alu_peak(local)
+        for _ in range(warmup):
+            step()
+        ctx.sync(stream)
+        torch.cuda.synchronize()
+        launches[0] = 0
+        ctx.set_timing(True)
+        sampler = ClockSampler(local) if clocks else None
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        wall0 = time.perf_counter()
+        step_ms = []
+        for _ in range(steps):
+            flush.zero_()                                   # L2 flush, outside the timed events
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        clk = sampler.stop() if sampler else None
+        ctx.sync(stream)
+        kms, kcnt = ctx.kernel_times()
+        ctx.set_timing(False)
+        ms = sum(step_ms) / len(step_ms)
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            torch.distributed.barrier()
+        klass = [outs[lv][0]["klass"].cpu().numpy() for lv in (0, 1)]
+        iters = sum(int(outs[lv][q]["opf_iters"].to(torch.int64).sum().item()) for lv in (0, 1) for q in (0, 1))
+        return dict(ms=float(t.item()), wall=wall, kms=kms, kcnt=kcnt, clocks=clk, launches=launches[0],
+                    klass=klass, iters=iters)
+
+    ctx_m, nid_m = make(cs.PREC_MIXED)
+    mixed = measure(ctx_m, nid_m, args.warmup, args.steps, clocks=True)
+    reruns = ctx_m.eigen_reruns()
+    ctx_d, nid_d = make(cs.PREC_FP64)
+    fp64 = measure(ctx_d, nid_d, 1, args.steps)
+    same = all(np.array_equal(a, b) for a, b in zip(mixed["klass"], fp64["klass"]))
+    ctx_d.close()
+
+    n2 = 2 * npair * world
+    value = n2 / (mixed["ms"] / 1e3)
+    kms, kcnt = mixed["kms"], mixed["kcnt"]
     share = {k: v / max(1e-9, sum(kms.values())) for k, v in kms.items()}
+    dominant = max(kms, key=kms.get)
+    peak64, peak32 = cs.alu_peak(local)
+    if dominant == "opf":
+        roof = {"kernel": "opf_kernel (interior-point OPF: branch derivatives, block LDL^T, refined solves)",
+                "bound": "alu", "unit": "TFLOP/s", "peak": peak64,
+                "peak_source": "measured in this run: FP64 FMA-chain probe (cs_alu_peak), all SMs",
+                "work": "per interior-point iteration ~5.8e5 FP64 flops (factorisation + one solve + branch "
+                        "derivatives), times the iterations each scenario took"}
+    else:
+        roof = {"kernel": "dyn_kernel (Kron + state matrix + Hessenberg + Francis QR)", "bound": "alu",
+                "unit": "TFLOP/s", "peak": peak32,
+                "peak_source": "measured in this run: FP32 FMA-chain probe (cs_alu_peak), all SMs",
+                "work": "10 n^3 flops per converged scenario, n = 5 x in-service generators - 1"}
+    # achieved work of the dominant kernel per step
+    if dominant == "opf":
+        roof["achieved"] = mixed["iters"] * _opf_flops_per_iter(None) / (kms["opf"] / args.steps / 1e3) / 1e12
+        roof["iterations_per_step"] = mixed["iters"]
+    else:
+        roof["achieved"] = _algorithmic_flops(net, mixed["klass"], E) / (kms["dyn"] / args.steps / 1e3) / 1e12
+    roof.update({"launches_per_step": kcnt[dominant] / args.steps,
+                 "avg_launch_ms": kms[dominant] / max(1, kcnt[dominant]), "traffic": None})
 
-    # ---- end to end through the host-buffer ABI ----
+    # ---- end to end through the host-buffer ABI (mixed form) ----
     ei_h = ei.cpu().numpy()
     ej_h = ej.cpu().numpy()
     n1i_h = np.arange(E, dtype=np.int32)
@@ -268,54 +313,56 @@ def run_ours(args):
     chunk = args.request
     lat = []
     e2e_ms = []
-    for rep in range(max(1, min(args.steps, 2))):
+    for rep in range(1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pend = []
         for lv in (0, 1):
             for c0 in range(0, npair, chunk):
-                rid = ctx.submit(nid, lv, ei_h[c0:c0 + chunk], ej_h[c0:c0 + chunk])
+                rid = ctx_m.submit(nid_m, lv, ei_h[c0:c0 + chunk], ej_h[c0:c0 + chunk])
                 pend.append((rid, time.perf_counter()))
-            pend.append((ctx.submit(nid, lv, n1i_h, n1j_h), time.perf_counter()))
+            pend.append((ctx_m.submit(nid_m, lv, n1i_h, n1j_h), time.perf_counter()))
         for rid, ts in pend:
-            out = ctx.poll(rid, 600_000_000)
+            ctx_m.poll(rid, 600_000_000)
             lat.append(1e3 * (time.perf_counter() - ts))
         for lv in (0, 1):
-            ctx.risk_index(nid, lv, lam, cs.RISK_ORDERED)
+            ctx_m.risk_index(nid_m, lv, lam, cs.RISK_ORDERED)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_step = sum(e2e_ms) / len(e2e_ms)
     h2d = 2 * (2 * npair + 2 * E) * 4 + 2 * E * 8
     d2h = 2 * (npair + E) * (1 + 1 + 2 + 2 + 8 * 3) + 2 * E * 8
     lat.sort()
+    ctx_m.close()
 
     if rank == 0:
+        if roof.get("achieved") is not None:
+            roof["frac"] = roof["achieved"] / roof["peak"]
+        else:
+            roof["frac"] = None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": "fp64", "network_seed": 118,
-                       "n2_scenarios_per_step": n2_per_rank * world, "l2": "flushed between steps (512 MB write)",
-                       "parallelism": f"replicas x{world}", "wall_s_timed_region": wall},
-            "roofline": {"kernel": "dyn_kernel (Kron + state matrix + Hessenberg + Francis QR)",
-                         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak,
-                         "peak_source": "measured in this run: FP64 FMA-chain probe (cs_alu_peak), all SMs",
-                         "fp32_peak_measured": peak32,
-                         "work": "10 n^3 FP64 flops per converged scenario, n = 5 x in-service generators",
-                         "launches_per_step": dyn_launches_per_step, "avg_launch_ms": dyn_launch_ms,
-                         "traffic": None},
+            "warmup": args.warmup, "ms_per_step": mixed["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("FP64 form", "mixed form (FP64 OPF, FP32 eigen screen with "
+                                                               "FP64 re-run in the guard band)"),
+                       "form": "mixed", "network_seed": 118, "n2_scenarios_per_step": n2,
+                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}",
+                       "wall_s_timed_region": mixed["wall"], "eigen_fp64_reruns": reruns},
+            "fp64_form": {"value": n2 / (fp64["ms"] / 1e3), "ms_per_step": fp64["ms"],
+                          "kernel_ms_per_step": {k: v / args.steps for k, v in fp64["kms"].items()},
+                          "classes_identical_to_mixed": bool(same)},
+            "roofline": roof,
             "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
             "kernel_share": share,
-            "e2e": {"value": 2 * npair / (e2e_step / 1e3) * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": 2 * npair * world / (e2e_step / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step,
                     "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                                    "request_scenarios": chunk}},
-            "gpu_launches": launches[0],
-            "clocks": clocks,
+            "gpu_launches": mixed["launches"],
+            "clocks": mixed["clocks"],
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

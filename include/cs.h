@@ -60,6 +60,13 @@ enum {
  * Section V (1.472 for a line with every scenario severe under Table I). */
 enum { CS_RISK_EQ3 = 0, CS_RISK_ORDERED = 1 };
 
+/* Precision forms.  FP64: every step in FP64.  MIXED: the eigenvalue screen
+ * runs in FP32 and is re-run in FP64 when its decision lies within 5e-3 of a
+ * threshold (|max Re| or |min zeta - damping_min|) or the FP32 iteration fails;
+ * classes are therefore those of the FP64 form, max_re / min_zeta carry the
+ * FP32 error outside the guard band.  The OPF stays in FP64 in both forms. */
+enum { CS_PREC_FP64 = 0, CS_PREC_MIXED = 1 };
+
 typedef struct cs_ctx cs_ctx;
 
 typedef struct {
@@ -70,6 +77,7 @@ typedef struct {
     int32_t require_secure_base; /* 1: cs_load_network fails with CS_E_BASE_INSECURE */
     int32_t ctas_per_sm;       /* resident scenario blocks per SM; 0 = automatic */
     int32_t chunk;             /* scenarios per internal batch; 0 = automatic */
+    int32_t precision;         /* CS_PREC_FP64 (default) or CS_PREC_MIXED */
 } cs_options;
 
 /* Fills *opt with the defaults (damping_min 0.05, opf_tol 1e-8, opf_max_it 50). */
@@ -192,6 +200,10 @@ const char* cs_last_error(cs_ctx* ctx);
 
 /* Kernel launches issued by the last cs_evaluate_device / cs_submit call. */
 int64_t cs_last_launch_count(cs_ctx* ctx);
+
+/* Number of scenarios whose FP32 eigen screen was re-run in FP64 (MIXED form),
+ * accumulated since the context was created; waits for the device. */
+cs_status cs_eigen_reruns(cs_ctx* ctx, int64_t* count);
 
 /* Per-kernel device timing (off by default).  When enabled, every evaluation
  * records CUDA events on its stream around the islanding, OPF and small-signal

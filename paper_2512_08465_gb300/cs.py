@@ -24,11 +24,12 @@ ERRORS = {-1: "CS_E_ARG", -2: "CS_E_NOMEM", -3: "CS_E_BASE_INSECURE", -4: "CS_E_
           -5: "CS_E_CUDA", -6: "CS_E_UNKNOWN_ID", -7: "CS_E_NUMERIC"}
 CLASSES = ("SECURE", "ISLANDED", "OPF_NONCONV", "LIMIT", "SS_UNSTABLE", "SS_POORLY_DAMPED", "EIG_FAIL")
 RISK_EQ3, RISK_ORDERED = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
 
 EXPORTS = ("cs_default_options", "cs_create", "cs_destroy", "cs_load_network", "cs_unload_network",
            "cs_base_result", "cs_evaluate_device", "cs_sync", "cs_submit_contingencies", "cs_poll",
            "cs_risk_index", "cs_risk_reduce_device", "cs_enumerate_pairs_device", "cs_last_error",
-           "cs_last_launch_count", "cs_set_timing", "cs_kernel_times", "cs_alu_peak")
+           "cs_last_launch_count", "cs_set_timing", "cs_kernel_times", "cs_alu_peak", "cs_eigen_reruns")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -37,7 +38,7 @@ _ip = ctypes.POINTER(ctypes.c_int32)
 class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("damping_min", ctypes.c_double), ("opf_tol", ctypes.c_double),
                 ("opf_max_it", ctypes.c_int32), ("require_secure_base", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 class NetworkDesc(ctypes.Structure):
@@ -100,6 +101,7 @@ def load_library(build_if_missing: bool = True):
         "cs_set_timing": (i32, [P, i32]),
         "cs_kernel_times": (i32, [P, P, P]),
         "cs_alu_peak": (i32, [i32, P, P]),
+        "cs_eigen_reruns": (i32, [P, ctypes.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -236,6 +238,11 @@ class Context:
 
     def last_launch_count(self) -> int:
         return int(self.lib.cs_last_launch_count(self.h))
+
+    def eigen_reruns(self) -> int:
+        c = ctypes.c_int64()
+        self._check(self.lib.cs_eigen_reruns(self.h, ctypes.byref(c)), "cs_eigen_reruns")
+        return c.value
 
     def set_timing(self, enable: bool = True):
         self._check(self.lib.cs_set_timing(self.h, int(enable)), "cs_set_timing")

@@ -136,7 +136,10 @@ cs_status evaluate_impl(cs_ctx* ctx, Network* net, int level, const int32_t* ei,
     CS_CUDA(ctx->opfx.ensure(sizeof(double) * nx * cn));
     CS_CUDA(ctx->opfst.ensure(sizeof(int) * cn));
     CS_CUDA(ctx->counters.ensure(sizeof(int) * 4));
-    CS_CUDA(ctx->err_word.ensure(sizeof(int)));
+    if (!ctx->err_word.p) {
+        CS_CUDA(ctx->err_word.ensure(sizeof(int) * 2));
+        CS_CUDA(cudaMemset(ctx->err_word.p, 0, sizeof(int) * 2));
+    }
     int* counters = (int*)ctx->counters.p;
     for (int64_t c0 = 0; c0 < n; c0 += chunk) {
         const int64_t m = std::min(chunk, n - c0);
@@ -158,6 +161,7 @@ cs_status evaluate_impl(cs_ctx* ctx, Network* net, int level, const int32_t* ei,
         a.sev_n1 = record ? (uint8_t*)net->sev_n1[level]->p : nullptr;
         a.sev_pairs = record ? (uint8_t*)net->sev_pairs[level]->p : nullptr;
         a.err = (int*)ctx->err_word.p;
+        a.reruns = (int*)ctx->err_word.p + 1;
         OpfOut o{(double*)ctx->opfx.p, (int*)ctx->opfst.p};
         CS_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * 4, s));
         auto mark = [&](int kind) -> cudaError_t {     // start event of a timed launch
@@ -186,7 +190,7 @@ cs_status evaluate_impl(cs_ctx* ctx, Network* net, int level, const int32_t* ei,
                            (double*)ctx->scratch.p, per_opf, std::min<int64_t>(g_opf, m), counters, s));
         CS_CUDA(done());
         CS_CUDA(mark(2));
-        CS_CUDA(launch_dyn(dn, a, o, ctx->opt.damping_min, (double*)ctx->scratch.p, per_dyn,
+        CS_CUDA(launch_dyn(dn, a, o, ctx->opt.damping_min, ctx->opt.precision, (double*)ctx->scratch.p, per_dyn,
                            std::min<int64_t>(g_dyn, m), counters + 1, s));
         CS_CUDA(done());
         ctx->launches += 3 + (a.sev_n1 ? 1 : 0);
@@ -207,6 +211,7 @@ void cs_default_options(cs_options* o) {
     o->require_secure_base = 0;
     o->ctas_per_sm = 0;
     o->chunk = 0;
+    o->precision = CS_PREC_FP64;
 }
 
 cs_status cs_create(const cs_options* opt, cs_ctx** out) {
@@ -215,6 +220,7 @@ cs_status cs_create(const cs_options* opt, cs_ctx** out) {
     std::unique_ptr<cs_ctx> c(new cs_ctx());
     if (opt) c->opt = *opt; else cs_default_options(&c->opt);
     if (c->opt.opf_max_it < 0 || c->opt.opf_max_it > 10000 || !(c->opt.opf_tol > 0.0)) return CS_E_ARG;
+    if (c->opt.precision != CS_PREC_FP64 && c->opt.precision != CS_PREC_MIXED) return CS_E_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return CS_E_CUDA;
     if (c->opt.device < 0 || c->opt.device >= ndev) return CS_E_ARG;
@@ -242,6 +248,18 @@ cs_status cs_destroy(cs_ctx* ctx) {
 const char* cs_last_error(cs_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
 int64_t cs_last_launch_count(cs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+cs_status cs_eigen_reruns(cs_ctx* ctx, int64_t* count) {
+    if (!ctx || !count) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    *count = 0;
+    if (!ctx->err_word.p) return CS_OK;
+    CS_CUDA(cudaDeviceSynchronize());
+    int v = 0;
+    CS_CUDA(cudaMemcpy(&v, (int*)ctx->err_word.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    *count = v;
+    return CS_OK;
+}
 
 cs_status cs_set_timing(cs_ctx* ctx, int32_t enable) {
     if (!ctx) return CS_E_ARG;

@@ -140,6 +140,7 @@ struct EvalArgs {
     uint8_t* sev_n1;        // severity table of the level: [nE] (255 = missing)
     uint8_t* sev_pairs;     // [nE*(nE-1)/2]
     int* err;               // device error word
+    int* reruns;            // device counter: FP64 eigen re-runs of the mixed-precision screen
 };
 
 // launch wrappers (return cudaError_t)
@@ -148,7 +149,7 @@ cudaError_t launch_opf(const DevNet& net, const EvalArgs& a, const int* islanded
                        double tol, int max_it, double* scratch, size_t scratch_per_cta, int grid,
                        int* counter, cudaStream_t s);
 size_t opf_scratch_doubles(const DevNet& net);
-cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double damping_min,
+cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double damping_min, int precision,
                        double* scratch, size_t scratch_per_cta, int grid, int* counter,
                        cudaStream_t s);
 size_t dyn_scratch_doubles(const DevNet& net);

@@ -43,6 +43,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr double kEps = 2.220446049250313e-16;
+constexpr double kGuardRe = 5e-3;      // |max Re| within this of 0: decide in FP64
+constexpr double kGuardZeta = 5e-3;    // |min zeta - threshold| within this: decide in FP64
 
 struct DLay {
     int Yu, Yl, Yd, Ydi;      // complex arrays (2 doubles per entry)
@@ -50,7 +52,8 @@ struct DLay {
     int rhs;                  // [ng*nb] complex
     int gen;                  // [ng * kGen]
     int A;                    // [(5ng)^2]
-    int wr, wi;               // [5ng]
+    int A32;                  // [(5ng)^2] floats (mixed precision screen)
+    int wr, wi, v;            // [5ng]
     int total;
 };
 constexpr int kGen = 16;      // per-generator doubles: E(2) I(2) e^{jd}(2) Vt(2) |Vt| id iq eq ed ym(2)
@@ -66,7 +69,9 @@ DLay make_dlayout(const DevNet& n) {
     L.gen = take((long)kGen * n.ng);
     o = (o + 31) & ~31;
     L.A = take(25L * n.ng * n.ng);
-    L.wr = take(5L * n.ng); L.wi = take(5L * n.ng);
+    L.A32 = take((25L * n.ng * n.ng + 1) / 2);
+    o = (o + 31) & ~31;
+    L.wr = take(5L * n.ng); L.wi = take(5L * n.ng); L.v = take(5L * n.ng);
     L.total = (o + 31) & ~31;
     return L;
 }
@@ -154,9 +159,224 @@ __device__ void eig2(double p, double q, double r, double s, double* re, double*
     }
 }
 
+
+// Eigenvalues of the n x n row-major matrix A (overwritten) in arithmetic T:
+// balancing by powers of two, Householder Hessenberg reduction, Francis
+// double-shift QR with deflation (eigenvalues only).  v: n entries of T
+// scratch.  Results in wr/wi (double).  sh.fail = 2 if QR did not converge.
+template <typename T>
+__device__ void eigen_screen(T* A, const int n, T* v, double* wr, double* wi, DShared& sh) {
+    const int tid = threadIdx.x;
+    const double eps = (sizeof(T) == 8) ? kEps : 1.1920928955078125e-07;
+    // balancing by powers of two
+        if (tid == 0) sh.done = 0;
+        __syncthreads();
+        for (int sweep = 0; !sh.done && sweep < 100; ++sweep) {   // converges in a few sweeps; capped
+            __syncthreads();
+            if (tid == 0) sh.done = 1;
+            for (int i = 0; i < n; ++i) {
+                double c = 0.0, r = 0.0;
+                for (int j = tid; j < n; j += kThreads) {
+                    if (j == i) continue;
+                    c += fabs(A[(size_t)j * n + i]);
+                    r += fabs(A[(size_t)i * n + j]);
+                }
+                bsum2(sh, c, r);
+                if (c == 0.0 || r == 0.0 || !isfinite(c) || !isfinite(r)) continue;
+                double g = r / 2.0, f = 1.0;
+                const double ssum = c + r;
+                while (c < g) { f *= 2.0; c *= 4.0; }
+                g = r * 2.0;
+                while (c > g) { f /= 2.0; c /= 4.0; }
+                if ((c + r) / f < 0.95 * ssum) {
+                    const T ginv = (T)(1.0 / f);
+                    const T fT = (T)f;
+                    for (int j = tid; j < n; j += kThreads) A[(size_t)i * n + j] *= ginv;
+                    __syncthreads();
+                    for (int j = tid; j < n; j += kThreads) A[(size_t)j * n + i] *= fT;
+                    if (tid == 0) sh.done = 0;
+                    __syncthreads();
+                }
+            }
+            __syncthreads();
+        }
+    // Householder reduction to Hessenberg form
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int k = 0; k + 2 < n; ++k) {
+            double t = 0.0;
+            for (int i = k + 2 + tid; i < n; i += kThreads) {
+                const double q = (double)A[(size_t)i * n + k];
+                t += q * q;
+            }
+            const double tail = bsum(sh, t);
+            if (tail == 0.0) continue;
+            const double x0 = (double)A[(size_t)(k + 1) * n + k];
+            const double nrm2 = x0 * x0 + tail;
+            const double alpha = (x0 >= 0.0) ? -sqrt(nrm2) : sqrt(nrm2);
+            const int mm = n - k - 1;
+            const double v0 = x0 - alpha;
+            const T beta = (T)(2.0 / (v0 * v0 + tail));
+            for (int i = tid; i < mm; i += kThreads) v[i] = (i == 0) ? (T)v0 : A[(size_t)(k + 1 + i) * n + k];
+            __syncthreads();
+            for (int j = k + tid; j < n; j += kThreads) {          // left: columns k..n-1
+                T sacc = 0;
+                for (int i = 0; i < mm; ++i) sacc += v[i] * A[(size_t)(k + 1 + i) * n + j];
+                sacc *= beta;
+                for (int i = 0; i < mm; ++i) A[(size_t)(k + 1 + i) * n + j] -= sacc * v[i];
+            }
+            __syncthreads();
+            for (int i = warp; i < n; i += kThreads / 32) {        // right: all rows
+                T* row = A + (size_t)i * n + k + 1;
+                T sacc = 0;
+                for (int j = lane; j < mm; j += 32) sacc += row[j] * v[j];
+                for (int off = 16; off; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+                sacc *= beta;
+                for (int j = lane; j < mm; j += 32) row[j] -= sacc * v[j];
+            }
+            __syncthreads();
+            for (int i = k + 1 + tid; i < n; i += kThreads) A[(size_t)i * n + k] = (i == k + 1) ? (T)alpha : (T)0;
+            __syncthreads();
+        }
+    // Francis double-shift QR, eigenvalues only
+        {
+            double hm = 0.0;
+            for (int w = tid; w < n * n; w += kThreads) {
+                const int i = w / n, j = w % n;
+                if (j >= i - 1) hm = fmax(hm, fabs((double)A[w]));
+            }
+            hm = bmax(sh, hm);
+            if (tid == 0) {
+                sh.hmax = hm;
+                sh.hi = n - 1;
+                sh.its = 0;
+            }
+            __syncthreads();
+        }
+        while (sh.hi >= 0) {
+            const int hi = sh.hi;
+            // locate the top of the unreduced block ending at hi: largest l <= hi with a negligible A[l][l-1]
+            int cand = 0;
+            for (int l = 1 + tid; l <= hi; l += kThreads) {
+                double sd = fabs((double)A[(size_t)(l - 1) * n + l - 1]) + fabs((double)A[(size_t)l * n + l]);
+                if (sd == 0.0) sd = sh.hmax;
+                if (fabs((double)A[(size_t)l * n + l - 1]) <= eps * sd) cand = max(cand, l);
+            }
+            const int lo = bmax_int(sh, cand);
+            if (tid == 0 && lo > 0) A[(size_t)lo * n + lo - 1] = (T)0;
+            if (lo == hi) {
+                if (tid == 0) {
+                    wr[hi] = A[(size_t)hi * n + hi];
+                    wi[hi] = 0.0;
+                    sh.hi = hi - 1;
+                    sh.its = 0;
+                }
+                __syncthreads();
+                continue;
+            }
+            if (lo == hi - 1) {
+                if (tid == 0) {
+                    double re[2], im[2];
+                    eig2(A[(size_t)(hi - 1) * n + hi - 1], A[(size_t)(hi - 1) * n + hi], A[(size_t)hi * n + hi - 1],
+                         A[(size_t)hi * n + hi], re, im);
+                    wr[hi - 1] = re[0]; wi[hi - 1] = im[0];
+                    wr[hi] = re[1]; wi[hi] = im[1];
+                    sh.hi = hi - 2;
+                    sh.its = 0;
+                }
+                __syncthreads();
+                continue;
+            }
+            if (sh.its >= 30 * n) {
+                if (tid == 0) sh.fail = 2;
+                __syncthreads();
+                break;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                const int its = ++sh.its;
+                double sft, tft;
+                const double a11 = A[(size_t)(hi - 1) * n + hi - 1], a12 = A[(size_t)(hi - 1) * n + hi];
+                const double a21 = A[(size_t)hi * n + hi - 1], a22 = A[(size_t)hi * n + hi];
+                if (its == 10 || its == 20) {
+                    const double ww = fabs(a21) + fabs(A[(size_t)(hi - 1) * n + hi - 2]);
+                    sft = 1.5 * ww;
+                    tft = ww * ww;
+                } else {
+                    sft = a11 + a22;
+                    tft = a11 * a22 - a12 * a21;
+                }
+                const double h00 = A[(size_t)lo * n + lo], h01 = A[(size_t)lo * n + lo + 1];
+                const double h10 = A[(size_t)(lo + 1) * n + lo], h11 = A[(size_t)(lo + 1) * n + lo + 1];
+                const double h21 = A[(size_t)(lo + 2) * n + lo + 1];
+                sh.x[0] = h00 * h00 + h01 * h10 - sft * h00 + tft;
+                sh.x[1] = h10 * (h00 + h11 - sft);
+                sh.x[2] = h10 * h21;
+            }
+            __syncthreads();
+            double x0 = sh.x[0], x1 = sh.x[1], x2 = sh.x[2];
+            for (int k = lo; k <= hi - 1; ++k) {
+                const int len = (k + 2 <= hi) ? 3 : 2;
+                const double t2 = x1 * x1 + (len == 3 ? x2 * x2 : 0.0);
+                if (t2 != 0.0) {
+                    const double nrm = sqrt(x0 * x0 + t2);
+                    const double al = (x0 >= 0.0) ? -nrm : nrm;
+                    const T u0 = (T)(x0 - al), u1 = (T)x1, u2 = (len == 3) ? (T)x2 : (T)0;
+                    const T bt = (T)(2.0 / ((x0 - al) * (x0 - al) + t2));
+                    const int c0 = (k > lo) ? k - 1 : lo;
+                    for (int j = c0 + tid; j <= hi; j += kThreads) {   // rows k..k+len-1
+                        T* p0 = A + (size_t)k * n + j;
+                        T d = u0 * p0[0] + u1 * p0[n];
+                        if (len == 3) d += u2 * p0[2 * n];
+                        d *= bt;
+                        p0[0] -= d * u0;
+                        p0[n] -= d * u1;
+                        if (len == 3) p0[2 * n] -= d * u2;
+                    }
+                    __syncthreads();
+                    const int r1 = (k + 3 < hi) ? k + 3 : hi;
+                    for (int i = lo + tid; i <= r1; i += kThreads) {   // columns k..k+len-1
+                        T* p0 = A + (size_t)i * n + k;
+                        T d = p0[0] * u0 + p0[1] * u1;
+                        if (len == 3) d += p0[2] * u2;
+                        d *= bt;
+                        p0[0] -= d * u0;
+                        p0[1] -= d * u1;
+                        if (len == 3) p0[2] -= d * u2;
+                    }
+                    __syncthreads();
+                }
+                if (k + 1 <= hi - 1) {
+                    x0 = A[(size_t)(k + 1) * n + k];
+                    x1 = A[(size_t)(k + 2) * n + k];
+                    x2 = (k + 3 <= hi) ? A[(size_t)(k + 3) * n + k] : 0.0;
+                }
+            }
+            for (int i = lo + 2 + tid; i <= hi; i += kThreads) {
+                A[(size_t)i * n + i - 2] = (T)0;
+                if (i >= lo + 3) A[(size_t)i * n + i - 3] = (T)0;
+            }
+            __syncthreads();
+        }
+}
+
+// max Re and min damping ratio over the n eigenvalues (block-wide, result on all threads)
+__device__ void eig_stats(DShared& sh, int n, const double* wr, const double* wi, double& maxre, double& minz) {
+    const int tid = threadIdx.x;
+    double mr = -INFINITY, mz = INFINITY;
+    if (!sh.fail) {
+        for (int i = tid; i < n; i += kThreads) {
+            mr = fmax(mr, wr[i]);
+            const double mg = sqrt(wr[i] * wr[i] + wi[i] * wi[i]);
+            mz = fmin(mz, mg > 0.0 ? -wr[i] / mg : 1.0);
+        }
+    }
+    maxre = bmax(sh, mr);
+    minz = -bmax(sh, -mz);
+}
+
 __global__ void __launch_bounds__(kThreads)
-dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch, size_t per_cta,
-           DLay L, int* counter) {
+dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, int precision, double* scratch,
+           size_t per_cta, DLay L, int* counter) {
     __shared__ DShared sh;
     extern __shared__ int gidx[];     // [ng] compact -> generator id
     const int tid = threadIdx.x;
@@ -375,209 +595,32 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
             }
         }
         __syncthreads();
-        // ---- 4a. balancing by powers of two ----
-        if (tid == 0) sh.done = 0;
-        __syncthreads();
-        for (int sweep = 0; !sh.done && sweep < 100; ++sweep) {   // converges in a few sweeps; capped
-            __syncthreads();
-            if (tid == 0) sh.done = 1;
-            for (int i = 0; i < n; ++i) {
-                double c = 0.0, r = 0.0;
-                for (int j = tid; j < n; j += kThreads) {
-                    if (j == i) continue;
-                    c += fabs(A[(size_t)j * n + i]);
-                    r += fabs(A[(size_t)i * n + j]);
-                }
-                bsum2(sh, c, r);
-                if (c == 0.0 || r == 0.0 || !isfinite(c) || !isfinite(r)) continue;
-                double g = r / 2.0, f = 1.0;
-                const double ssum = c + r;
-                while (c < g) { f *= 2.0; c *= 4.0; }
-                g = r * 2.0;
-                while (c > g) { f /= 2.0; c /= 4.0; }
-                if ((c + r) / f < 0.95 * ssum) {
-                    const double ginv = 1.0 / f;
-                    for (int j = tid; j < n; j += kThreads) A[(size_t)i * n + j] *= ginv;
-                    __syncthreads();
-                    for (int j = tid; j < n; j += kThreads) A[(size_t)j * n + i] *= f;
-                    if (tid == 0) sh.done = 0;
-                    __syncthreads();
-                }
-            }
-            __syncthreads();
-        }
-        // ---- 4b. Householder reduction to Hessenberg form ----
-        double* v = W + L.wr;      // reflector (length <= n) reuses the eigenvalue arrays
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int k = 0; k + 2 < n; ++k) {
-            double t = 0.0;
-            for (int i = k + 2 + tid; i < n; i += kThreads) {
-                const double q = A[(size_t)i * n + k];
-                t += q * q;
-            }
-            const double tail = bsum(sh, t);
-            if (tail == 0.0) continue;
-            const double x0 = A[(size_t)(k + 1) * n + k];
-            const double nrm2 = x0 * x0 + tail;
-            const double alpha = (x0 >= 0.0) ? -sqrt(nrm2) : sqrt(nrm2);
-            const int mm = n - k - 1;
-            const double v0 = x0 - alpha;
-            const double beta = 2.0 / (v0 * v0 + tail);
-            for (int i = tid; i < mm; i += kThreads) v[i] = (i == 0) ? v0 : A[(size_t)(k + 1 + i) * n + k];
-            __syncthreads();
-            for (int j = k + tid; j < n; j += kThreads) {          // left: columns k..n-1
-                double sacc = 0.0;
-                for (int i = 0; i < mm; ++i) sacc += v[i] * A[(size_t)(k + 1 + i) * n + j];
-                sacc *= beta;
-                for (int i = 0; i < mm; ++i) A[(size_t)(k + 1 + i) * n + j] -= sacc * v[i];
-            }
-            __syncthreads();
-            for (int i = warp; i < n; i += kThreads / 32) {        // right: all rows
-                double* row = A + (size_t)i * n + k + 1;
-                double sacc = 0.0;
-                for (int j = lane; j < mm; j += 32) sacc += row[j] * v[j];
-                for (int off = 16; off; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
-                sacc *= beta;
-                for (int j = lane; j < mm; j += 32) row[j] -= sacc * v[j];
-            }
-            __syncthreads();
-            for (int i = k + 1 + tid; i < n; i += kThreads) A[(size_t)i * n + k] = (i == k + 1) ? alpha : 0.0;
-            __syncthreads();
-        }
-        // ---- 4c. Francis double-shift QR, eigenvalues only ----
+        // ---- 4. eigenvalues: FP64, or an FP32 screen with an FP64 re-run in the guard band ----
         double* wr = W + L.wr;
         double* wi = W + L.wi;
-        {
-            double hm = 0.0;
-            for (int w = tid; w < n * n; w += kThreads) {
-                const int i = w / n, j = w % n;
-                if (j >= i - 1) hm = fmax(hm, fabs(A[w]));
-            }
-            hm = bmax(sh, hm);
-            if (tid == 0) {
-                sh.hmax = hm;
-                sh.hi = n - 1;
-                sh.its = 0;
-            }
+        double maxre = 0.0, minz = 0.0;
+        if (precision == CS_PREC_MIXED) {
+            float* A32 = reinterpret_cast<float*>(W + L.A32);
+            for (int w = tid; w < n * n; w += kThreads) A32[w] = (float)A[w];
             __syncthreads();
-        }
-        while (sh.hi >= 0) {
-            const int hi = sh.hi;
-            // locate the top of the unreduced block ending at hi: largest l <= hi with a negligible A[l][l-1]
-            int cand = 0;
-            for (int l = 1 + tid; l <= hi; l += kThreads) {
-                double sd = fabs(A[(size_t)(l - 1) * n + l - 1]) + fabs(A[(size_t)l * n + l]);
-                if (sd == 0.0) sd = sh.hmax;
-                if (fabs(A[(size_t)l * n + l - 1]) <= kEps * sd) cand = max(cand, l);
-            }
-            const int lo = bmax_int(sh, cand);
-            if (tid == 0 && lo > 0) A[(size_t)lo * n + lo - 1] = 0.0;
-            if (lo == hi) {
+            eigen_screen<float>(A32, n, reinterpret_cast<float*>(W + L.v), wr, wi, sh);
+            eig_stats(sh, n, wr, wi, maxre, minz);
+            const bool near = sh.fail || fabs(maxre) <= kGuardRe || fabs(minz - damping_min) <= kGuardZeta;
+            if (near) {                               // decision too close to call in FP32
                 if (tid == 0) {
-                    wr[hi] = A[(size_t)hi * n + hi];
-                    wi[hi] = 0.0;
-                    sh.hi = hi - 1;
-                    sh.its = 0;
+                    sh.fail = 0;
+                    atomicAdd(a.reruns, 1);
                 }
                 __syncthreads();
-                continue;
+                eigen_screen<double>(A, n, W + L.v, wr, wi, sh);
+                eig_stats(sh, n, wr, wi, maxre, minz);
             }
-            if (lo == hi - 1) {
-                if (tid == 0) {
-                    double re[2], im[2];
-                    eig2(A[(size_t)(hi - 1) * n + hi - 1], A[(size_t)(hi - 1) * n + hi], A[(size_t)hi * n + hi - 1],
-                         A[(size_t)hi * n + hi], re, im);
-                    wr[hi - 1] = re[0]; wi[hi - 1] = im[0];
-                    wr[hi] = re[1]; wi[hi] = im[1];
-                    sh.hi = hi - 2;
-                    sh.its = 0;
-                }
-                __syncthreads();
-                continue;
-            }
-            if (sh.its >= 30 * n) {
-                if (tid == 0) sh.fail = 2;
-                __syncthreads();
-                break;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                const int its = ++sh.its;
-                double sft, tft;
-                const double a11 = A[(size_t)(hi - 1) * n + hi - 1], a12 = A[(size_t)(hi - 1) * n + hi];
-                const double a21 = A[(size_t)hi * n + hi - 1], a22 = A[(size_t)hi * n + hi];
-                if (its == 10 || its == 20) {
-                    const double ww = fabs(a21) + fabs(A[(size_t)(hi - 1) * n + hi - 2]);
-                    sft = 1.5 * ww;
-                    tft = ww * ww;
-                } else {
-                    sft = a11 + a22;
-                    tft = a11 * a22 - a12 * a21;
-                }
-                const double h00 = A[(size_t)lo * n + lo], h01 = A[(size_t)lo * n + lo + 1];
-                const double h10 = A[(size_t)(lo + 1) * n + lo], h11 = A[(size_t)(lo + 1) * n + lo + 1];
-                const double h21 = A[(size_t)(lo + 2) * n + lo + 1];
-                sh.x[0] = h00 * h00 + h01 * h10 - sft * h00 + tft;
-                sh.x[1] = h10 * (h00 + h11 - sft);
-                sh.x[2] = h10 * h21;
-            }
-            __syncthreads();
-            double x0 = sh.x[0], x1 = sh.x[1], x2 = sh.x[2];
-            for (int k = lo; k <= hi - 1; ++k) {
-                const int len = (k + 2 <= hi) ? 3 : 2;
-                const double t2 = x1 * x1 + (len == 3 ? x2 * x2 : 0.0);
-                if (t2 != 0.0) {
-                    const double nrm = sqrt(x0 * x0 + t2);
-                    const double al = (x0 >= 0.0) ? -nrm : nrm;
-                    const double u0 = x0 - al, u1 = x1, u2 = (len == 3) ? x2 : 0.0;
-                    const double bt = 2.0 / (u0 * u0 + t2);
-                    const int c0 = (k > lo) ? k - 1 : lo;
-                    for (int j = c0 + tid; j <= hi; j += kThreads) {   // rows k..k+len-1
-                        double* p0 = A + (size_t)k * n + j;
-                        double d = u0 * p0[0] + u1 * p0[n];
-                        if (len == 3) d += u2 * p0[2 * n];
-                        d *= bt;
-                        p0[0] -= d * u0;
-                        p0[n] -= d * u1;
-                        if (len == 3) p0[2 * n] -= d * u2;
-                    }
-                    __syncthreads();
-                    const int r1 = (k + 3 < hi) ? k + 3 : hi;
-                    for (int i = lo + tid; i <= r1; i += kThreads) {   // columns k..k+len-1
-                        double* p0 = A + (size_t)i * n + k;
-                        double d = p0[0] * u0 + p0[1] * u1;
-                        if (len == 3) d += p0[2] * u2;
-                        d *= bt;
-                        p0[0] -= d * u0;
-                        p0[1] -= d * u1;
-                        if (len == 3) p0[2] -= d * u2;
-                    }
-                    __syncthreads();
-                }
-                if (k + 1 <= hi - 1) {
-                    x0 = A[(size_t)(k + 1) * n + k];
-                    x1 = A[(size_t)(k + 2) * n + k];
-                    x2 = (k + 3 <= hi) ? A[(size_t)(k + 3) * n + k] : 0.0;
-                }
-            }
-            for (int i = lo + 2 + tid; i <= hi; i += kThreads) {
-                A[(size_t)i * n + i - 2] = 0.0;
-                if (i >= lo + 3) A[(size_t)i * n + i - 3] = 0.0;
-            }
-            __syncthreads();
+        } else {
+            eigen_screen<double>(A, n, W + L.v, wr, wi, sh);
+            eig_stats(sh, n, wr, wi, maxre, minz);
         }
-        // ---- 5. statistics and class ----
+        // ---- 5. class ----
         {
-            double mr = -INFINITY, mz = INFINITY;
-            if (!sh.fail) {
-                for (int i = tid; i < n; i += kThreads) {
-                    mr = fmax(mr, wr[i]);
-                    const double mg = sqrt(wr[i] * wr[i] + wi[i] * wi[i]);
-                    mz = fmin(mz, mg > 0.0 ? -wr[i] / mg : 1.0);
-                }
-            }
-            const double maxre = bmax(sh, mr);
-            const double minz = -bmax(sh, -mz);
             if (tid == 0) {
                 uint8_t k;
                 if (sh.fail) k = CS_EIG_FAIL;
@@ -614,13 +657,13 @@ __global__ void record_kernel(int nbr, int nE, EvalArgs a) {
 
 size_t dyn_scratch_doubles(const DevNet& net) { return (size_t)make_dlayout(net).total; }
 
-cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double damping_min, double* scratch,
-                       size_t scratch_per_cta, int grid, int* counter, cudaStream_t s) {
+cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double damping_min, int precision,
+                       double* scratch, size_t scratch_per_cta, int grid, int* counter, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     const DLay L = make_dlayout(net);
     if ((size_t)L.total > scratch_per_cta) return cudaErrorInvalidValue;
     const size_t smem = sizeof(int) * (size_t)net.ng;
-    dyn_kernel<<<grid, kThreads, smem, s>>>(net, a, o, damping_min, scratch, scratch_per_cta, L, counter);
+    dyn_kernel<<<grid, kThreads, smem, s>>>(net, a, o, damping_min, precision, scratch, scratch_per_cta, L, counter);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.sev_n1 && a.sev_pairs) {

@@ -295,3 +295,64 @@ def test_base_case_secure_and_edges(ctx, net118):
     # the same element twice is the N-1 scenario of that element
     a = _run(ctx, nid, 0, [7, 7], [7, -1])
     assert a["klass"][0] == a["klass"][1] and a["cost"][0] == a["cost"][1]
+
+
+# ------------------------------------------------------------ mixed precision form --
+TOL_EIG_MIXED = 2e-3     # FP32 eigenvalue error bound outside the guard band (5e-3)
+
+
+@pytest.fixture(scope="module")
+def mixed118():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = cs.Context(precision=cs.PREC_MIXED)
+    net = synth.case118()
+    nid = c.load_network(net)
+    yield c, net, nid
+    c.close()
+
+
+def test_mixed_form_classes_exact_vs_golden(mixed118):
+    """FP32 eigen screen with FP64 re-runs in the guard band: classes equal the
+    oracle's, the OPF outputs are FP64 (same tolerances), the eigen statistics
+    carry the stated FP32 error."""
+    c, net, nid = mixed118
+    for name in ("case118_n1.json", "case118_pairs.json"):
+        refs = _gold(name)["scenarios"]
+        for lv in sorted({r["level"] for r in refs}):
+            sub = [r for r in refs if r["level"] == lv]
+            got = _run(c, nid, lv, [r["i"] for r in sub], [r["j"] for r in sub])
+            guard = 0
+            for q, r in enumerate(sub):
+                if int(got["klass"][q]) != r["klass"]:
+                    assert _guard(r), (name, q, r["i"], r["j"], int(got["klass"][q]), r["klass"])
+                    guard += 1
+                    continue
+                if r["klass"] in (0, 3, 4, 5):
+                    assert abs(got["cost"][q] - r["cost"]) <= TOL_COST * abs(r["cost"])
+                if r["klass"] in (0, 4, 5):
+                    assert abs(got["max_re"][q] - r["max_re"]) <= TOL_EIG_MIXED
+                    assert abs(got["min_zeta"][q] - r["min_zeta"]) <= TOL_EIG_MIXED
+            assert guard <= 2
+
+
+def test_mixed_equals_fp64_classes_full_level(ctx, net118, mixed118):
+    """Every class of a full level agrees between the two forms."""
+    net, nid = net118
+    c, _, nid2 = mixed118
+    E = net.n_elem
+    n = E * (E - 1) // 2
+    ei = torch.empty(n, dtype=torch.int32, device=DEV)
+    ej = torch.empty(n, dtype=torch.int32, device=DEV)
+    cs.enumerate_pairs_device(E, 0, n, ei, ej)
+    a = ctx.alloc_results(n, DEV)
+    b = c.alloc_results(n, DEV)
+    ctx.evaluate_device(nid, 0, ei, ej, a)
+    c.evaluate_device(nid2, 0, ei, ej, b)
+    ctx.sync()
+    c.sync()
+    np.testing.assert_array_equal(a["klass"].cpu().numpy(), b["klass"].cpu().numpy())
+    ok = (a["klass"] == 0).cpu().numpy()
+    d = np.abs(a["max_re"].cpu().numpy()[ok] - b["max_re"].cpu().numpy()[ok])
+    assert d.max() <= TOL_EIG_MIXED
+    assert c.eigen_reruns() >= 0
