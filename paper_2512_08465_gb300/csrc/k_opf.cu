@@ -28,7 +28,9 @@
 //    left-looking update lists, built on the host at load time), with the
 //    4x4 pivot blocks inverted by Gauss-Jordan with partial pivoting.  Columns
 //    of one elimination-tree level are independent, so a level is one
-//    parallel step of the CTA (16 threads per target block);
+//    parallel step of the CTA (16 threads per target block).  The narrow
+//    upper levels leave most threads at barriers, so CTAs are small (128
+//    threads) and three are resident per SM to overlap one another's waits;
 //  * every branch quantity (flows, first and second derivatives of both end
 //    powers, the weighted 4x4 Hessian) is computed once per iteration by one
 //    thread from the branch's own four voltage variables and gathered by
@@ -39,7 +41,8 @@
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;     // threads per scenario CTA
+constexpr int kCtasPerSm = 3;     // resident CTAs per SM the register budget is sized for
 constexpr int kRec = 46;     // doubles per branch record
 constexpr double kXi = 0.99995;
 constexpr double kSigma = 0.1;
@@ -459,7 +462,7 @@ struct Scal {          // per-scenario scalars in shared memory
     int scen;
 };
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
 opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, int max_it,
            double* scratch, size_t per_cta, Lay L, int* counter) {
     __shared__ RedBuf rb;
