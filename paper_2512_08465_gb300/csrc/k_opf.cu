@@ -70,7 +70,7 @@ struct Lay {
     // branch
     int zf, zt, muf, mut, hf, ht, dzf, dzt, dmuf, dmut, rec;
     // KKT: assembled blocks (Kb, Kd) kept for refinement, factor (Ub, Lb, Db, Di), vectors
-    int Kb, Kd, Ub, Lb, Db, Di, x, bv, rv;
+    int Kb, Kd, Ub, Lb, Db, Di, x, bv, rv, cs;
     long dense;                 // dense fallback matrix (4nb)^2, -1 if the network is too large
     long total;
 };
@@ -93,7 +93,7 @@ Lay make_layout(const DevNet& n) {
     o = (o + 15) & ~15;
     L.Kb = take(16 * n.nL); L.Kd = take(16 * nb);
     L.Ub = take(16 * n.nL); L.Lb = take(16 * n.nL); L.Db = take(16 * nb); L.Di = take(16 * nb);
-    L.x = take(4 * nb); L.bv = take(4 * nb); L.rv = take(4 * nb);
+    L.x = take(4 * nb); L.bv = take(4 * nb); L.rv = take(4 * nb); L.cs = take(4 * nb);
     o = (o + 31) & ~31;
     if (4 * nb <= kDenseMax) {
         L.dense = o;
@@ -375,8 +375,8 @@ struct DenseShared {
     double pv;
 };
 
-// Dense LU with partial pivoting of the assembled reduced system (order 4 nb,
-// row-major in scratch), solving for b into x.  Backstop for the Newton steps
+// Dense LU with partial pivoting of the equilibrated assembled reduced system
+// (order 4 nb, row-major in scratch), solving for b into x.  Backstop for the Newton steps
 // whose block solve did not reach the backward-error target.  Returns false
 // when a pivot column is exactly zero.
 __device__ bool dense_solve(const DevNet& net, double* W, const Lay& L, DenseShared& ds) {
@@ -397,7 +397,31 @@ __device__ bool dense_solve(const DevNet& net, double* W, const Lay& L, DenseSha
         A[(long)(4 * i + r) * N + 4 * j + c] = v;
         A[(long)(4 * j + c) * N + 4 * i + r] = v;
     }
-    for (int w = tid; w < N; w += kThreads) x[w] = W[L.bv + w];
+    // Equilibrate rows then columns by powers of two (exact): the reduced system's
+    // rows span ~1e-5..1e12 near convergence, and partial pivoting is only normwise
+    // stable, so without scaling the balance rows lose all accuracy.
+    double* rs = W + L.rv;          // row scales (the refinement residual is free here)
+    double* cs = W + L.cs;          // column scales
+    for (int i = tid; i < N; i += kThreads) {
+        double m = 0.0;
+        for (int j = 0; j < N; ++j) m = fmax(m, fabs(A[(long)i * N + j]));
+        int e;
+        frexp(m, &e);
+        rs[i] = (m > 0.0) ? ldexp(1.0, -e) : 1.0;
+    }
+    __syncthreads();
+    for (long w = tid; w < (long)N * N; w += kThreads) A[w] *= rs[w / N];
+    for (int w = tid; w < N; w += kThreads) x[w] = W[L.bv + w] * rs[w];
+    __syncthreads();
+    for (int j = tid; j < N; j += kThreads) {
+        double m = 0.0;
+        for (int i = 0; i < N; ++i) m = fmax(m, fabs(A[(long)i * N + j]));
+        int e;
+        frexp(m, &e);
+        cs[j] = (m > 0.0) ? ldexp(1.0, -e) : 1.0;
+    }
+    __syncthreads();
+    for (long w = tid; w < (long)N * N; w += kThreads) A[w] *= cs[w % N];
     __syncthreads();
     for (int k = 0; k < N; ++k) {
         double best = -1.0;
@@ -451,6 +475,8 @@ __device__ bool dense_solve(const DevNet& net, double* W, const Lay& L, DenseSha
         for (int i = tid; i < k; i += kThreads) x[i] -= A[(long)i * N + k] * xk;
         __syncthreads();
     }
+    for (int w = tid; w < N; w += kThreads) x[w] *= cs[w];     // undo the column scaling
+    __syncthreads();
     return true;
 }
 
