@@ -140,10 +140,13 @@ cs_status cs_base_result(cs_ctx* ctx, int32_t net_id, int32_t level, const cs_re
  * (a cudaStream_t, NULL = legacy default stream).  Every severity is also
  * recorded in the context's severity table of (net_id, level) that
  * cs_risk_index reads.  Sizes and ids are validated: n, net_id and level on
- * the host (CS_E_ARG); element ids on the device, where an id out of range
- * marks that record CS_EIG_FAIL-free garbage-free: the record is left with
- * class CS_OPF_NONCONV... 
- * dynamic model + eigenvalues, classification, all in the library's kernels. */
+ * the host (CS_E_ARG); element ids on the device.  A record whose ids are out
+ * of range (below -1, at or above n_branch + n_gen, or elem_i = -1 with
+ * elem_j >= 0) gets class 255, severe = 1, NaN cost and eigen statistics, is
+ * not written to the severity table, and sets a device error bit that the
+ * next cs_sync reports as CS_E_ARG.  The other records are unaffected.  Every
+ * step runs in the library's kernels: islanding, the interior-point OPF, the
+ * dynamic model + eigenvalues and the classification (Section II-B). */
 cs_status cs_evaluate_device(cs_ctx* ctx, int32_t net_id, int32_t level,
                              const int32_t* elem_i, const int32_t* elem_j, int64_t n,
                              const cs_result* out, void* stream);
