@@ -193,6 +193,21 @@ cs_status cs_risk_reduce_device(int32_t n_elem, const uint8_t* S1, const uint8_t
 cs_status cs_enumerate_pairs_device(int32_t n_elem, int64_t first, int64_t count,
                                     int32_t* elem_i, int32_t* elem_j, void* stream);
 
+/* cs_risk_index without any device allocation (the paper has no counterpart:
+ * this is a deployment variant of the Eq. 3 reduction).  Same arguments,
+ * result and errors as cs_risk_index, bit for bit.  For callers that must not
+ * call cudaMalloc/cudaFree (a serving loop whose other streams would stall on
+ * the synchronisation cudaFree implies, or a process whose device memory is
+ * reserved in full by another allocator).  Its scratch is one static device
+ * array per device sized for at most 4096 outage elements (n_branch + n_gen);
+ * larger networks are rejected with CS_E_ARG and a message naming the limit.
+ * The array's address is looked up on the first call for a device, which
+ * should come before any stream capture on that device.  All calls in the
+ * process share the array, so they are serialised by a process-wide lock;
+ * each returns after its stream has drained.  Blocking; HOST lambda, R_out. */
+cs_status cs_risk_index_static(cs_ctx* ctx, int32_t net_id, int32_t level, const double* lambda,
+                               int32_t mode, double* R_out, int64_t* n_missing);
+
 /* Measured ALU peaks of `device` for roofline reporting: independent fused
  * multiply-add chains in FP64 and FP32 timed with CUDA events, in TFLOP/s
  * (2 flops per FMA).  Host outputs.  Runs ~10 ms of GPU work. */

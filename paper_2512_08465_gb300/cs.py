@@ -29,7 +29,8 @@ PREC_FP64, PREC_MIXED = 0, 1
 EXPORTS = ("cs_default_options", "cs_create", "cs_destroy", "cs_load_network", "cs_unload_network",
            "cs_base_result", "cs_evaluate_device", "cs_sync", "cs_submit_contingencies", "cs_poll",
            "cs_risk_index", "cs_risk_reduce_device", "cs_enumerate_pairs_device", "cs_last_error",
-           "cs_last_launch_count", "cs_set_timing", "cs_kernel_times", "cs_alu_peak", "cs_eigen_reruns")
+           "cs_last_launch_count", "cs_set_timing", "cs_kernel_times", "cs_alu_peak", "cs_eigen_reruns",
+           "cs_risk_index_static")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -94,6 +95,7 @@ def load_library(build_if_missing: bool = True):
         "cs_submit_contingencies": (i32, [P, i32, i32, P, P, i64, ctypes.POINTER(u64)]),
         "cs_poll": (i32, [P, u64, i32, ctypes.POINTER(Result)]),
         "cs_risk_index": (i32, [P, i32, i32, P, i32, P, ctypes.POINTER(i64)]),
+        "cs_risk_index_static": (i32, [P, i32, i32, P, i32, P, ctypes.POINTER(i64)]),
         "cs_risk_reduce_device": (i32, [i32, P, P, P, i32, P, P]),
         "cs_enumerate_pairs_device": (i32, [i32, i64, i64, P, P, P]),
         "cs_last_error": (ctypes.c_char_p, [P]),
@@ -293,6 +295,16 @@ class Context:
         miss = ctypes.c_int64()
         st = self.lib.cs_risk_index(self.h, net_id, level, _ptr(lam), mode, _ptr(R), ctypes.byref(miss))
         self._check(st, "cs_risk_index")
+        return R, miss.value
+
+    def risk_index_static(self, net_id: int, level: int, lam, mode: int = RISK_ORDERED):
+        """cs_risk_index_static: the same reduction with its device scratch in a
+        static array (no device allocation; at most 4096 outage elements)."""
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        R = np.empty_like(lam)
+        miss = ctypes.c_int64()
+        st = self.lib.cs_risk_index_static(self.h, net_id, level, _ptr(lam), mode, _ptr(R), ctypes.byref(miss))
+        self._check(st, "cs_risk_index_static")
         return R, miss.value
 
 

@@ -705,4 +705,83 @@ cs_status cs_enumerate_pairs_device(int32_t n_elem, int64_t first, int64_t count
     return e == cudaSuccess ? CS_OK : CS_E_CUDA;
 }
 
+
+// ---------------------------------------------------------------------------
+// Risk Index without any device allocation.
+//
+// Who needs it: a caller that must not call cudaMalloc/cudaFree between its
+// own launches -- a serving loop whose other streams would stall behind the
+// device-wide synchronisation cudaFree implies, or a process whose device
+// memory is already reserved in full by another allocator (a caching
+// allocator with a memory fraction), where a fresh cudaMalloc may fail.
+// cs_risk_index allocates three small device buffers per call; this variant
+// takes them from one file-scope device array instead.
+//
+// The array holds lambda[kStaticRiskMaxElem], R[kStaticRiskMaxElem] and the
+// 64-bit missing-pair counter, which is cleared by cudaMemsetAsync before
+// every launch (the other two are fully overwritten).  Its device address is
+// looked up once per device, with that device current, on the first call for
+// it; that first call should happen before any stream capture on the device.
+// All calls in the process share the one array per device, so overlapping
+// calls would race on it: the whole call runs under a process-wide lock and
+// returns only after its stream has drained.
+constexpr int kStaticRiskMaxElem = 4096;
+constexpr int kStaticRiskDoubles = 2 * kStaticRiskMaxElem + 32;   // + counter, padded
+static __device__ __align__(256) double g_static_risk[kStaticRiskDoubles];
+
+namespace {
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+double* g_static_ptr[kStaticMaxDevices] = {};
+
+cudaError_t static_risk_scratch(int device, double** p) {
+    if (device < 0 || device >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_static_ptr[device]) {
+        void* a = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&a, g_static_risk);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[device] = (double*)a;
+    }
+    *p = g_static_ptr[device];
+    return cudaSuccess;
+}
+}  // namespace
+
+cs_status cs_risk_index_static(cs_ctx* ctx, int32_t net_id, int32_t level, const double* lambda, int32_t mode,
+                               double* R_out, int64_t* n_missing) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> glock(g_static_mu);
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    auto it = ctx->nets.find(net_id);
+    if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
+    Network* net = it->second.get();
+    if (level < 0 || level >= net->nlev || !lambda || !R_out || (mode != CS_RISK_EQ3 && mode != CS_RISK_ORDERED))
+        return fail(ctx, CS_E_ARG, "bad level, mode or NULL");
+    const int nE = net->dev.nE;
+    if (nE > kStaticRiskMaxElem)
+        return fail(ctx, CS_E_ARG, "cs_risk_index_static: " + std::to_string(nE) + " outage elements exceed its " +
+                                       std::to_string(kStaticRiskMaxElem) + "-element static scratch; use cs_risk_index");
+    for (int i = 0; i < nE; ++i)
+        if (!(lambda[i] >= std::ldexp(1.0, -30) && lambda[i] <= std::ldexp(1.0, 10)))
+            return fail(ctx, CS_E_ARG, "lambda outside [2^-30, 2^10]");
+    CS_CUDA(cudaSetDevice(ctx->device));
+    double* base = nullptr;
+    CS_CUDA(static_risk_scratch(ctx->device, &base));
+    double* dl = base;
+    double* dr = base + kStaticRiskMaxElem;
+    int64_t* dm = (int64_t*)(base + 2 * kStaticRiskMaxElem);
+    cudaStream_t s = ctx->req_stream;
+    CS_CUDA(cudaDeviceSynchronize());      // tables written by earlier evaluations on any stream
+    CS_CUDA(cudaMemcpyAsync(dl, lambda, sizeof(double) * nE, cudaMemcpyHostToDevice, s));
+    CS_CUDA(cudaMemsetAsync(dm, 0, sizeof(int64_t), s));
+    CS_CUDA(launch_risk(nE, (const uint8_t*)net->sev_n1[level]->p, (const uint8_t*)net->sev_pairs[level]->p, dl,
+                        mode, dr, dm, s));
+    CS_CUDA(cudaMemcpyAsync(R_out, dr, sizeof(double) * nE, cudaMemcpyDeviceToHost, s));
+    int64_t miss = 0;
+    CS_CUDA(cudaMemcpyAsync(&miss, dm, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CS_CUDA(cudaStreamSynchronize(s));
+    if (n_missing) *n_missing = miss;
+    return CS_OK;
+}
+
 }  // extern "C"
