@@ -373,7 +373,7 @@ def run_profile(args):
     from paper_2512_08465_gb300 import cs, synth
     dev = torch.device("cuda", 0)
     net = synth.case118()
-    ctx = cs.Context()
+    ctx = cs.Context(precision=cs.PREC_FP64 if args.fp64 else cs.PREC_MIXED)
     nid = ctx.load_network(net)
     E = net.n_elem
     n = min(args.profile, E * (E - 1) // 2)
@@ -403,6 +403,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--request", type=int, default=4096, help="scenarios per request in the e2e leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64", action="store_true", help="--profile: run the FP64 form instead of the mixed one")
     ap.add_argument("--profile", type=int, default=0, metavar="N",
                     help="profiling case for ncu: N pairs of the 70 %% level, one warm-up and one launch set, "
                          "no baseline, no e2e, prints per-kernel times")

@@ -75,7 +75,11 @@ struct cs_ctx {
     std::vector<std::unique_ptr<Request>> pool;     // finished requests kept for buffer reuse
     cudaStream_t req_stream = nullptr;
     // workspace
-    DevBuf scratch, isl, opfx, opfst, counters, err_word;
+    DevBuf scratch, isl, opfx, opfst, counters, err_word, hbuf;
+    // the workspace above is shared by every evaluation of the context: each one waits
+    // for the previous one (whatever its stream) through this event
+    cudaEvent_t ws_free = nullptr;
+    bool ws_used = false;
     int64_t launches = 0;
     // optional per-kernel timing (cs_set_timing): events around each launch
     bool timing = false;
@@ -136,11 +140,16 @@ cs_status evaluate_impl(cs_ctx* ctx, Network* net, int level, const int32_t* ei,
     CS_CUDA(ctx->opfx.ensure(sizeof(double) * nx * cn));
     CS_CUDA(ctx->opfst.ensure(sizeof(int) * cn));
     CS_CUDA(ctx->counters.ensure(sizeof(int) * 4));
+    // packed Hessenberg matrices between the two halves of the FP32 screen
+    const bool split = ctx->opt.precision == CS_PREC_MIXED && dyn_split_fits(dn, ctx->device);
+    if (split) CS_CUDA(ctx->hbuf.ensure(sizeof(float) * dyn_hbuf_stride(dn) * cn));
     if (!ctx->err_word.p) {
         CS_CUDA(ctx->err_word.ensure(sizeof(int) * 2));
         CS_CUDA(cudaMemset(ctx->err_word.p, 0, sizeof(int) * 2));
     }
     int* counters = (int*)ctx->counters.p;
+    if (!ctx->ws_free) CS_CUDA(cudaEventCreateWithFlags(&ctx->ws_free, cudaEventDisableTiming));
+    if (ctx->ws_used) CS_CUDA(cudaStreamWaitEvent(s, ctx->ws_free, 0));
     for (int64_t c0 = 0; c0 < n; c0 += chunk) {
         const int64_t m = std::min(chunk, n - c0);
         EvalArgs a{};
@@ -190,11 +199,15 @@ cs_status evaluate_impl(cs_ctx* ctx, Network* net, int level, const int32_t* ei,
                            (double*)ctx->scratch.p, per_opf, std::min<int64_t>(g_opf, m), counters, s));
         CS_CUDA(done());
         CS_CUDA(mark(2));
+        int nl = 0;
         CS_CUDA(launch_dyn(dn, a, o, ctx->opt.damping_min, ctx->opt.precision, (double*)ctx->scratch.p, per_dyn,
-                           std::min<int64_t>(g_dyn, m), counters + 1, s));
+                           std::min<int64_t>(g_dyn, m), split ? (float*)ctx->hbuf.p : nullptr, ctx->sms,
+                           counters + 1, &nl, s));
         CS_CUDA(done());
-        ctx->launches += 3 + (a.sev_n1 ? 1 : 0);
+        ctx->launches += 2 + nl;
     }
+    CS_CUDA(cudaEventRecord(ctx->ws_free, s));
+    ctx->ws_used = true;
     return CS_OK;
 }
 
@@ -240,6 +253,7 @@ cs_status cs_destroy(cs_ctx* ctx) {
     ctx->pool.clear();
     ctx->nets.clear();
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    if (ctx->ws_free) cudaEventDestroy(ctx->ws_free);
     if (ctx->req_stream) cudaStreamDestroy(ctx->req_stream);
     delete ctx;
     return CS_OK;

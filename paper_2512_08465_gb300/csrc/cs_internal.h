@@ -128,7 +128,8 @@ CS_HD bool gen_out(const Outage& o, int g) { return g == o.g0 || g == o.g1; }
 // dynamics kernel (device, chunk-sized).
 struct OpfOut {
     double* x;          // [chunk * (2 nb + 2 ng)]  Va, Vm, Pg, Qg
-    int* status;        // [chunk] 0 not run, 1 converged, 2 failed, 3 islanded
+    int* status;        // [chunk] 0 not run, 1 converged, 2 failed, 3 islanded;
+                        // small-signal screen: 6 = FP64 re-run pending, 7 = done early
 };
 
 struct EvalArgs {
@@ -149,10 +150,16 @@ cudaError_t launch_opf(const DevNet& net, const EvalArgs& a, const int* islanded
                        double tol, int max_it, double* scratch, size_t scratch_per_cta, int grid,
                        int* counter, cudaStream_t s);
 size_t opf_scratch_doubles(const DevNet& net);
+// Small-signal screen.  counters: 3 work counters (zeroed by the caller).
+// hbuf (mixed form, NULL otherwise): a.n * dyn_hbuf_stride(net) floats for the
+// packed Hessenberg matrices handed from the front kernel to the shared-memory
+// QR; only usable when dyn_split_fits(net, device).  *launches: kernels issued.
 cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double damping_min, int precision,
-                       double* scratch, size_t scratch_per_cta, int grid, int* counter,
-                       cudaStream_t s);
+                       double* scratch, size_t scratch_per_cta, int grid, float* hbuf, int sms, int* counters,
+                       int* launches, cudaStream_t s);
 size_t dyn_scratch_doubles(const DevNet& net);
+size_t dyn_hbuf_stride(const DevNet& net);
+bool dyn_split_fits(const DevNet& net, int device);
 cudaError_t launch_risk(int nE, const uint8_t* S1, const uint8_t* S2, const double* lam, int mode,
                         double* R, int64_t* missing, cudaStream_t s);
 cudaError_t launch_enumerate(int nE, int64_t first, int64_t count, int* ei, int* ej,

@@ -35,6 +35,7 @@
 // (common rotation) to which the slow common-frequency mode is nearly parallel;
 // the referred matrix (5m - 1 states) has the same eigenvalues less that zero
 // and a well-conditioned slow mode.
+#include <algorithm>
 #include <cmath>
 
 #include "cs_internal.h"
@@ -82,43 +83,16 @@ __device__ __forceinline__ void st(double* p, cplx v) { p[0] = v.re; p[1] = v.im
 struct DShared {
     double red[2][kThreads];
     int ired[kThreads];
-    double u[3];
     double x[3];
+    double xs[2][3];                 // next bulge column, double-buffered by step parity
+    double part[2][kThreads / 32];   // per-warp partial sums, double-buffered
     int lo, hi, its, fail, scen, m, nn;
     double hmax;
-    double f_bal;
-    int done;
+    double bal_f;
+    int bal_i;
 };
 
 // block reductions ---------------------------------------------------------
-__device__ double bsum(DShared& sh, double v) {
-    const int tid = threadIdx.x;
-    sh.red[0][tid] = v;
-    __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
-        if (tid < s) sh.red[0][tid] += sh.red[0][tid + s];
-        __syncthreads();
-    }
-    const double r = sh.red[0][0];
-    __syncthreads();
-    return r;
-}
-__device__ void bsum2(DShared& sh, double& a, double& b) {
-    const int tid = threadIdx.x;
-    sh.red[0][tid] = a;
-    sh.red[1][tid] = b;
-    __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
-        if (tid < s) {
-            sh.red[0][tid] += sh.red[0][tid + s];
-            sh.red[1][tid] += sh.red[1][tid + s];
-        }
-        __syncthreads();
-    }
-    a = sh.red[0][0];
-    b = sh.red[1][0];
-    __syncthreads();
-}
 __device__ int bmax_int(DShared& sh, int v) {
     const int tid = threadIdx.x;
     for (int off = 16; off; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
@@ -160,204 +134,281 @@ __device__ void eig2(double p, double q, double r, double s, double* re, double*
 }
 
 
-// Eigenvalues of the n x n row-major matrix A (overwritten) in arithmetic T:
-// balancing by powers of two, Householder Hessenberg reduction, Francis
-// double-shift QR with deflation (eigenvalues only).  v: n entries of T
-// scratch.  Results in wr/wi (double).  sh.fail = 2 if QR did not converge.
+// ---------------------------------------------------------------------------
+// Eigenvalues of a real matrix: balancing by powers of two, Householder
+// reduction to upper Hessenberg form, Francis double-shift QR with deflation
+// (eigenvalues only), as in the textbook algorithm.  A is row-major n x n in
+// global memory; cs, rs, v are n-entry shared arrays of T.
+
+// Balancing (radix 2).  Each sweep starts from exact off-diagonal column and
+// row 1-norms; within the sweep the norms are updated as rows and columns are
+// scaled (a scaling by a power of two changes the other norms by a known
+// amount), so the sequential scan over the indices needs no reduction.  One
+// thread takes each index's decision; only indices that are scaled cost a
+// pass over the matrix.
 template <typename T>
-__device__ void eigen_screen(T* A, const int n, T* v, double* wr, double* wi, DShared& sh) {
+__device__ void balance(T* A, const int n, T* cs, T* rs, DShared& sh) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        for (int j = tid; j < n; j += kThreads) {
+            T c = 0;
+            for (int i = 0; i < n; ++i)
+                if (i != j) c += fabs(A[(size_t)i * n + j]);
+            cs[j] = c;
+        }
+        for (int i = warp; i < n; i += kThreads / 32) {
+            T r = 0;
+            for (int j = lane; j < n; j += 32)
+                if (j != i) r += fabs(A[(size_t)i * n + j]);
+            for (int off = 16; off; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+            if (lane == 0) rs[i] = r;
+        }
+        __syncthreads();
+        bool changed = false;
+        int i0 = 0;
+        for (;;) {
+            if (tid == 0) {
+                int pick = -1;
+                double fpick = 1.0;
+                for (int i = i0; i < n && pick < 0; ++i) {
+                    T c = cs[i];
+                    const T r = rs[i];
+                    if (c == 0 || r == 0 || !isfinite(c) || !isfinite(r)) continue;
+                    T g = r / 2, f = 1;
+                    const T ssum = c + r;
+                    while (c < g) { f *= 2; c *= 4; }
+                    g = r * 2;
+                    while (c > g) { f /= 2; c /= 4; }
+                    if ((c + r) / f < (T)0.95 * ssum) { pick = i; fpick = (double)f; }
+                }
+                sh.bal_i = pick;
+                sh.bal_f = fpick;
+            }
+            __syncthreads();
+            const int i = sh.bal_i;
+            if (i < 0) break;
+            const T f = (T)sh.bal_f, finv = (T)(1.0 / sh.bal_f);
+            for (int j = tid; j < n; j += kThreads) {
+                if (j == i) {
+                    cs[i] *= f;
+                    rs[i] *= finv;
+                    continue;
+                }
+                const T a = A[(size_t)i * n + j], b = A[(size_t)j * n + i];
+                A[(size_t)i * n + j] = a * finv;
+                A[(size_t)j * n + i] = b * f;
+                cs[j] += fabs(a) * (finv - 1);
+                rs[j] += fabs(b) * (f - 1);
+            }
+            changed = true;
+            i0 = i + 1;
+            __syncthreads();
+        }
+        if (!changed) break;
+    }
+}
+
+// Householder reduction to upper Hessenberg form (column k: reflector from
+// rows k+1.., applied from the left to columns k+1.. and from the right to all
+// rows).  The reflector lives in shared memory.
+template <typename T>
+__device__ void hessenberg(T* A, const int n, T* v, DShared& sh) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int k = 0; k + 2 < n; ++k) {
+        T t = 0;
+        for (int i = k + 2 + tid; i < n; i += kThreads) {
+            const T q = A[(size_t)i * n + k];
+            t += q * q;
+        }
+        for (int off = 16; off; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0) sh.part[k & 1][warp] = (double)t;
+        __syncthreads();
+        T tail = 0;
+        for (int w = 0; w < kThreads / 32; ++w) tail += (T)sh.part[k & 1][w];
+        if (tail == 0) continue;               // column already reduced (uniform)
+        const T x0 = A[(size_t)(k + 1) * n + k];
+        const T nrm = sqrt(x0 * x0 + tail);
+        const T alpha = (x0 >= 0) ? -nrm : nrm;
+        const T v0 = x0 - alpha;
+        const T beta = (T)2 / (v0 * v0 + tail);
+        const int mm = n - k - 1;
+        for (int i = tid; i < mm; i += kThreads) v[i] = (i == 0) ? v0 : A[(size_t)(k + 1 + i) * n + k];
+        __syncthreads();
+        for (int j = k + 1 + tid; j < n; j += kThreads) {          // left, columns k+1..n-1
+            T* col = A + (size_t)(k + 1) * n + j;
+            T s = 0;
+#pragma unroll 8
+            for (int i = 0; i < mm; ++i) s += v[i] * col[(size_t)i * n];
+            s *= beta;
+#pragma unroll 8
+            for (int i = 0; i < mm; ++i) col[(size_t)i * n] -= s * v[i];
+        }
+        for (int i = k + 1 + tid; i < n; i += kThreads)            // column k itself
+            A[(size_t)i * n + k] = (i == k + 1) ? alpha : (T)0;
+        __syncthreads();
+        for (int i = warp; i < n; i += kThreads / 32) {            // right, all rows
+            T* row = A + (size_t)i * n + k + 1;
+            T s = 0;
+            for (int j = lane; j < mm; j += 32) s += row[j] * v[j];
+            for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            s *= beta;
+            for (int j = lane; j < mm; j += 32) row[j] -= s * v[j];
+        }
+        __syncthreads();
+    }
+}
+
+// Francis double-shift QR on the Hessenberg matrix in global memory,
+// eigenvalues only (updates restricted to the active block lo..hi).
+// sh.fail = 2 if it does not converge in 30 n sweeps.
+template <typename T>
+__device__ void hqr_global(T* A, const int n, double* wr, double* wi, DShared& sh) {
     const int tid = threadIdx.x;
     const double eps = (sizeof(T) == 8) ? kEps : 1.1920928955078125e-07;
-    // balancing by powers of two
-        if (tid == 0) sh.done = 0;
+    {
+        double hm = 0.0;
+        for (int w = tid; w < n * n; w += kThreads) {
+            const int i = w / n, j = w % n;
+            if (j >= i - 1) hm = fmax(hm, fabs((double)A[w]));
+        }
+        hm = bmax(sh, hm);
+        if (tid == 0) {
+            sh.hmax = hm;
+            sh.hi = n - 1;
+            sh.its = 0;
+        }
         __syncthreads();
-        for (int sweep = 0; !sh.done && sweep < 100; ++sweep) {   // converges in a few sweeps; capped
-            __syncthreads();
-            if (tid == 0) sh.done = 1;
-            for (int i = 0; i < n; ++i) {
-                double c = 0.0, r = 0.0;
-                for (int j = tid; j < n; j += kThreads) {
-                    if (j == i) continue;
-                    c += fabs(A[(size_t)j * n + i]);
-                    r += fabs(A[(size_t)i * n + j]);
-                }
-                bsum2(sh, c, r);
-                if (c == 0.0 || r == 0.0 || !isfinite(c) || !isfinite(r)) continue;
-                double g = r / 2.0, f = 1.0;
-                const double ssum = c + r;
-                while (c < g) { f *= 2.0; c *= 4.0; }
-                g = r * 2.0;
-                while (c > g) { f /= 2.0; c /= 4.0; }
-                if ((c + r) / f < 0.95 * ssum) {
-                    const T ginv = (T)(1.0 / f);
-                    const T fT = (T)f;
-                    for (int j = tid; j < n; j += kThreads) A[(size_t)i * n + j] *= ginv;
-                    __syncthreads();
-                    for (int j = tid; j < n; j += kThreads) A[(size_t)j * n + i] *= fT;
-                    if (tid == 0) sh.done = 0;
-                    __syncthreads();
-                }
-            }
-            __syncthreads();
+    }
+    while (sh.hi >= 0) {
+        const int hi = sh.hi;
+        // top of the unreduced block ending at hi: largest l <= hi with a negligible A[l][l-1]
+        int cand = 0;
+        for (int l = 1 + tid; l <= hi; l += kThreads) {
+            double sd = fabs((double)A[(size_t)(l - 1) * n + l - 1]) + fabs((double)A[(size_t)l * n + l]);
+            if (sd == 0.0) sd = sh.hmax;
+            if (fabs((double)A[(size_t)l * n + l - 1]) <= eps * sd) cand = max(cand, l);
         }
-    // Householder reduction to Hessenberg form
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int k = 0; k + 2 < n; ++k) {
-            double t = 0.0;
-            for (int i = k + 2 + tid; i < n; i += kThreads) {
-                const double q = (double)A[(size_t)i * n + k];
-                t += q * q;
-            }
-            const double tail = bsum(sh, t);
-            if (tail == 0.0) continue;
-            const double x0 = (double)A[(size_t)(k + 1) * n + k];
-            const double nrm2 = x0 * x0 + tail;
-            const double alpha = (x0 >= 0.0) ? -sqrt(nrm2) : sqrt(nrm2);
-            const int mm = n - k - 1;
-            const double v0 = x0 - alpha;
-            const T beta = (T)(2.0 / (v0 * v0 + tail));
-            for (int i = tid; i < mm; i += kThreads) v[i] = (i == 0) ? (T)v0 : A[(size_t)(k + 1 + i) * n + k];
-            __syncthreads();
-            for (int j = k + tid; j < n; j += kThreads) {          // left: columns k..n-1
-                T sacc = 0;
-                for (int i = 0; i < mm; ++i) sacc += v[i] * A[(size_t)(k + 1 + i) * n + j];
-                sacc *= beta;
-                for (int i = 0; i < mm; ++i) A[(size_t)(k + 1 + i) * n + j] -= sacc * v[i];
-            }
-            __syncthreads();
-            for (int i = warp; i < n; i += kThreads / 32) {        // right: all rows
-                T* row = A + (size_t)i * n + k + 1;
-                T sacc = 0;
-                for (int j = lane; j < mm; j += 32) sacc += row[j] * v[j];
-                for (int off = 16; off; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
-                sacc *= beta;
-                for (int j = lane; j < mm; j += 32) row[j] -= sacc * v[j];
-            }
-            __syncthreads();
-            for (int i = k + 1 + tid; i < n; i += kThreads) A[(size_t)i * n + k] = (i == k + 1) ? (T)alpha : (T)0;
-            __syncthreads();
-        }
-    // Francis double-shift QR, eigenvalues only
-        {
-            double hm = 0.0;
-            for (int w = tid; w < n * n; w += kThreads) {
-                const int i = w / n, j = w % n;
-                if (j >= i - 1) hm = fmax(hm, fabs((double)A[w]));
-            }
-            hm = bmax(sh, hm);
+        const int lo = bmax_int(sh, cand);
+        if (lo == hi) {
             if (tid == 0) {
-                sh.hmax = hm;
-                sh.hi = n - 1;
+                wr[hi] = A[(size_t)hi * n + hi];
+                wi[hi] = 0.0;
+                sh.hi = hi - 1;
                 sh.its = 0;
             }
             __syncthreads();
+            continue;
         }
-        while (sh.hi >= 0) {
-            const int hi = sh.hi;
-            // locate the top of the unreduced block ending at hi: largest l <= hi with a negligible A[l][l-1]
-            int cand = 0;
-            for (int l = 1 + tid; l <= hi; l += kThreads) {
-                double sd = fabs((double)A[(size_t)(l - 1) * n + l - 1]) + fabs((double)A[(size_t)l * n + l]);
-                if (sd == 0.0) sd = sh.hmax;
-                if (fabs((double)A[(size_t)l * n + l - 1]) <= eps * sd) cand = max(cand, l);
-            }
-            const int lo = bmax_int(sh, cand);
-            if (tid == 0 && lo > 0) A[(size_t)lo * n + lo - 1] = (T)0;
-            if (lo == hi) {
-                if (tid == 0) {
-                    wr[hi] = A[(size_t)hi * n + hi];
-                    wi[hi] = 0.0;
-                    sh.hi = hi - 1;
-                    sh.its = 0;
-                }
-                __syncthreads();
-                continue;
-            }
-            if (lo == hi - 1) {
-                if (tid == 0) {
-                    double re[2], im[2];
-                    eig2(A[(size_t)(hi - 1) * n + hi - 1], A[(size_t)(hi - 1) * n + hi], A[(size_t)hi * n + hi - 1],
-                         A[(size_t)hi * n + hi], re, im);
-                    wr[hi - 1] = re[0]; wi[hi - 1] = im[0];
-                    wr[hi] = re[1]; wi[hi] = im[1];
-                    sh.hi = hi - 2;
-                    sh.its = 0;
-                }
-                __syncthreads();
-                continue;
-            }
-            if (sh.its >= 30 * n) {
-                if (tid == 0) sh.fail = 2;
-                __syncthreads();
-                break;
-            }
-            __syncthreads();
+        if (lo == hi - 1) {
             if (tid == 0) {
-                const int its = ++sh.its;
-                double sft, tft;
-                const double a11 = A[(size_t)(hi - 1) * n + hi - 1], a12 = A[(size_t)(hi - 1) * n + hi];
-                const double a21 = A[(size_t)hi * n + hi - 1], a22 = A[(size_t)hi * n + hi];
-                if (its == 10 || its == 20) {
-                    const double ww = fabs(a21) + fabs(A[(size_t)(hi - 1) * n + hi - 2]);
-                    sft = 1.5 * ww;
-                    tft = ww * ww;
-                } else {
-                    sft = a11 + a22;
-                    tft = a11 * a22 - a12 * a21;
-                }
-                const double h00 = A[(size_t)lo * n + lo], h01 = A[(size_t)lo * n + lo + 1];
-                const double h10 = A[(size_t)(lo + 1) * n + lo], h11 = A[(size_t)(lo + 1) * n + lo + 1];
-                const double h21 = A[(size_t)(lo + 2) * n + lo + 1];
-                sh.x[0] = h00 * h00 + h01 * h10 - sft * h00 + tft;
-                sh.x[1] = h10 * (h00 + h11 - sft);
-                sh.x[2] = h10 * h21;
+                double re[2], im[2];
+                eig2(A[(size_t)(hi - 1) * n + hi - 1], A[(size_t)(hi - 1) * n + hi], A[(size_t)hi * n + hi - 1],
+                     A[(size_t)hi * n + hi], re, im);
+                wr[hi - 1] = re[0]; wi[hi - 1] = im[0];
+                wr[hi] = re[1]; wi[hi] = im[1];
+                sh.hi = hi - 2;
+                sh.its = 0;
             }
             __syncthreads();
-            double x0 = sh.x[0], x1 = sh.x[1], x2 = sh.x[2];
-            for (int k = lo; k <= hi - 1; ++k) {
-                const int len = (k + 2 <= hi) ? 3 : 2;
-                const double t2 = x1 * x1 + (len == 3 ? x2 * x2 : 0.0);
-                if (t2 != 0.0) {
-                    const double nrm = sqrt(x0 * x0 + t2);
-                    const double al = (x0 >= 0.0) ? -nrm : nrm;
-                    const T u0 = (T)(x0 - al), u1 = (T)x1, u2 = (len == 3) ? (T)x2 : (T)0;
-                    const T bt = (T)(2.0 / ((x0 - al) * (x0 - al) + t2));
-                    const int c0 = (k > lo) ? k - 1 : lo;
-                    for (int j = c0 + tid; j <= hi; j += kThreads) {   // rows k..k+len-1
-                        T* p0 = A + (size_t)k * n + j;
-                        T d = u0 * p0[0] + u1 * p0[n];
-                        if (len == 3) d += u2 * p0[2 * n];
-                        d *= bt;
-                        p0[0] -= d * u0;
-                        p0[n] -= d * u1;
-                        if (len == 3) p0[2 * n] -= d * u2;
-                    }
-                    __syncthreads();
-                    const int r1 = (k + 3 < hi) ? k + 3 : hi;
-                    for (int i = lo + tid; i <= r1; i += kThreads) {   // columns k..k+len-1
-                        T* p0 = A + (size_t)i * n + k;
-                        T d = p0[0] * u0 + p0[1] * u1;
-                        if (len == 3) d += p0[2] * u2;
-                        d *= bt;
-                        p0[0] -= d * u0;
-                        p0[1] -= d * u1;
-                        if (len == 3) p0[2] -= d * u2;
-                    }
-                    __syncthreads();
-                }
-                if (k + 1 <= hi - 1) {
-                    x0 = A[(size_t)(k + 1) * n + k];
-                    x1 = A[(size_t)(k + 2) * n + k];
-                    x2 = (k + 3 <= hi) ? A[(size_t)(k + 3) * n + k] : 0.0;
-                }
-            }
-            for (int i = lo + 2 + tid; i <= hi; i += kThreads) {
-                A[(size_t)i * n + i - 2] = (T)0;
-                if (i >= lo + 3) A[(size_t)i * n + i - 3] = (T)0;
-            }
-            __syncthreads();
+            continue;
         }
+        if (sh.its >= 30 * n) {
+            if (tid == 0) sh.fail = 2;
+            __syncthreads();
+            break;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const int its = ++sh.its;
+            double sft, tft;
+            const double a11 = A[(size_t)(hi - 1) * n + hi - 1], a12 = A[(size_t)(hi - 1) * n + hi];
+            const double a21 = A[(size_t)hi * n + hi - 1], a22 = A[(size_t)hi * n + hi];
+            if (its == 10 || its == 20) {              // exceptional shift
+                const double ww = fabs(a21) + fabs(A[(size_t)(hi - 1) * n + hi - 2]);
+                sft = 1.5 * ww;
+                tft = ww * ww;
+            } else {
+                sft = a11 + a22;
+                tft = a11 * a22 - a12 * a21;
+            }
+            const double h00 = A[(size_t)lo * n + lo], h01 = A[(size_t)lo * n + lo + 1];
+            const double h10 = A[(size_t)(lo + 1) * n + lo], h11 = A[(size_t)(lo + 1) * n + lo + 1];
+            const double h21 = A[(size_t)(lo + 2) * n + lo + 1];
+            sh.x[0] = h00 * h00 + h01 * h10 - sft * h00 + tft;
+            sh.x[1] = h10 * (h00 + h11 - sft);
+            sh.x[2] = h10 * h21;
+        }
+        __syncthreads();
+        double x0 = sh.x[0], x1 = sh.x[1], x2 = sh.x[2];
+        for (int k = lo; k <= hi - 1; ++k) {
+            const int len = (k + 2 <= hi) ? 3 : 2;
+            const double t2 = x1 * x1 + (len == 3 ? x2 * x2 : 0.0);
+            const bool more = (k + 1 <= hi - 1);
+            if (t2 != 0.0) {
+                const double nrm = sqrt(x0 * x0 + t2);
+                const double al = (x0 >= 0.0) ? -nrm : nrm;
+                const T u0 = (T)(x0 - al), u1 = (T)x1, u2 = (len == 3) ? (T)x2 : (T)0;
+                const T bt = (T)(2.0 / ((x0 - al) * (x0 - al) + t2));
+                const int c0 = (k > lo) ? k - 1 : lo;
+                for (int j = c0 + tid; j <= hi; j += kThreads) {   // rows k..k+len-1
+                    T* p0 = A + (size_t)k * n + j;
+                    T d = u0 * p0[0] + u1 * p0[n];
+                    if (len == 3) d += u2 * p0[2 * n];
+                    d *= bt;
+                    p0[0] -= d * u0;
+                    p0[n] -= d * u1;
+                    if (len == 3) p0[2 * n] -= d * u2;
+                }
+                __syncthreads();
+                const int r1 = (k + 3 < hi) ? k + 3 : hi;
+                for (int i = lo + tid; i <= r1; i += kThreads) {   // columns k..k+len-1
+                    T* p0 = A + (size_t)i * n + k;
+                    T d = p0[0] * u0 + p0[1] * u1;
+                    if (len == 3) d += p0[2] * u2;
+                    d *= bt;
+                    p0[0] -= d * u0;
+                    p0[1] -= d * u1;
+                    if (len == 3) p0[2] -= d * u2;
+                    if (i > k && i <= k + 3) sh.xs[k & 1][i - k - 1] = (double)p0[0];   // next bulge column
+                }
+                __syncthreads();
+                if (more) {
+                    x0 = sh.xs[k & 1][0];
+                    x1 = sh.xs[k & 1][1];
+                    x2 = (k + 3 <= hi) ? sh.xs[k & 1][2] : 0.0;
+                }
+            } else if (more) {
+                x0 = A[(size_t)(k + 1) * n + k];
+                x1 = A[(size_t)(k + 2) * n + k];
+                x2 = (k + 3 <= hi) ? (double)A[(size_t)(k + 3) * n + k] : 0.0;
+                __syncthreads();                           // all read before the next step writes column k
+            }
+        }
+        for (int i = lo + 2 + tid; i <= hi; i += kThreads) {
+            A[(size_t)i * n + i - 2] = (T)0;
+            if (i >= lo + 3) A[(size_t)i * n + i - 3] = (T)0;
+        }
+        __syncthreads();
+    }
 }
+
+template <typename T>
+__device__ void eigen_screen(T* A, const int n, T* cs, T* rs, T* v, double* wr, double* wi, DShared& sh) {
+    balance<T>(A, n, cs, rs, sh);
+    hessenberg<T>(A, n, v, sh);
+    hqr_global<T>(A, n, wr, wi, sh);
+}
+
+// ---------------------------------------------------------------------------
+// Packed Hessenberg storage for the shared-memory QR: row i keeps columns
+// max(i-3, 0)..n-1 (the Hessenberg part plus the two sub-diagonals the bulge
+// passes through).  hq_off(n, i) is the offset of row i; hq_off(n, n) the size.
+__host__ __device__ inline int hq_start(int i) { return i > 3 ? i - 3 : 0; }
+__host__ __device__ inline int hq_off(int n, int i) {
+    if (i <= 3) return n * i;
+    return 3 * n + (i - 3) * (n + 3) - (i * (i - 1) / 2 - 3);
+}
+constexpr int kHqHead = 4;          // floats before the packed matrix: the order n (int bits), padding
 
 // max Re and min damping ratio over the n eigenvalues (block-wide, result on all threads)
 __device__ void eig_stats(DShared& sh, int n, const double* wr, const double* wi, double& maxre, double& minz) {
@@ -374,11 +425,24 @@ __device__ void eig_stats(DShared& sh, int n, const double* wr, const double* wi
     minz = -bmax(sh, -mz);
 }
 
+// Kernel modes.  FULL64: FP64 screen of every converged OPF point (the FP64
+// form).  MIXED_INLINE: FP32 screen in global memory with the FP64 re-run
+// inline (mixed form, networks whose Hessenberg matrix exceeds shared memory).
+// FRONT: model, FP32 balancing and Hessenberg reduction; the packed Hessenberg
+// matrix goes to hbuf for hqr_smem_kernel.  RERUN: FP64 screen of the
+// scenarios that kernel marked (status 6).
+enum { DYN_FULL64 = 0, DYN_MIXED_INLINE = 1, DYN_FRONT = 2, DYN_RERUN = 3 };
+
+template <int kMode>
 __global__ void __launch_bounds__(kThreads)
-dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, int precision, double* scratch,
-           size_t per_cta, DLay L, int* counter) {
+dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch, size_t per_cta, DLay L,
+           float* hbuf, size_t hstride, int* counter) {
     __shared__ DShared sh;
-    extern __shared__ int gidx[];     // [ng] compact -> generator id
+    extern __shared__ double dsm[];   // [ng] ints (compact -> generator id), then cs, rs, v [5 ng] each
+    int* gidx = reinterpret_cast<int*>(dsm);
+    double* cs_d = dsm + ((net.ng + 1) >> 1);
+    double* rs_d = cs_d + 5 * net.ng;
+    double* v_d = rs_d + 5 * net.ng;
     const int tid = threadIdx.x;
     double* W = scratch + per_cta * blockIdx.x;
     const int nb = net.nb, ng = net.ng, nbr = net.nbr;
@@ -391,7 +455,7 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, int precision, 
         __syncthreads();
         const int s = sh.scen;
         if (s >= a.n) break;
-        if (o.status[s] != 1) {
+        if (o.status[s] != (kMode == DYN_RERUN ? 6 : 1)) {
             __syncthreads();
             continue;
         }
@@ -595,28 +659,59 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, int precision, 
             }
         }
         __syncthreads();
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        if (sh.fail) {                                // Y_bb singular: no model at this point
+            if (tid == 0) {
+                a.out.klass[s] = CS_EIG_FAIL;
+                a.out.severe[s] = 1;
+                a.out.max_re[s] = nan;
+                a.out.min_zeta[s] = nan;
+                if (kMode == DYN_FRONT) o.status[s] = 7;
+            }
+            __syncthreads();
+            continue;
+        }
         // ---- 4. eigenvalues: FP64, or an FP32 screen with an FP64 re-run in the guard band ----
         double* wr = W + L.wr;
         double* wi = W + L.wi;
         double maxre = 0.0, minz = 0.0;
-        if (precision == CS_PREC_MIXED) {
+        if (kMode == DYN_FRONT) {
             float* A32 = reinterpret_cast<float*>(W + L.A32);
             for (int w = tid; w < n * n; w += kThreads) A32[w] = (float)A[w];
             __syncthreads();
-            eigen_screen<float>(A32, n, reinterpret_cast<float*>(W + L.v), wr, wi, sh);
+            float* csf = reinterpret_cast<float*>(cs_d);
+            balance<float>(A32, n, csf, reinterpret_cast<float*>(rs_d), sh);
+            hessenberg<float>(A32, n, reinterpret_cast<float*>(v_d), sh);
+            float* dst = hbuf + (size_t)s * hstride;   // packed rows for the shared-memory QR
+            if (tid == 0) dst[0] = __int_as_float(n);
+            const int warp = tid >> 5, lane = tid & 31;
+            for (int i = warp; i < n; i += kThreads / 32) {
+                const int j0 = hq_start(i);
+                float* drow = dst + kHqHead + hq_off(n, i) - j0;
+                for (int j = j0 + lane; j < n; j += 32) drow[j] = A32[(size_t)i * n + j];
+            }
+            __syncthreads();
+            continue;
+        }
+        if (kMode == DYN_MIXED_INLINE) {
+            float* A32 = reinterpret_cast<float*>(W + L.A32);
+            for (int w = tid; w < n * n; w += kThreads) A32[w] = (float)A[w];
+            __syncthreads();
+            eigen_screen<float>(A32, n, reinterpret_cast<float*>(cs_d), reinterpret_cast<float*>(rs_d),
+                                reinterpret_cast<float*>(v_d), wr, wi, sh);
             eig_stats(sh, n, wr, wi, maxre, minz);
-            const bool near = sh.fail || fabs(maxre) <= kGuardRe || fabs(minz - damping_min) <= kGuardZeta;
+            const bool near = sh.fail || !(fabs(maxre) > kGuardRe) || !(fabs(minz - damping_min) > kGuardZeta);
             if (near) {                               // decision too close to call in FP32
                 if (tid == 0) {
                     sh.fail = 0;
                     atomicAdd(a.reruns, 1);
                 }
                 __syncthreads();
-                eigen_screen<double>(A, n, W + L.v, wr, wi, sh);
+                eigen_screen<double>(A, n, cs_d, rs_d, v_d, wr, wi, sh);
                 eig_stats(sh, n, wr, wi, maxre, minz);
             }
         } else {
-            eigen_screen<double>(A, n, W + L.v, wr, wi, sh);
+            eigen_screen<double>(A, n, cs_d, rs_d, v_d, wr, wi, sh);
             eig_stats(sh, n, wr, wi, maxre, minz);
         }
         // ---- 5. class ----
@@ -629,7 +724,6 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, int precision, 
                 else k = CS_SECURE;
                 a.out.klass[s] = k;
                 a.out.severe[s] = (k != CS_SECURE);
-                const double nan = __longlong_as_double(0x7ff8000000000000ll);
                 a.out.max_re[s] = sh.fail ? nan : maxre;
                 a.out.min_zeta[s] = sh.fail ? nan : minz;
             }
@@ -653,24 +747,318 @@ __global__ void record_kernel(int nbr, int nE, EvalArgs a) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// FP32 screen, second half: Francis double-shift QR of the packed Hessenberg
+// matrix held in shared memory (one scenario per CTA, one CTA per SM).  Every
+// thread carries the same loop state (lo, hi, shifts, reflector), computed
+// redundantly from shared memory in FP32, so a bulge step costs two barriers.
+// A scenario whose decision falls inside the guard band (or whose QR does not
+// converge) is marked for the FP64 re-run; the others are classified here.
+constexpr int kQrThreads = 256;
+
+__device__ __forceinline__ void eig2f(float p, float q, float r, float s, float* re, float* im) {
+    const float hm = 0.5f * (p - s);
+    const float disc = hm * hm + q * r;
+    const float mean = 0.5f * (p + s);
+    if (disc >= 0.0f) {
+        const float root = sqrtf(disc);
+        const float big = mean + (hm >= 0.0f ? root : -root);
+        const float det = p * s - q * r;
+        const float other = (big != 0.0f) ? det / big : mean - (hm >= 0.0f ? root : -root);
+        re[0] = big; im[0] = 0.0f;
+        re[1] = other; im[1] = 0.0f;
+    } else {
+        const float root = sqrtf(-disc);
+        re[0] = mean; im[0] = root;
+        re[1] = mean; im[1] = -root;
+    }
+}
+
+__global__ void __launch_bounds__(kQrThreads, 1)
+hqr_smem_kernel(EvalArgs a, OpfOut o, const float* __restrict__ hbuf, size_t hstride, int nmax,
+                double damping_min, int* counter) {
+    extern __shared__ float qsm[];
+    __shared__ float red[2][kQrThreads / 32];
+    __shared__ float xs[2][3];
+    __shared__ int scen;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float* H = qsm;                                           // hq_off(nmax, nmax) floats
+    int* rb = reinterpret_cast<int*>(qsm + ((hq_off(nmax, nmax) + 3) & ~3));   // row i at H[rb[i] + j]
+    float* wr = reinterpret_cast<float*>(rb + nmax);
+    float* wi = wr + nmax;
+    const float eps = 1.1920928955078125e-07f;
+
+    for (;;) {
+        if (tid == 0) scen = atomicAdd(counter, 1);
+        __syncthreads();
+        const int s = scen;
+        if (s >= a.n) break;
+        if (o.status[s] != 1) {
+            __syncthreads();
+            continue;
+        }
+        const float* src = hbuf + (size_t)s * hstride;
+        const int n = __float_as_int(src[0]);
+        const int hs = hq_off(n, n);
+        {
+            const float4* s4 = reinterpret_cast<const float4*>(src + kHqHead);
+            float4* d4 = reinterpret_cast<float4*>(H);
+            for (int w = tid; w < (hs >> 2); w += kQrThreads) d4[w] = s4[w];
+            for (int w = (hs & ~3) + tid; w < hs; w += kQrThreads) H[w] = src[kHqHead + w];
+        }
+        for (int i = tid; i < n; i += kQrThreads) rb[i] = hq_off(n, i) - hq_start(i);
+        __syncthreads();
+        float hmax;
+        {
+            float hm = 0.0f;
+            for (int w = tid; w < hs; w += kQrThreads) hm = fmaxf(hm, fabsf(H[w]));
+            for (int off = 16; off; off >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, off));
+            if (lane == 0) red[0][warp] = hm;
+            __syncthreads();
+            hmax = red[0][0];
+            for (int w = 1; w < kQrThreads / 32; ++w) hmax = fmaxf(hmax, red[0][w]);
+        }
+        int hi = n - 1, its = 0;
+        bool fail = false;
+        while (hi >= 0) {
+            // top of the unreduced block ending at hi (every warp scans; all agree)
+            int lo = 0;
+            for (int base = hi; base >= 1; base -= 32) {
+                const int l = base - lane;
+                bool neg = false;
+                if (l >= 1) {
+                    float sd = fabsf(H[rb[l - 1] + l - 1]) + fabsf(H[rb[l] + l]);
+                    if (sd == 0.0f) sd = hmax;
+                    neg = fabsf(H[rb[l] + l - 1]) <= eps * sd;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, neg);
+                if (m) {
+                    lo = base - (__ffs(m) - 1);
+                    break;
+                }
+            }
+            if (lo == hi) {
+                if (tid == 0) {
+                    wr[hi] = H[rb[hi] + hi];
+                    wi[hi] = 0.0f;
+                }
+                hi -= 1;
+                its = 0;
+                continue;
+            }
+            if (lo == hi - 1) {
+                if (tid == 0) {
+                    float re[2], im[2];
+                    eig2f(H[rb[hi - 1] + hi - 1], H[rb[hi - 1] + hi], H[rb[hi] + hi - 1], H[rb[hi] + hi], re, im);
+                    wr[hi - 1] = re[0]; wi[hi - 1] = im[0];
+                    wr[hi] = re[1]; wi[hi] = im[1];
+                }
+                hi -= 2;
+                its = 0;
+                continue;
+            }
+            if (its >= 30 * n) {
+                fail = true;
+                break;
+            }
+            ++its;
+            float sft, tft;
+            {
+                const float a11 = H[rb[hi - 1] + hi - 1], a12 = H[rb[hi - 1] + hi];
+                const float a21 = H[rb[hi] + hi - 1], a22 = H[rb[hi] + hi];
+                if (its == 10 || its == 20) {              // exceptional shift
+                    const float ww = fabsf(a21) + fabsf(H[rb[hi - 1] + hi - 2]);
+                    sft = 1.5f * ww;
+                    tft = ww * ww;
+                } else {
+                    sft = a11 + a22;
+                    tft = a11 * a22 - a12 * a21;
+                }
+            }
+            float x0, x1, x2;
+            {
+                const float h00 = H[rb[lo] + lo], h01 = H[rb[lo] + lo + 1];
+                const float h10 = H[rb[lo + 1] + lo], h11 = H[rb[lo + 1] + lo + 1];
+                const float h21 = H[rb[lo + 2] + lo + 1];
+                x0 = h00 * h00 + h01 * h10 - sft * h00 + tft;
+                x1 = h10 * (h00 + h11 - sft);
+                x2 = h10 * h21;
+            }
+            for (int k = lo; k <= hi - 1; ++k) {
+                const int len = (k + 2 <= hi) ? 3 : 2;
+                const float t2 = x1 * x1 + (len == 3 ? x2 * x2 : 0.0f);
+                const bool more = (k + 1 <= hi - 1);
+                if (t2 != 0.0f) {
+                    const float nrm = sqrtf(x0 * x0 + t2);
+                    const float al = (x0 >= 0.0f) ? -nrm : nrm;
+                    const float u0 = x0 - al, u1 = x1, u2 = (len == 3) ? x2 : 0.0f;
+                    const float bt = 2.0f / (u0 * u0 + t2);
+                    const int c0 = (k > lo) ? k - 1 : lo;
+                    const int b0 = rb[k], b1 = rb[k + 1], b2 = (len == 3) ? rb[k + 2] : 0;
+                    for (int j = c0 + tid; j <= hi; j += kQrThreads) {     // rows k..k+len-1
+                        const float p0 = H[b0 + j], p1 = H[b1 + j];
+                        const float p2 = (len == 3) ? H[b2 + j] : 0.0f;
+                        const float d = (u0 * p0 + u1 * p1 + u2 * p2) * bt;
+                        H[b0 + j] = p0 - d * u0;
+                        H[b1 + j] = p1 - d * u1;
+                        if (len == 3) H[b2 + j] = p2 - d * u2;
+                    }
+                    __syncthreads();
+                    const int r1 = (k + 3 < hi) ? k + 3 : hi;
+                    for (int i = lo + tid; i <= r1; i += kQrThreads) {     // columns k..k+len-1
+                        float* p = H + rb[i] + k;
+                        const float q0 = p[0], q1 = p[1];
+                        const float q2 = (len == 3) ? p[2] : 0.0f;
+                        const float d = (q0 * u0 + q1 * u1 + q2 * u2) * bt;
+                        const float n0 = q0 - d * u0;
+                        p[0] = n0;
+                        p[1] = q1 - d * u1;
+                        if (len == 3) p[2] = q2 - d * u2;
+                        if (i > k && i <= k + 3) xs[k & 1][i - k - 1] = n0;     // next bulge column
+                    }
+                    __syncthreads();
+                    if (more) {
+                        x0 = xs[k & 1][0];
+                        x1 = xs[k & 1][1];
+                        x2 = (k + 3 <= hi) ? xs[k & 1][2] : 0.0f;
+                    }
+                } else if (more) {
+                    x0 = H[rb[k + 1] + k];
+                    x1 = H[rb[k + 2] + k];
+                    x2 = (k + 3 <= hi) ? H[rb[k + 3] + k] : 0.0f;
+                    __syncthreads();                       // all read before the next step writes column k
+                }
+            }
+            for (int i = lo + 2 + tid; i <= hi; i += kQrThreads) {
+                H[rb[i] + i - 2] = 0.0f;
+                if (i >= lo + 3) H[rb[i] + i - 3] = 0.0f;
+            }
+            __syncthreads();
+        }
+        __syncthreads();                                   // wr, wi written by thread 0
+        // statistics over all eigenvalues: max Re, min damping ratio
+        float mr = -INFINITY, mz = INFINITY;
+        if (!fail) {
+            for (int i = tid; i < n; i += kQrThreads) {
+                mr = fmaxf(mr, wr[i]);
+                const float mg = sqrtf(wr[i] * wr[i] + wi[i] * wi[i]);
+                mz = fminf(mz, mg > 0.0f ? -wr[i] / mg : 1.0f);
+            }
+        }
+        for (int off = 16; off; off >>= 1) {
+            mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, off));
+            mz = fminf(mz, __shfl_xor_sync(0xffffffffu, mz, off));
+        }
+        if (lane == 0) {
+            red[0][warp] = mr;
+            red[1][warp] = mz;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float maxre = red[0][0], minz = red[1][0];
+            for (int w = 1; w < kQrThreads / 32; ++w) {
+                maxre = fmaxf(maxre, red[0][w]);
+                minz = fminf(minz, red[1][w]);
+            }
+            const bool near = fail || !(fabsf(maxre) > (float)kGuardRe) ||
+                              !(fabsf(minz - (float)damping_min) > (float)kGuardZeta);
+            if (near) {                                    // decision too close to call in FP32
+                o.status[s] = 6;
+                atomicAdd(a.reruns, 1);
+            } else {
+                uint8_t k;
+                if (maxre >= 0.0f) k = CS_SS_UNSTABLE;
+                else if (minz < damping_min) k = CS_SS_POORLY_DAMPED;
+                else k = CS_SECURE;
+                a.out.klass[s] = k;
+                a.out.severe[s] = (k != CS_SECURE);
+                a.out.max_re[s] = maxre;
+                a.out.min_zeta[s] = minz;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 size_t dyn_scratch_doubles(const DevNet& net) { return (size_t)make_dlayout(net).total; }
 
+size_t dyn_hbuf_stride(const DevNet& net) {
+    const int nmax = 5 * net.ng - 1;
+    return (size_t)kHqHead + (size_t)((hq_off(nmax, nmax) + 3) & ~3);
+}
+
+static size_t qr_smem_bytes(int nmax) {
+    return sizeof(float) * ((size_t)((hq_off(nmax, nmax) + 3) & ~3) + 3 * (size_t)nmax);
+}
+
+bool dyn_split_fits(const DevNet& net, int device) {
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return false;
+    return qr_smem_bytes(5 * net.ng - 1) + 1024 <= (size_t)optin;
+}
+
+template <int kMode>
+static cudaError_t launch_mode(const DevNet& net, const EvalArgs& a, OpfOut o, double damping_min, double* scratch,
+                               size_t per_cta, const DLay& L, float* hbuf, size_t hstride, int grid, int* counter,
+                               cudaStream_t s) {
+    const size_t smem = sizeof(double) * ((size_t)((net.ng + 1) >> 1) + 15 * (size_t)net.ng);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(dyn_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dyn_kernel<kMode><<<grid, kThreads, smem, s>>>(net, a, o, damping_min, scratch, per_cta, L, hbuf, hstride, counter);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double damping_min, int precision,
-                       double* scratch, size_t scratch_per_cta, int grid, int* counter, cudaStream_t s) {
+                       double* scratch, size_t scratch_per_cta, int grid, float* hbuf, int sms, int* counters,
+                       int* launches, cudaStream_t s) {
+    *launches = 0;
     if (a.n <= 0) return cudaSuccess;
     const DLay L = make_dlayout(net);
     if ((size_t)L.total > scratch_per_cta) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(int) * (size_t)net.ng;
-    dyn_kernel<<<grid, kThreads, smem, s>>>(net, a, o, damping_min, precision, scratch, scratch_per_cta, L, counter);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if (precision == CS_PREC_MIXED && hbuf) {
+        // FP32 screen split in two: front (model, balancing, Hessenberg) at several CTAs
+        // per SM, then the QR from shared memory at one CTA per SM, then the FP64 re-run
+        // of the scenarios the FP32 screen cannot decide.
+        const size_t hstride = dyn_hbuf_stride(net);
+        e = launch_mode<DYN_FRONT>(net, a, o, damping_min, scratch, scratch_per_cta, L, hbuf, hstride, grid,
+                                   counters, s);
+        if (e != cudaSuccess) return e;
+        const int nmax = 5 * net.ng - 1;
+        const size_t qsm = qr_smem_bytes(nmax);
+        e = cudaFuncSetAttribute(hqr_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
+        if (e != cudaSuccess) return e;
+        const int gq = (int)std::min<int64_t>((int64_t)sms, a.n);
+        hqr_smem_kernel<<<gq, kQrThreads, qsm, s>>>(a, o, hbuf, hstride, nmax, damping_min, counters + 1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = launch_mode<DYN_RERUN>(net, a, o, damping_min, scratch, scratch_per_cta, L, nullptr, 0, grid,
+                                   counters + 2, s);
+        if (e != cudaSuccess) return e;
+        *launches = 3;
+    } else if (precision == CS_PREC_MIXED) {
+        e = launch_mode<DYN_MIXED_INLINE>(net, a, o, damping_min, scratch, scratch_per_cta, L, nullptr, 0, grid,
+                                          counters, s);
+        if (e != cudaSuccess) return e;
+        *launches = 1;
+    } else {
+        e = launch_mode<DYN_FULL64>(net, a, o, damping_min, scratch, scratch_per_cta, L, nullptr, 0, grid,
+                                    counters, s);
+        if (e != cudaSuccess) return e;
+        *launches = 1;
+    }
     if (a.sev_n1 && a.sev_pairs) {
         int blocks = (a.n + 255) / 256;
         if (blocks > 4096) blocks = 4096;
         record_kernel<<<blocks, 256, 0, s>>>(net.nbr, net.nE, a);
         e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        *launches += 1;
     }
-    return e;
+    return cudaSuccess;
 }
