@@ -128,7 +128,7 @@ cs_status evaluate_impl(cs_ctx* ctx, Network* net, int level, const int32_t* ei,
     const int64_t chunk = ctx->opt.chunk > 0 ? ctx->opt.chunk : 16384;
     const int64_t cn = std::min<int64_t>(n, chunk);
     // grids: persistent kernels sized from occupancy, capped per SM
-    const int cap_opf = ctx->opt.ctas_per_sm > 0 ? ctx->opt.ctas_per_sm : 3;
+    const int cap_opf = ctx->opt.ctas_per_sm > 0 ? ctx->opt.ctas_per_sm : opf_ctas_per_sm();
     const int cap_dyn = ctx->opt.ctas_per_sm > 0 ? ctx->opt.ctas_per_sm : 2;
     const int g_opf = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->sms * cap_opf, cn));
     const int g_dyn = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->sms * cap_dyn, cn));

@@ -150,6 +150,7 @@ cudaError_t launch_opf(const DevNet& net, const EvalArgs& a, const int* islanded
                        double tol, int max_it, double* scratch, size_t scratch_per_cta, int grid,
                        int* counter, cudaStream_t s);
 size_t opf_scratch_doubles(const DevNet& net);
+int opf_ctas_per_sm();       // resident OPF CTAs per SM the kernel is built for
 // Small-signal screen.  counters: 3 work counters (zeroed by the caller).
 // hbuf (mixed form, NULL otherwise): a.n * dyn_hbuf_stride(net) floats for the
 // packed Hessenberg matrices handed from the front kernel to the shared-memory

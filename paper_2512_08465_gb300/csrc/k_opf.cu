@@ -41,16 +41,24 @@
 
 namespace {
 
-constexpr int kThreads = 128;     // threads per scenario CTA
-constexpr int kCtasPerSm = 3;     // resident CTAs per SM the register budget is sized for
+#ifndef CS_OPF_THREADS
+#define CS_OPF_THREADS 128
+#endif
+#ifndef CS_OPF_CTAS
+#define CS_OPF_CTAS 3
+#endif
+constexpr int kThreads = CS_OPF_THREADS;   // threads per scenario CTA
+constexpr int kCtasPerSm = CS_OPF_CTAS;    // resident CTAs per SM the register budget is sized for
+constexpr int kWarps = kThreads / 32;
 constexpr int kRec = 46;     // doubles per branch record
 constexpr double kXi = 0.99995;
 constexpr double kSigma = 0.1;
 constexpr double kLimitTol = 1e-6;
 constexpr int kRefineSteps = 3;              // FP64 iterative refinement steps per Newton solve (at most)
-constexpr double kRefineStop = 0x1p-50;      // stop when the correction is below 2^-50 of the solution
+constexpr double kRefineTol = 4.0 * 2.220446049250313e-16;   // refinement done: backward error at rounding level
 constexpr double kBackwardTol = 1e-13;       // componentwise backward error accepted from the block solve
 constexpr int kDenseMax = 1024;              // dense fallback for reduced systems up to this order
+constexpr int kGmresM = 8;                   // GMRES iterations per Newton solve (at most)
 
 // record layout
 constexpr int R_DSF = 0, R_DST = 8, R_GF = 16, R_GT = 20, R_H = 24, R_LG = 34, R_NG = 38, R_SF = 42, R_ST = 44;
@@ -71,6 +79,7 @@ struct Lay {
     int zf, zt, muf, mut, hf, ht, dzf, dzt, dmuf, dmut, rec;
     // KKT: assembled blocks (Kb, Kd) kept for refinement, factor (Ub, Lb, Db, Di), vectors
     int Kb, Kd, Ub, Lb, Db, Di, x, bv, rv, cs;
+    int kv, kz, gx0, gxb, gr;   // GMRES: Krylov basis, preconditioned basis, start, best iterate, work
     long dense;                 // dense fallback matrix (4nb)^2, -1 if the network is too large
     long total;
 };
@@ -94,6 +103,8 @@ Lay make_layout(const DevNet& n) {
     L.Kb = take(16 * n.nL); L.Kd = take(16 * nb);
     L.Ub = take(16 * n.nL); L.Lb = take(16 * n.nL); L.Db = take(16 * nb); L.Di = take(16 * nb);
     L.x = take(4 * nb); L.bv = take(4 * nb); L.rv = take(4 * nb); L.cs = take(4 * nb);
+    L.kv = take(4 * nb * (kGmresM + 1)); L.kz = take(4 * nb * kGmresM);
+    L.gx0 = take(4 * nb); L.gxb = take(4 * nb); L.gr = take(4 * nb);
     o = (o + 31) & ~31;
     if (4 * nb <= kDenseMax) {
         L.dense = o;
@@ -108,25 +119,39 @@ Lay make_layout(const DevNet& n) {
 
 // ------------------------------------------------------------------ helpers --
 struct RedBuf {
-    double v[10][kThreads];
+    double v[10][kWarps];
 };
 
-// reduce K values per thread: ops[k] = 0 max, 1 sum, 2 min.  Result broadcast in out[].
+__device__ __forceinline__ double red_op(int op, double a, double b) {
+    return op == 1 ? a + b : (op == 0 ? fmax(a, b) : fmin(a, b));
+}
+
+// reduce K values per thread: ops[k] = 0 max, 1 sum, 2 min.  Result broadcast in out[]
+// (shared).  Warp shuffles, then one pass over the per-warp results.
 template <int K>
 __device__ void block_reduce(RedBuf& rb, double (&val)[K], const int (&ops)[K], double* out) {
-    const int tid = threadIdx.x;
-    for (int k = 0; k < K; ++k) rb.v[k][tid] = val[k];
-    __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
-        if (tid < s) {
-            for (int k = 0; k < K; ++k) {
-                double a = rb.v[k][tid], b = rb.v[k][tid + s];
-                rb.v[k][tid] = ops[k] == 1 ? a + b : (ops[k] == 0 ? fmax(a, b) : fmin(a, b));
-            }
-        }
-        __syncthreads();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int k = 0; k < K; ++k) {
+        double v = val[k];
+        for (int off = 16; off; off >>= 1) v = red_op(ops[k], v, __shfl_xor_sync(0xffffffffu, v, off));
+        val[k] = v;
     }
-    if (tid < K) out[tid] = rb.v[tid][0];
+    if (kWarps == 1) {
+        if (tid == 0)
+            for (int k = 0; k < K; ++k) out[k] = val[k];
+        __syncthreads();
+        return;
+    }
+    if (lane == 0)
+        for (int k = 0; k < K; ++k) rb.v[k][warp] = val[k];
+    __syncthreads();
+    if (tid == 0) {
+        for (int k = 0; k < K; ++k) {
+            double v = rb.v[k][0];
+            for (int w = 1; w < kWarps; ++w) v = red_op(ops[k], v, rb.v[k][w]);
+            out[k] = v;
+        }
+    }
     __syncthreads();
 }
 
@@ -317,32 +342,10 @@ __device__ void ldl_solve(const DevNet& net, const double* W, const Lay& L, doub
     }
 }
 
-// r = b - K x with the assembled (unfactored) blocks, one thread per (bus, row).
-__device__ void kkt_residual(const DevNet& net, const double* W, const Lay& L, const double* x, double* r) {
-    const int tid = threadIdx.x, nb = net.nb;
-    for (int w = tid; w < 4 * nb; w += kThreads) {
-        const int i = w >> 2, rr = w & 3;
-        const double* Kd = W + L.Kd + 16 * i + 4 * rr;
-        const double* xi = x + 4 * i;
-        double acc = W[L.bv + w] - (Kd[0] * xi[0] + Kd[1] * xi[1] + Kd[2] * xi[2] + Kd[3] * xi[3]);
-        for (int e = net.Lrowptr[i]; e < net.Lrowptr[i + 1]; ++e) {        // blocks (i, k), k < i
-            const double* Kq = W + L.Kb + 16 * net.Lrowblk[e] + 4 * rr;
-            const double* xk = x + 4 * net.Lrowcol[e];
-            acc -= Kq[0] * xk[0] + Kq[1] * xk[1] + Kq[2] * xk[2] + Kq[3] * xk[3];
-        }
-        for (int e = net.Lcolptr[i]; e < net.Lcolptr[i + 1]; ++e) {        // blocks (j, i)^T, j > i
-            const double* Kq = W + L.Kb + 16 * e + rr;
-            const double* xj = x + 4 * net.Lrow[e];
-            acc -= Kq[0] * xj[0] + Kq[4] * xj[1] + Kq[8] * xj[2] + Kq[12] * xj[3];
-        }
-        r[w] = acc;
-    }
-    __syncthreads();
-}
-
-// Componentwise backward error of x: max_i |b - K x|_i / (|K| |x| + |b|)_i (per thread,
-// to be max-reduced by the caller).
-__device__ double kkt_backward_error(const DevNet& net, const double* W, const Lay& L, const double* x) {
+// r = b - K x with the assembled (unfactored) blocks, one thread per (bus, row),
+// and the componentwise backward error of x, max_i |r_i| / (|K| |x| + |b|)_i
+// (returned per thread, to be max-reduced by the caller).
+__device__ double kkt_residual(const DevNet& net, const double* W, const Lay& L, const double* x, double* r) {
     const int tid = threadIdx.x, nb = net.nb;
     double worst = 0.0;
     for (int w = tid; w < 4 * nb; w += kThreads) {
@@ -350,27 +353,188 @@ __device__ double kkt_backward_error(const DevNet& net, const double* W, const L
         const double* Kd = W + L.Kd + 16 * i + 4 * rr;
         const double* xi = x + 4 * i;
         const double bw = W[L.bv + w];
-        double r = bw, sc = fabs(bw);
-        for (int c = 0; c < 4; ++c) { r -= Kd[c] * xi[c]; sc += fabs(Kd[c] * xi[c]); }
+        double acc = bw, sc = fabs(bw);
+        for (int c = 0; c < 4; ++c) {
+            const double t = Kd[c] * xi[c];
+            acc -= t;
+            sc += fabs(t);
+        }
+        for (int e = net.Lrowptr[i]; e < net.Lrowptr[i + 1]; ++e) {        // blocks (i, k), k < i
+            const double* Kq = W + L.Kb + 16 * net.Lrowblk[e] + 4 * rr;
+            const double* xk = x + 4 * net.Lrowcol[e];
+            for (int c = 0; c < 4; ++c) {
+                const double t = Kq[c] * xk[c];
+                acc -= t;
+                sc += fabs(t);
+            }
+        }
+        for (int e = net.Lcolptr[i]; e < net.Lcolptr[i + 1]; ++e) {        // blocks (j, i)^T, j > i
+            const double* Kq = W + L.Kb + 16 * e + rr;
+            const double* xj = x + 4 * net.Lrow[e];
+            for (int c = 0; c < 4; ++c) {
+                const double t = Kq[4 * c] * xj[c];
+                acc -= t;
+                sc += fabs(t);
+            }
+        }
+        r[w] = acc;
+        const double be = (sc > 0.0) ? fabs(acc) / sc : (acc == 0.0 ? 0.0 : INFINITY);
+        worst = fmax(worst, isfinite(be) ? be : INFINITY);
+    }
+    __syncthreads();
+    return worst;
+}
+
+// y = K x with the assembled blocks (x, y: 4-vectors per bus, new order).
+__device__ void kkt_matvec(const DevNet& net, const double* W, const Lay& L, const double* x, double* y) {
+    const int tid = threadIdx.x, nb = net.nb;
+    for (int w = tid; w < 4 * nb; w += kThreads) {
+        const int i = w >> 2, rr = w & 3;
+        const double* Kd = W + L.Kd + 16 * i + 4 * rr;
+        const double* xi = x + 4 * i;
+        double acc = Kd[0] * xi[0] + Kd[1] * xi[1] + Kd[2] * xi[2] + Kd[3] * xi[3];
         for (int e = net.Lrowptr[i]; e < net.Lrowptr[i + 1]; ++e) {
             const double* Kq = W + L.Kb + 16 * net.Lrowblk[e] + 4 * rr;
             const double* xk = x + 4 * net.Lrowcol[e];
-            for (int c = 0; c < 4; ++c) { r -= Kq[c] * xk[c]; sc += fabs(Kq[c] * xk[c]); }
+            acc += Kq[0] * xk[0] + Kq[1] * xk[1] + Kq[2] * xk[2] + Kq[3] * xk[3];
         }
         for (int e = net.Lcolptr[i]; e < net.Lcolptr[i + 1]; ++e) {
             const double* Kq = W + L.Kb + 16 * e + rr;
             const double* xj = x + 4 * net.Lrow[e];
-            for (int c = 0; c < 4; ++c) { r -= Kq[4 * c] * xj[c]; sc += fabs(Kq[4 * c] * xj[c]); }
+            acc += Kq[0] * xj[0] + Kq[4] * xj[1] + Kq[8] * xj[2] + Kq[12] * xj[3];
         }
-        const double be = (sc > 0.0) ? fabs(r) / sc : (r == 0.0 ? 0.0 : INFINITY);
-        worst = fmax(worst, isfinite(be) ? be : INFINITY);
+        y[w] = acc;
     }
-    return worst;
+    __syncthreads();
+}
+
+struct GmresShared {
+    double H[kGmresM + 1][kGmresM];
+    double g[kGmresM + 1], c[kGmresM], s[kGmresM], y[kGmresM];
+};
+
+// GMRES on K d = r, right-preconditioned by the block LDL^T factors, starting
+// from the current solution x (r = b - K x in rv, omega0 its backward error).
+// When the pivot blocks are nearly singular, the factors are exact except in
+// a subspace of small dimension, so a few Krylov steps remove what plain
+// refinement cannot.  Arnoldi with classical Gram-Schmidt applied twice; the
+// candidate solution is formed and its componentwise backward error checked
+// after every step; x ends as the best candidate.  Returns its backward error.
+__device__ double kkt_gmres(const DevNet& net, double* W, const Lay& L, RedBuf& rb, double* red, GmresShared& gs,
+                            double omega0) {
+    const int tid = threadIdx.x, N = 4 * net.nb;
+    double* x = W + L.x;
+    double* x0 = W + L.gx0;
+    double* xb = W + L.gxb;
+    double* V = W + L.kv;
+    double* Z = W + L.kz;
+    double* t = W + L.gr;
+    const int ops_sum[1] = {1}, ops_max[1] = {0};
+    int ops_h[kGmresM + 1];
+    for (int i = 0; i <= kGmresM; ++i) ops_h[i] = 1;
+    {
+        double ss = 0.0;
+        for (int w = tid; w < N; w += kThreads) {
+            x0[w] = x[w];
+            xb[w] = x[w];
+            const double rw = W[L.rv + w];
+            ss += rw * rw;
+        }
+        double v1[1] = {ss};
+        block_reduce<1>(rb, v1, ops_sum, red);
+    }
+    const double beta = sqrt(red[0]);
+    if (!(beta > 0.0) || !isfinite(beta)) return omega0;
+    for (int w = tid; w < N; w += kThreads) V[w] = W[L.rv + w] / beta;
+    if (tid == 0) {
+        for (int i = 0; i <= kGmresM; ++i) gs.g[i] = 0.0;
+        gs.g[0] = beta;
+    }
+    __syncthreads();
+    double best = omega0;
+    for (int j = 0; j < kGmresM; ++j) {
+        double* zj = Z + (size_t)j * N;
+        for (int w = tid; w < N; w += kThreads) zj[w] = V[(size_t)j * N + w];
+        __syncthreads();
+        ldl_solve(net, W, L, zj);
+        kkt_matvec(net, W, L, zj, t);
+        for (int pass = 0; pass < 2; ++pass) {              // classical Gram-Schmidt, twice
+            double h[kGmresM + 1];
+            for (int i = 0; i <= kGmresM; ++i) h[i] = 0.0;
+            for (int w = tid; w < N; w += kThreads) {
+                const double tw = t[w];
+#pragma unroll
+                for (int i = 0; i <= kGmresM; ++i)
+                    if (i <= j) h[i] += V[(size_t)i * N + w] * tw;
+            }
+            block_reduce<kGmresM + 1>(rb, h, ops_h, red);
+            for (int w = tid; w < N; w += kThreads) {
+                double tw = t[w];
+#pragma unroll
+                for (int i = 0; i <= kGmresM; ++i)
+                    if (i <= j) tw -= red[i] * V[(size_t)i * N + w];
+                t[w] = tw;
+            }
+            if (tid == 0)
+                for (int i = 0; i <= j; ++i) gs.H[i][j] = (pass == 0 ? 0.0 : gs.H[i][j]) + red[i];
+            __syncthreads();
+        }
+        double hn;
+        {
+            double ss = 0.0;
+            for (int w = tid; w < N; w += kThreads) ss += t[w] * t[w];
+            double v1[1] = {ss};
+            block_reduce<1>(rb, v1, ops_sum, red);
+            hn = sqrt(red[0]);
+        }
+        if (tid == 0) {                                     // Givens rotations, least-squares solve
+            gs.H[j + 1][j] = hn;
+            for (int i = 0; i < j; ++i) {
+                const double a0 = gs.H[i][j], a1 = gs.H[i + 1][j];
+                gs.H[i][j] = gs.c[i] * a0 + gs.s[i] * a1;
+                gs.H[i + 1][j] = -gs.s[i] * a0 + gs.c[i] * a1;
+            }
+            const double d = hypot(gs.H[j][j], gs.H[j + 1][j]);
+            gs.c[j] = (d > 0.0) ? gs.H[j][j] / d : 1.0;
+            gs.s[j] = (d > 0.0) ? gs.H[j + 1][j] / d : 0.0;
+            gs.H[j][j] = d;
+            gs.H[j + 1][j] = 0.0;
+            gs.g[j + 1] = -gs.s[j] * gs.g[j];
+            gs.g[j] = gs.c[j] * gs.g[j];
+            for (int i = j; i >= 0; --i) {
+                double acc = gs.g[i];
+                for (int k = i + 1; k <= j; ++k) acc -= gs.H[i][k] * gs.y[k];
+                gs.y[i] = (gs.H[i][i] != 0.0) ? acc / gs.H[i][i] : 0.0;
+            }
+        }
+        __syncthreads();
+        if (hn > 0.0)
+            for (int w = tid; w < N; w += kThreads) V[(size_t)(j + 1) * N + w] = t[w] / hn;
+        for (int w = tid; w < N; w += kThreads) {
+            double xw = x0[w];
+            for (int i = 0; i <= j; ++i) xw += gs.y[i] * Z[(size_t)i * N + w];
+            x[w] = xw;
+        }
+        __syncthreads();
+        double v1[1] = {kkt_residual(net, W, L, x, t)};
+        block_reduce<1>(rb, v1, ops_max, red);
+        const double om = red[0];
+        if (om < best) {
+            best = om;
+            for (int w = tid; w < N; w += kThreads) xb[w] = x[w];
+        }
+        if (om <= kBackwardTol || !(hn > 0.0)) break;
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int w = tid; w < N; w += kThreads) x[w] = xb[w];
+    __syncthreads();
+    return best;
 }
 
 struct DenseShared {
-    double val[kThreads / 32];
-    int idx[kThreads / 32];
+    double val[kWarps];
+    int idx[kWarps];
     int piv;
     double pv;
 };
@@ -782,28 +946,22 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
             // near convergence some pivot blocks become nearly singular (a load bus whose
             // voltage sits at a bound has one free local variable for two balance rows),
             // which leaves a low-rank error in the first solve that refinement removes.
+            // Refinement stops once the componentwise backward error is at rounding level.
             ldl_solve(net, W, L, W + L.x);
-            for (int ref_step = 0; ref_step < kRefineSteps; ++ref_step) {
-                kkt_residual(net, W, L, W + L.x, W + L.rv);
-                ldl_solve(net, W, L, W + L.rv);
-                double dmax = 0.0, xmax = 0.0;
-                for (int w = tid; w < 4 * nb; w += kThreads) {
-                    const double d = W[L.rv + w];
-                    const double xn = W[L.x + w] + d;
-                    W[L.x + w] = xn;
-                    dmax = fmax(dmax, fabs(d));
-                    xmax = fmax(xmax, fabs(xn));
-                }
-                double v2[2] = {dmax, xmax};
-                const int ops2[2] = {0, 0};
-                block_reduce<2>(rb, v2, ops2, sc.red);
-                if (!(sc.red[0] > kRefineStop * sc.red[1])) break;     // correction negligible (or NaN: caught below)
-            }
-            if (L.dense >= 0) {
-                double v1[1] = {kkt_backward_error(net, W, L, W + L.x)};
+            for (int ref_step = 0;; ++ref_step) {
+                double v1[1] = {kkt_residual(net, W, L, W + L.x, W + L.rv)};
                 const int ops1[1] = {0};
                 block_reduce<1>(rb, v1, ops1, sc.red);
-                if (!(sc.red[0] <= kBackwardTol)) {
+                if (sc.red[0] <= kRefineTol || ref_step == kRefineSteps) break;   // NaN: refine, then caught below
+                ldl_solve(net, W, L, W + L.rv);
+                for (int w = tid; w < 4 * nb; w += kThreads) W[L.x + w] += W[L.rv + w];
+                __syncthreads();
+            }
+            if (!(sc.red[0] <= kBackwardTol)) {
+                // Krylov steps on the factors, then, if those stall, the dense backstop
+                __shared__ GmresShared gs;
+                const double om = kkt_gmres(net, W, L, rb, sc.red, gs, sc.red[0]);
+                if (L.dense >= 0 && !(om <= kBackwardTol)) {
                     __shared__ DenseShared ds;
                     if (!dense_solve(net, W, L, ds)) sc.fail = 1;
                     __syncthreads();
@@ -1003,6 +1161,8 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
 }
 
 }  // namespace
+
+int opf_ctas_per_sm() { return kCtasPerSm; }
 
 size_t opf_scratch_doubles(const DevNet& net) { return (size_t)make_layout(net).total; }
 
