@@ -179,12 +179,19 @@ def _algorithmic_flops(net, res_lv, E, mixed_reruns=0):
     return tot
 
 
-def _opf_flops_per_iter(ctx_sym):
-    """Algorithmic FP64 flops of one interior-point iteration on the 118-bus
-    network: block factorisation (1,857 block updates x 128 + 464 L blocks x 128
-    + 118 pivot inverses x ~200), one solve (2 x 464 x 32 + 118 x 32), branch
-    derivatives (186 x ~1,200)."""
-    return 1857 * 128 + 464 * 128 + 118 * 200 + 2 * 464 * 32 + 118 * 32 + 186 * 1200
+def _opf_flops_per_iter(st):
+    """Algorithmic FP64 flops of one interior-point iteration, from the sizes of
+    the network's symbolic analysis (cs_network_stats): block factorisation
+    (each 4x4 block update and each L = U D^-1 block is 64 FMA, each pivot
+    inverse ~200 flops), one block solve (two 4x4 mat-vecs per L block, one per
+    pivot), one residual with its backward error (one 4x4 mat-vec per stored
+    block, both triangles), and the branch flows with their first and second
+    derivatives (~1,200 flops per branch)."""
+    nb, nl, nu, nbr = st["n_bus"], st["l_blocks"], st["block_updates"], st["n_branch"]
+    factor = nu * 128 + nl * 128 + nb * 200
+    solve = 2 * nl * 32 + nb * 32
+    residual = (2 * nl + nb) * 32
+    return factor + solve + residual + nbr * 1200
 
 
 def run_ours(args):
@@ -289,17 +296,21 @@ def run_ours(args):
         roof = {"kernel": "opf_kernel (interior-point OPF: branch derivatives, block LDL^T, refined solves)",
                 "bound": "alu", "unit": "TFLOP/s", "peak": peak64,
                 "peak_source": "measured in this run: FP64 FMA-chain probe (cs_alu_peak), all SMs",
-                "work": "per interior-point iteration ~5.8e5 FP64 flops (factorisation + one solve + branch "
-                        "derivatives), times the iterations each scenario took"}
+                "work": "per interior-point iteration: block factorisation + one block solve + one residual "
+                        "+ branch derivatives, counted from the symbolic analysis (cs_network_stats), times the "
+                        "iterations each scenario took"}
     else:
-        roof = {"kernel": "dyn_kernel (Kron + state matrix + Hessenberg + Francis QR)", "bound": "alu",
+        roof = {"kernel": "small-signal kernels (Kron + state matrix + Hessenberg; shared-memory Francis QR)",
+                "bound": "alu",
                 "unit": "TFLOP/s", "peak": peak32,
                 "peak_source": "measured in this run: FP32 FMA-chain probe (cs_alu_peak), all SMs",
                 "work": "10 n^3 flops per converged scenario, n = 5 x in-service generators - 1"}
     # achieved work of the dominant kernel per step
     if dominant == "opf":
-        roof["achieved"] = mixed["iters"] * _opf_flops_per_iter(None) / (kms["opf"] / args.steps / 1e3) / 1e12
+        fl = _opf_flops_per_iter(ctx_m.network_stats(nid_m))
+        roof["achieved"] = mixed["iters"] * fl / (kms["opf"] / args.steps / 1e3) / 1e12
         roof["iterations_per_step"] = mixed["iters"]
+        roof["flops_per_iteration"] = fl
     else:
         roof["achieved"] = _algorithmic_flops(net, mixed["klass"], E) / (kms["dyn"] / args.steps / 1e3) / 1e12
     roof.update({"launches_per_step": kcnt[dominant] / args.steps,

@@ -131,6 +131,14 @@ cs_status cs_destroy(cs_ctx* ctx);
 cs_status cs_load_network(cs_ctx* ctx, const cs_network_desc* net, int32_t* net_id);
 cs_status cs_unload_network(cs_ctx* ctx, int32_t net_id);
 
+/* Sizes of a loaded network and of its symbolic analysis (Section II-A step 1),
+ * for work accounting: stats[0..7] = n_bus, n_branch, n_gen, off-diagonal
+ * 4x4 blocks of L (and of the bus-level KKT pattern below the diagonal),
+ * block updates of one numeric factorisation, elimination-tree levels,
+ * largest state-matrix order (5 n_gen - 1), load levels.  The first n_stats
+ * entries are written (HOST array). */
+cs_status cs_network_stats(cs_ctx* ctx, int32_t net_id, int64_t* stats, int32_t n_stats);
+
 /* Base-case result of a level (host out, one record). */
 cs_status cs_base_result(cs_ctx* ctx, int32_t net_id, int32_t level, const cs_result* out);
 

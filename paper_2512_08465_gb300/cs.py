@@ -30,7 +30,7 @@ EXPORTS = ("cs_default_options", "cs_create", "cs_destroy", "cs_load_network", "
            "cs_base_result", "cs_evaluate_device", "cs_sync", "cs_submit_contingencies", "cs_poll",
            "cs_risk_index", "cs_risk_reduce_device", "cs_enumerate_pairs_device", "cs_last_error",
            "cs_last_launch_count", "cs_set_timing", "cs_kernel_times", "cs_alu_peak", "cs_eigen_reruns",
-           "cs_risk_index_static")
+           "cs_risk_index_static", "cs_network_stats")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -96,6 +96,7 @@ def load_library(build_if_missing: bool = True):
         "cs_poll": (i32, [P, u64, i32, ctypes.POINTER(Result)]),
         "cs_risk_index": (i32, [P, i32, i32, P, i32, P, ctypes.POINTER(i64)]),
         "cs_risk_index_static": (i32, [P, i32, i32, P, i32, P, ctypes.POINTER(i64)]),
+        "cs_network_stats": (i32, [P, i32, P, i32]),
         "cs_risk_reduce_device": (i32, [i32, P, P, P, i32, P, P]),
         "cs_enumerate_pairs_device": (i32, [i32, i64, i64, P, P, P]),
         "cs_last_error": (ctypes.c_char_p, [P]),
@@ -287,6 +288,13 @@ class Context:
         if out is None:
             raise CSError(-4, "request did not finish in time")
         return out
+
+    def network_stats(self, net_id: int) -> dict:
+        """Sizes of a loaded network and its symbolic analysis (cs_network_stats)."""
+        v = np.zeros(8, np.int64)
+        self._check(self.lib.cs_network_stats(self.h, net_id, _ptr(v), 8), "cs_network_stats")
+        keys = ("n_bus", "n_branch", "n_gen", "l_blocks", "block_updates", "levels", "states_max", "levels_load")
+        return dict(zip(keys, (int(x) for x in v)))
 
     # ------------------------------------------------------------ Risk Index --
     def risk_index(self, net_id: int, level: int, lam, mode: int = RISK_ORDERED):

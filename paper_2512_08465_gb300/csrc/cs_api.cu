@@ -503,6 +503,20 @@ cs_status cs_unload_network(cs_ctx* ctx, int32_t net_id) {
     return CS_OK;
 }
 
+cs_status cs_network_stats(cs_ctx* ctx, int32_t net_id, int64_t* stats, int32_t n_stats) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    auto it = ctx->nets.find(net_id);
+    if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
+    if (!stats || n_stats < 0) return fail(ctx, CS_E_ARG, "NULL stats");
+    const DevNet& d = it->second->dev;
+    const Symbolic& S = it->second->sym;
+    const int64_t v[8] = {d.nb, d.nbr, d.ng, d.nL, (int64_t)S.upd_a.size(), d.nlevels, 5LL * d.ng - 1,
+                          (int64_t)it->second->nlev};
+    for (int i = 0; i < n_stats && i < 8; ++i) stats[i] = v[i];
+    return CS_OK;
+}
+
 cs_status cs_base_result(cs_ctx* ctx, int32_t net_id, int32_t level, const cs_result* out) {
     if (!ctx) return CS_E_ARG;
     std::lock_guard<std::mutex> lock(ctx->mu);
