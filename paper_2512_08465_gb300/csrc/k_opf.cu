@@ -163,7 +163,7 @@ __device__ void block_reduce(RedBuf& rb, double (&val)[K], const int (&ops)[K], 
 // removes, where a Gauss-Jordan inverse did not.)  Returns false if a pivot
 // is exactly zero or not finite.
 __device__ bool inv4(const double* A, double* Ainv) {
-    double a[4][4];
+    double a[4][4], dinv[4];
     int piv[4] = {0, 1, 2, 3};
     for (int r = 0; r < 4; ++r)                  // symmetric part of the updated pivot
         for (int c = 0; c < 4; ++c) a[r][c] = 0.5 * (A[4 * r + c] + A[4 * c + r]);
@@ -177,8 +177,9 @@ __device__ bool inv4(const double* A, double* Ainv) {
             for (int q = 0; q < 4; ++q) { double t = a[c][q]; a[c][q] = a[p][q]; a[p][q] = t; }
             int t = piv[c]; piv[c] = piv[p]; piv[p] = t;
         }
+        dinv[c] = 1.0 / a[c][c];                  // one division per pivot
         for (int r = c + 1; r < 4; ++r) {
-            a[r][c] /= a[c][c];
+            a[r][c] *= dinv[c];
             const double m = a[r][c];
             for (int q = c + 1; q < 4; ++q) a[r][q] -= m * a[c][q];
         }
@@ -193,7 +194,7 @@ __device__ bool inv4(const double* A, double* Ainv) {
         for (int i = 3; i >= 0; --i) {
             double v = y[i];
             for (int q = i + 1; q < 4; ++q) v -= a[i][q] * y[q];
-            y[i] = v / a[i][i];
+            y[i] = v * dinv[i];
         }
         for (int i = 0; i < 4; ++i) Ainv[4 * i + j] = y[i];
     }
@@ -303,18 +304,43 @@ __device__ void eval_branch(const DevNet& net, int b, double* W, const Lay& L, d
 // Solve (L D L^T) v = v in place for the 4-vector-per-bus array v (new order):
 // forward by elimination-tree levels, block diagonal, backward by levels.
 __device__ void ldl_solve(const DevNet& net, const double* W, const Lay& L, double* v) {
-    const int tid = threadIdx.x, nb = net.nb;
+    const int tid = threadIdx.x, nb = net.nb, lane = tid & 31, warp = tid >> 5;
     for (int lev = 0; lev < net.nlevels; ++lev) {
         const int c0 = net.lev_ptr[lev], c1 = net.lev_ptr[lev + 1];
-        for (int w = tid; w < 4 * (c1 - c0); w += kThreads) {
-            const int j = net.lev_col[c0 + (w >> 2)], r = w & 3;
-            double acc = v[4 * j + r];
-            for (int e = net.Lrowptr[j]; e < net.Lrowptr[j + 1]; ++e) {
-                const double* Lq = W + L.Lb + 16 * net.Lrowblk[e] + 4 * r;
-                const double* y = v + 4 * net.Lrowcol[e];
-                acc -= Lq[0] * y[0] + Lq[1] * y[1] + Lq[2] * y[2] + Lq[3] * y[3];
+        if (c1 - c0 <= kWarps) {
+            // narrow level (the top of the elimination tree): a warp per column, its
+            // lanes over the blocks of the row, partial sums reduced by shuffles
+            if (warp < c1 - c0) {
+                const int j = net.lev_col[c0 + warp];
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+                for (int e = net.Lrowptr[j] + lane; e < net.Lrowptr[j + 1]; e += 32) {
+                    const double* Lq = W + L.Lb + 16 * net.Lrowblk[e];
+                    const double* y = v + 4 * net.Lrowcol[e];
+                    const double y0 = y[0], y1 = y[1], y2 = y[2], y3 = y[3];
+                    a0 += Lq[0] * y0 + Lq[1] * y1 + Lq[2] * y2 + Lq[3] * y3;
+                    a1 += Lq[4] * y0 + Lq[5] * y1 + Lq[6] * y2 + Lq[7] * y3;
+                    a2 += Lq[8] * y0 + Lq[9] * y1 + Lq[10] * y2 + Lq[11] * y3;
+                    a3 += Lq[12] * y0 + Lq[13] * y1 + Lq[14] * y2 + Lq[15] * y3;
+                }
+                for (int off = 16; off; off >>= 1) {
+                    a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+                    a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+                    a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+                    a3 += __shfl_xor_sync(0xffffffffu, a3, off);
+                }
+                if (lane < 4) v[4 * j + lane] -= (lane == 0 ? a0 : lane == 1 ? a1 : lane == 2 ? a2 : a3);
             }
-            v[4 * j + r] = acc;
+        } else {
+            for (int w = tid; w < 4 * (c1 - c0); w += kThreads) {
+                const int j = net.lev_col[c0 + (w >> 2)], r = w & 3;
+                double acc = v[4 * j + r];
+                for (int e = net.Lrowptr[j]; e < net.Lrowptr[j + 1]; ++e) {
+                    const double* Lq = W + L.Lb + 16 * net.Lrowblk[e] + 4 * r;
+                    const double* y = v + 4 * net.Lrowcol[e];
+                    acc -= Lq[0] * y[0] + Lq[1] * y[1] + Lq[2] * y[2] + Lq[3] * y[3];
+                }
+                v[4 * j + r] = acc;
+            }
         }
         __syncthreads();
     }
@@ -328,15 +354,38 @@ __device__ void ldl_solve(const DevNet& net, const double* W, const Lay& L, doub
     __syncthreads();
     for (int lev = net.nlevels - 1; lev >= 0; --lev) {
         const int c0 = net.lev_ptr[lev], c1 = net.lev_ptr[lev + 1];
-        for (int w = tid; w < 4 * (c1 - c0); w += kThreads) {
-            const int j = net.lev_col[c0 + (w >> 2)], r = w & 3;
-            double acc = v[4 * j + r];
-            for (int e = net.Lcolptr[j]; e < net.Lcolptr[j + 1]; ++e) {
-                const double* Lq = W + L.Lb + 16 * e + r;
-                const double* xi = v + 4 * net.Lrow[e];
-                acc -= Lq[0] * xi[0] + Lq[4] * xi[1] + Lq[8] * xi[2] + Lq[12] * xi[3];
+        if (c1 - c0 <= kWarps) {
+            if (warp < c1 - c0) {
+                const int j = net.lev_col[c0 + warp];
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+                for (int e = net.Lcolptr[j] + lane; e < net.Lcolptr[j + 1]; e += 32) {
+                    const double* Lq = W + L.Lb + 16 * e;
+                    const double* xi = v + 4 * net.Lrow[e];
+                    const double x0 = xi[0], x1 = xi[1], x2 = xi[2], x3 = xi[3];
+                    a0 += Lq[0] * x0 + Lq[4] * x1 + Lq[8] * x2 + Lq[12] * x3;
+                    a1 += Lq[1] * x0 + Lq[5] * x1 + Lq[9] * x2 + Lq[13] * x3;
+                    a2 += Lq[2] * x0 + Lq[6] * x1 + Lq[10] * x2 + Lq[14] * x3;
+                    a3 += Lq[3] * x0 + Lq[7] * x1 + Lq[11] * x2 + Lq[15] * x3;
+                }
+                for (int off = 16; off; off >>= 1) {
+                    a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+                    a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+                    a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+                    a3 += __shfl_xor_sync(0xffffffffu, a3, off);
+                }
+                if (lane < 4) v[4 * j + lane] -= (lane == 0 ? a0 : lane == 1 ? a1 : lane == 2 ? a2 : a3);
             }
-            v[4 * j + r] = acc;
+        } else {
+            for (int w = tid; w < 4 * (c1 - c0); w += kThreads) {
+                const int j = net.lev_col[c0 + (w >> 2)], r = w & 3;
+                double acc = v[4 * j + r];
+                for (int e = net.Lcolptr[j]; e < net.Lcolptr[j + 1]; ++e) {
+                    const double* Lq = W + L.Lb + 16 * e + r;
+                    const double* xi = v + 4 * net.Lrow[e];
+                    acc -= Lq[0] * xi[0] + Lq[4] * xi[1] + Lq[8] * xi[2] + Lq[12] * xi[3];
+                }
+                v[4 * j + r] = acc;
+            }
         }
         __syncthreads();
     }

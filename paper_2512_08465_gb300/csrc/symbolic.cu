@@ -163,6 +163,12 @@ std::string symbolic_analysis(int n, const std::vector<int>& f, const std::vecto
         S.upd_ptr[q + 1] = (int)S.upd_a.size();
         S.block_updates += (long long)upd[q].size();
     }
+    // within a level, targets with similar update counts sit next to each other, so
+    // that the threads sharing a warp run loops of similar length
+    for (int h = 0; h < H; ++h)
+        std::stable_sort(S.tgt.begin() + S.tgt_ptr[h], S.tgt.begin() + S.tgt_ptr[h + 1], [&](int x, int y) {
+            return upd[x].size() > upd[y].size();
+        });
     // block -> branches whose off-diagonal pair it holds
     std::vector<std::vector<int>> bb(nL);
     for (size_t k = 0; k < f.size(); ++k) {
