@@ -58,6 +58,7 @@ constexpr int kRefineSteps = 3;              // FP64 iterative refinement steps 
 constexpr double kRefineTol = 4.0 * 2.220446049250313e-16;   // refinement done: backward error at rounding level
 constexpr double kBackwardTol = 1e-13;       // componentwise backward error accepted from the block solve
 constexpr int kDenseMax = 1024;              // dense fallback for reduced systems up to this order
+constexpr int kPanel = 8;                    // panel width of the dense fallback's blocked LU
 constexpr int kGmresM = 8;                   // GMRES iterations per Newton solve (at most)
 
 // record layout
@@ -623,7 +624,10 @@ __device__ bool dense_solve(const DevNet& net, double* W, const Lay& L, DenseSha
         rs[i] = (m > 0.0) ? ldexp(1.0, -e) : 1.0;
     }
     __syncthreads();
-    for (long w = tid; w < (long)N * N; w += kThreads) A[w] *= rs[w / N];
+    for (int i = warp; i < N; i += kWarps) {
+        const double ri = rs[i];
+        for (int j = lane; j < N; j += 32) A[(long)i * N + j] *= ri;
+    }
     for (int w = tid; w < N; w += kThreads) x[w] = W[L.bv + w] * rs[w];
     __syncthreads();
     for (int j = tid; j < N; j += kThreads) {
@@ -634,51 +638,85 @@ __device__ bool dense_solve(const DevNet& net, double* W, const Lay& L, DenseSha
         cs[j] = (m > 0.0) ? ldexp(1.0, -e) : 1.0;
     }
     __syncthreads();
-    for (long w = tid; w < (long)N * N; w += kThreads) A[w] *= cs[w % N];
+    for (int i = warp; i < N; i += kWarps)
+        for (int j = lane; j < N; j += 32) A[(long)i * N + j] *= cs[j];
     __syncthreads();
-    for (int k = 0; k < N; ++k) {
-        double best = -1.0;
-        int bi = k;
-        for (int i = k + tid; i < N; i += kThreads) {
-            const double a = fabs(A[(long)i * N + k]);
-            if (a > best) { best = a; bi = i; }
-        }
-        for (int off = 16; off; off >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, off);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (lane == 0) { ds.val[warp] = best; ds.idx[warp] = bi; }
-        __syncthreads();
-        if (tid == 0) {
-            double b0 = ds.val[0];
-            int i0 = ds.idx[0];
-            for (int q = 1; q < kThreads / 32; ++q)
-                if (ds.val[q] > b0 || (ds.val[q] == b0 && ds.idx[q] < i0)) { b0 = ds.val[q]; i0 = ds.idx[q]; }
-            ds.piv = i0;
-            ds.pv = b0;
-        }
-        __syncthreads();
-        if (!(ds.pv > 0.0) || !isfinite(ds.pv)) return false;
-        const int p = ds.piv;
-        if (p != k) {
-            for (int c = tid; c < N; c += kThreads) {
-                const double t = A[(long)k * N + c];
-                A[(long)k * N + c] = A[(long)p * N + c];
-                A[(long)p * N + c] = t;
+    // Right-looking LU with partial pivoting in panels of kPanel columns: the panel is
+    // factorised column by column (whole rows are swapped), then the block row of U
+    // is solved with the panel's unit lower triangle and the trailing matrix takes
+    // one rank-kPanel update, so it is read and written once per panel.  The right-
+    // hand side is eliminated along the way.
+    for (int k0 = 0; k0 < N; k0 += kPanel) {
+        const int ke = min(k0 + kPanel, N);
+        for (int k = k0; k < ke; ++k) {
+            double best = -1.0;
+            int bi = k;
+            for (int i = k + tid; i < N; i += kThreads) {
+                const double a = fabs(A[(long)i * N + k]);
+                if (a > best) { best = a; bi = i; }
             }
-            if (tid == 0) { const double t = x[k]; x[k] = x[p]; x[p] = t; }
+            for (int off = 16; off; off >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) { ds.val[warp] = best; ds.idx[warp] = bi; }
+            __syncthreads();
+            if (tid == 0) {
+                double b0 = ds.val[0];
+                int i0 = ds.idx[0];
+                for (int q = 1; q < kWarps; ++q)
+                    if (ds.val[q] > b0 || (ds.val[q] == b0 && ds.idx[q] < i0)) { b0 = ds.val[q]; i0 = ds.idx[q]; }
+                ds.piv = i0;
+                ds.pv = b0;
+            }
+            __syncthreads();
+            if (!(ds.pv > 0.0) || !isfinite(ds.pv)) return false;
+            const int p = ds.piv;
+            if (p != k) {
+                for (int c = tid; c < N; c += kThreads) {
+                    const double t = A[(long)k * N + c];
+                    A[(long)k * N + c] = A[(long)p * N + c];
+                    A[(long)p * N + c] = t;
+                }
+                if (tid == 0) { const double t = x[k]; x[k] = x[p]; x[p] = t; }
+                __syncthreads();
+            }
+            const double* pk = A + (long)k * N;
+            const double inv = 1.0 / pk[k];
+            const double xk = x[k];
+            for (int i = k + 1 + tid; i < N; i += kThreads) {       // column k and the rest of the panel
+                double* ri = A + (long)i * N;
+                const double l = ri[k] * inv;
+                ri[k] = l;
+                for (int j = k + 1; j < ke; ++j) ri[j] -= l * pk[j];
+                x[i] -= l * xk;
+            }
             __syncthreads();
         }
-        const double inv = 1.0 / A[(long)k * N + k];
-        for (int i = k + 1 + tid; i < N; i += kThreads) A[(long)i * N + k] *= inv;
-        __syncthreads();
-        const int m = N - k - 1;
-        for (long w = tid; w < (long)m * m; w += kThreads) {
-            const int i = k + 1 + (int)(w / m), j = k + 1 + (int)(w % m);
-            A[(long)i * N + j] -= A[(long)i * N + k] * A[(long)k * N + j];
+        if (ke == N) break;
+        for (int j = ke + tid; j < N; j += kThreads) {               // U block row: unit lower solve
+            for (int r = k0 + 1; r < ke; ++r) {
+                double acc = A[(long)r * N + j];
+                for (int t = k0; t < r; ++t) acc -= A[(long)r * N + t] * A[(long)t * N + j];
+                A[(long)r * N + j] = acc;
+            }
         }
-        for (int i = k + 1 + tid; i < N; i += kThreads) x[i] -= A[(long)i * N + k] * x[k];
+        __syncthreads();
+        const int kb = ke - k0;
+        for (int i = ke + warp; i < N; i += kWarps) {                // trailing rank-kb update
+            double* ri = A + (long)i * N;
+            double l[kPanel];
+#pragma unroll
+            for (int t = 0; t < kPanel; ++t) l[t] = (t < kb) ? ri[k0 + t] : 0.0;
+            for (int j = ke + lane; j < N; j += 32) {
+                double acc = ri[j];
+#pragma unroll
+                for (int t = 0; t < kPanel; ++t)
+                    if (t < kb) acc -= l[t] * A[(long)(k0 + t) * N + j];
+                ri[j] = acc;
+            }
+        }
         __syncthreads();
     }
     for (int k = N - 1; k >= 0; --k) {
