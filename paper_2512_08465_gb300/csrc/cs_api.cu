@@ -75,7 +75,7 @@ struct cs_ctx {
     std::vector<std::unique_ptr<Request>> pool;     // finished requests kept for buffer reuse
     cudaStream_t req_stream = nullptr;
     // workspace
-    DevBuf scratch, isl, opfx, opfst, counters, err_word, hbuf;
+    DevBuf scratch, isl, opfx, opfst, counters, err_word, hbuf, abuf;
     // the workspace above is shared by every evaluation of the context: each one waits
     // for the previous one (whatever its stream) through this event
     cudaEvent_t ws_free = nullptr;
@@ -139,10 +139,13 @@ cs_status evaluate_impl(cs_ctx* ctx, Network* net, int level, const int32_t* ei,
     CS_CUDA(ctx->isl.ensure(sizeof(int) * cn));
     CS_CUDA(ctx->opfx.ensure(sizeof(double) * nx * cn));
     CS_CUDA(ctx->opfst.ensure(sizeof(int) * cn));
-    CS_CUDA(ctx->counters.ensure(sizeof(int) * 4));
+    CS_CUDA(ctx->counters.ensure(sizeof(int) * 5));
     // packed Hessenberg matrices between the two halves of the FP32 screen
     const bool split = ctx->opt.precision == CS_PREC_MIXED && dyn_split_fits(dn, ctx->device);
-    if (split) CS_CUDA(ctx->hbuf.ensure(sizeof(float) * dyn_hbuf_stride(dn) * cn));
+    if (split) {
+        CS_CUDA(ctx->hbuf.ensure(sizeof(float) * dyn_hbuf_stride(dn) * cn));
+        CS_CUDA(ctx->abuf.ensure(sizeof(float) * dyn_abuf_stride(dn) * cn));
+    }
     if (!ctx->err_word.p) {
         CS_CUDA(ctx->err_word.ensure(sizeof(int) * 2));
         CS_CUDA(cudaMemset(ctx->err_word.p, 0, sizeof(int) * 2));
@@ -172,7 +175,7 @@ cs_status evaluate_impl(cs_ctx* ctx, Network* net, int level, const int32_t* ei,
         a.err = (int*)ctx->err_word.p;
         a.reruns = (int*)ctx->err_word.p + 1;
         OpfOut o{(double*)ctx->opfx.p, (int*)ctx->opfst.p};
-        CS_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * 4, s));
+        CS_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * 5, s));
         auto mark = [&](int kind) -> cudaError_t {     // start event of a timed launch
             if (!ctx->timing) return cudaSuccess;
             while (ctx->ev.size() < 2 * (ctx->ev_used + 1)) {
@@ -201,7 +204,8 @@ cs_status evaluate_impl(cs_ctx* ctx, Network* net, int level, const int32_t* ei,
         CS_CUDA(mark(2));
         int nl = 0;
         CS_CUDA(launch_dyn(dn, a, o, ctx->opt.damping_min, ctx->opt.precision, (double*)ctx->scratch.p, per_dyn,
-                           std::min<int64_t>(g_dyn, m), split ? (float*)ctx->hbuf.p : nullptr, ctx->sms,
+                           std::min<int64_t>(g_dyn, m), split ? (float*)ctx->abuf.p : nullptr,
+                           split ? (float*)ctx->hbuf.p : nullptr, ctx->sms,
                            counters + 1, &nl, s));
         CS_CUDA(done());
         ctx->launches += 2 + nl;

@@ -38,6 +38,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "cs_internal.h"
 
 namespace {
@@ -428,9 +430,9 @@ __device__ void eig_stats(DShared& sh, int n, const double* wr, const double* wi
 // Kernel modes.  FULL64: FP64 screen of every converged OPF point (the FP64
 // form).  MIXED_INLINE: FP32 screen in global memory with the FP64 re-run
 // inline (mixed form, networks whose Hessenberg matrix exceeds shared memory).
-// FRONT: model, FP32 balancing and Hessenberg reduction; the packed Hessenberg
-// matrix goes to hbuf for hqr_smem_kernel.  RERUN: FP64 screen of the
-// scenarios that kernel marked (status 6).
+// FRONT: model and FP32 balancing; the balanced matrix goes to a per-scenario
+// buffer for hess_cluster_kernel.  RERUN: FP64 screen of the scenarios that
+// hqr_smem_kernel marked (status 6).
 enum { DYN_FULL64 = 0, DYN_MIXED_INLINE = 1, DYN_FRONT = 2, DYN_RERUN = 3 };
 
 template <int kMode>
@@ -675,21 +677,13 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
         double* wr = W + L.wr;
         double* wi = W + L.wi;
         double maxre = 0.0, minz = 0.0;
-        if (kMode == DYN_FRONT) {
-            float* A32 = reinterpret_cast<float*>(W + L.A32);
+        if (kMode == DYN_FRONT) {                     // balanced FP32 matrix for the cluster kernel
+            float* dst = hbuf + (size_t)s * hstride;
+            float* A32 = dst + kHqHead;
             for (int w = tid; w < n * n; w += kThreads) A32[w] = (float)A[w];
-            __syncthreads();
-            float* csf = reinterpret_cast<float*>(cs_d);
-            balance<float>(A32, n, csf, reinterpret_cast<float*>(rs_d), sh);
-            hessenberg<float>(A32, n, reinterpret_cast<float*>(v_d), sh);
-            float* dst = hbuf + (size_t)s * hstride;   // packed rows for the shared-memory QR
             if (tid == 0) dst[0] = __int_as_float(n);
-            const int warp = tid >> 5, lane = tid & 31;
-            for (int i = warp; i < n; i += kThreads / 32) {
-                const int j0 = hq_start(i);
-                float* drow = dst + kHqHead + hq_off(n, i) - j0;
-                for (int j = j0 + lane; j < n; j += 32) drow[j] = A32[(size_t)i * n + j];
-            }
+            __syncthreads();
+            balance<float>(A32, n, reinterpret_cast<float*>(cs_d), reinterpret_cast<float*>(rs_d), sh);
             __syncthreads();
             continue;
         }
@@ -748,14 +742,154 @@ __global__ void record_kernel(int nbr, int nE, EvalArgs a) {
 }
 
 
+
 // ---------------------------------------------------------------------------
-// FP32 screen, second half: Francis double-shift QR of the packed Hessenberg
+// FP32 screen, middle part: Householder reduction to Hessenberg form of the
+// balanced matrix, held on chip by a cluster of two CTAs (each keeps half of
+// the rows in its shared memory; the 269 x 269 matrix of the 118-bus network
+// is 289 KB, more than one CTA may hold).  Per column, each CTA writes its
+// rows' part of the reflector and of the squared norm into both CTAs' shared
+// memory (distributed shared memory), then the partial sums v^T A of the left
+// update; two cluster barriers per column.  Exchange buffers alternate with the
+// column parity, so a CTA that runs ahead never overwrites what its peer still
+// reads.  The packed Hessenberg matrix goes to hbuf for hqr_smem_kernel.
+constexpr int kHsThreads = 256;
+constexpr int kHsWarps = kHsThreads / 32;
+constexpr int kHsCols = 12;         // columns per lane in the row pass: orders up to 32 * 12 + 1
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kHsThreads, 1)
+hess_cluster_kernel(EvalArgs a, OpfOut o, const float* __restrict__ abuf, size_t astride, float* __restrict__ hbuf,
+                    size_t hstride, int nmax, int* counter) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    extern __shared__ float csm[];
+    const int hmax = (nmax + 1) / 2;
+    float* As = csm;                                  // own rows, row stride n
+    float* vb = As + (size_t)hmax * nmax;             // [2 parity][nmax] raw column k (vb[.][0] = x0)
+    float* wb = vb + 2 * nmax;                        // [2 parity][2 rank][nmax] partial v^T A
+    float* np = wb + 4 * nmax;                        // [2 parity][2 rank] partial squared norms
+    __shared__ float red[kHsWarps];
+    __shared__ int scen;
+    float* peer_vb = cl.map_shared_rank(vb, rank ^ 1);
+    float* peer_wb = cl.map_shared_rank(wb, rank ^ 1);
+    float* peer_np = cl.map_shared_rank(np, rank ^ 1);
+    int* peer_scen = cl.map_shared_rank(&scen, rank ^ 1);
+
+    for (;;) {
+        if (rank == 0 && tid == 0) {
+            const int s0 = atomicAdd(counter, 1);
+            scen = s0;
+            *peer_scen = s0;
+        }
+        cl.sync();
+        const int s = scen;
+        cl.sync();                                    // both have read scen
+        if (s >= a.n) break;
+        if (o.status[s] != 1) continue;
+        const float* src = abuf + (size_t)s * astride;
+        const int n = __float_as_int(src[0]);
+        const float* Ag = src + kHqHead;
+        const int h = (n + 1) / 2, r0 = rank * h, r1 = min(n, r0 + h), nr = max(0, r1 - r0);
+        for (int w = tid; w < nr * n; w += kHsThreads) As[w] = Ag[(size_t)r0 * n + w];
+        __syncthreads();
+        for (int k = 0; k + 2 < n; ++k) {
+            const int par = k & 1;
+            float* v = vb + par * nmax;
+            float* pv = peer_vb + par * nmax;
+            const int i0 = max(r0, k + 1);
+            float t = 0.0f;
+            for (int i = i0 + tid; i < r1; i += kHsThreads) {
+                const float q = As[(i - r0) * n + k];
+                v[i - k - 1] = q;
+                pv[i - k - 1] = q;
+                if (i >= k + 2) t += q * q;
+            }
+            for (int off = 16; off; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+            if (lane == 0) red[warp] = t;
+            __syncthreads();
+            if (tid == 0) {
+                float tt = 0.0f;
+                for (int q = 0; q < kHsWarps; ++q) tt += red[q];
+                np[par * 2 + rank] = tt;
+                peer_np[par * 2 + rank] = tt;
+            }
+            cl.sync();                                // reflector and norm partials in place
+            const float tail = np[par * 2] + np[par * 2 + 1];
+            if (tail == 0.0f) continue;               // column already reduced (same in both CTAs)
+            const float x0 = v[0];
+            const float nrm = sqrtf(x0 * x0 + tail);
+            const float alpha = (x0 >= 0.0f) ? -nrm : nrm;
+            const float v0 = x0 - alpha;
+            const float beta = 2.0f / (v0 * v0 + tail);
+            float* w_own = wb + (par * 2 + rank) * nmax;
+            float* w_peer = peer_wb + (par * 2 + rank) * nmax;
+            for (int j = k + 1 + tid; j < n; j += kHsThreads) {   // partial v^T A over own rows
+                float acc = 0.0f;
+                for (int i = i0; i < r1; ++i) acc += ((i == k + 1) ? v0 : v[i - k - 1]) * As[(i - r0) * n + j];
+                w_own[j] = acc;
+                w_peer[j] = acc;
+            }
+            cl.sync();                                // partial sums exchanged
+            // One pass per own row, a warp per row: the left update (rows k+1..),
+            // column k, then the right update, with the row held in registers.  Each
+            // lane keeps w and v for its columns k+1+lane+32t in registers.
+            const float* w0 = wb + (par * 2) * nmax;
+            const float* w1 = wb + (par * 2 + 1) * nmax;
+            const int mm = n - k - 1;
+            float wr_[kHsCols], vr_[kHsCols];
+#pragma unroll
+            for (int t = 0; t < kHsCols; ++t) {
+                const int jj = lane + 32 * t;             // offset from column k+1
+                wr_[t] = (jj < mm) ? beta * (w0[k + 1 + jj] + w1[k + 1 + jj]) : 0.0f;
+                vr_[t] = (jj < mm) ? (jj == 0 ? v0 : v[jj]) : 0.0f;
+            }
+            for (int i = warp; i < nr; i += kHsWarps) {
+                float* row = As + i * n + k + 1;
+                const int gi = r0 + i;
+                const float vi = (gi >= k + 1) ? ((gi == k + 1) ? v0 : v[gi - k - 1]) : 0.0f;
+                float x[kHsCols];
+                float acc = 0.0f;
+#pragma unroll
+                for (int t = 0; t < kHsCols; ++t) {
+                    const int jj = lane + 32 * t;
+                    x[t] = (jj < mm) ? row[jj] - vi * wr_[t] : 0.0f;
+                    acc += x[t] * vr_[t];
+                }
+                for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                acc *= beta;
+#pragma unroll
+                for (int t = 0; t < kHsCols; ++t) {
+                    const int jj = lane + 32 * t;
+                    if (jj < mm) row[jj] = x[t] - acc * vr_[t];
+                }
+                if (lane == 0 && gi >= k + 1) row[-1] = (gi == k + 1) ? alpha : 0.0f;
+            }
+            __syncthreads();
+        }
+        float* dst = hbuf + (size_t)s * hstride;      // packed rows for the shared-memory QR
+        if (rank == 0 && tid == 0) dst[0] = __int_as_float(n);
+        for (int i = r0 + warp; i < r1; i += kHsWarps) {
+            const int j0 = hq_start(i);
+            float* drow = dst + kHqHead + hq_off(n, i) - j0;
+            for (int j = j0 + lane; j < n; j += 32) drow[j] = As[(i - r0) * n + j];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 screen, last part: Francis double-shift QR of the packed Hessenberg
 // matrix held in shared memory (one scenario per CTA, one CTA per SM).  Every
 // thread carries the same loop state (lo, hi, shifts, reflector), computed
 // redundantly from shared memory in FP32, so a bulge step costs two barriers.
 // A scenario whose decision falls inside the guard band (or whose QR does not
 // converge) is marked for the FP64 re-run; the others are classified here.
-constexpr int kQrThreads = 256;
+#ifndef CS_QR_THREADS
+#define CS_QR_THREADS 256
+#endif
+constexpr int kQrThreads = CS_QR_THREADS;
 
 __device__ __forceinline__ void eig2f(float p, float q, float r, float s, float* re, float* im) {
     const float hm = 0.5f * (p - s);
@@ -885,6 +1019,7 @@ hqr_smem_kernel(EvalArgs a, OpfOut o, const float* __restrict__ hbuf, size_t hst
                 x1 = h10 * (h00 + h11 - sft);
                 x2 = h10 * h21;
             }
+            __syncthreads();              // every warp has read the block and the shifts before the sweep writes
             for (int k = lo; k <= hi - 1; ++k) {
                 const int len = (k + 2 <= hi) ? 3 : 2;
                 const float t2 = x1 * x1 + (len == 3 ? x2 * x2 : 0.0f);
@@ -990,14 +1125,25 @@ size_t dyn_hbuf_stride(const DevNet& net) {
     return (size_t)kHqHead + (size_t)((hq_off(nmax, nmax) + 3) & ~3);
 }
 
+size_t dyn_abuf_stride(const DevNet& net) {
+    const size_t nmax = 5 * (size_t)net.ng - 1;
+    return (size_t)kHqHead + ((nmax * nmax + 3) & ~(size_t)3);
+}
+
 static size_t qr_smem_bytes(int nmax) {
     return sizeof(float) * ((size_t)((hq_off(nmax, nmax) + 3) & ~3) + 3 * (size_t)nmax);
+}
+
+static size_t hess_smem_bytes(int nmax) {
+    return sizeof(float) * ((size_t)((nmax + 1) / 2) * nmax + 6 * (size_t)nmax + 4);
 }
 
 bool dyn_split_fits(const DevNet& net, int device) {
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return false;
-    return qr_smem_bytes(5 * net.ng - 1) + 1024 <= (size_t)optin;
+    const int nmax = 5 * net.ng - 1;
+    if (nmax - 1 > 32 * kHsCols) return false;
+    return qr_smem_bytes(nmax) + 1024 <= (size_t)optin && hess_smem_bytes(nmax) + 1024 <= (size_t)optin;
 }
 
 template <int kMode>
@@ -1014,22 +1160,29 @@ static cudaError_t launch_mode(const DevNet& net, const EvalArgs& a, OpfOut o, d
 }
 
 cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double damping_min, int precision,
-                       double* scratch, size_t scratch_per_cta, int grid, float* hbuf, int sms, int* counters,
-                       int* launches, cudaStream_t s) {
+                       double* scratch, size_t scratch_per_cta, int grid, float* abuf, float* hbuf, int sms,
+                       int* counters, int* launches, cudaStream_t s) {
     *launches = 0;
     if (a.n <= 0) return cudaSuccess;
     const DLay L = make_dlayout(net);
     if ((size_t)L.total > scratch_per_cta) return cudaErrorInvalidValue;
     cudaError_t e;
-    if (precision == CS_PREC_MIXED && hbuf) {
-        // FP32 screen split in two: front (model, balancing, Hessenberg) at several CTAs
-        // per SM, then the QR from shared memory at one CTA per SM, then the FP64 re-run
-        // of the scenarios the FP32 screen cannot decide.
-        const size_t hstride = dyn_hbuf_stride(net);
-        e = launch_mode<DYN_FRONT>(net, a, o, damping_min, scratch, scratch_per_cta, L, hbuf, hstride, grid,
+    if (precision == CS_PREC_MIXED && hbuf && abuf) {
+        // FP32 screen in four kernels: front (model, balancing) at several CTAs per SM,
+        // Hessenberg reduction on a two-CTA cluster, QR from shared memory at one CTA per
+        // SM, and the FP64 re-run of the scenarios the FP32 screen cannot decide.
+        const size_t hstride = dyn_hbuf_stride(net), astride = dyn_abuf_stride(net);
+        e = launch_mode<DYN_FRONT>(net, a, o, damping_min, scratch, scratch_per_cta, L, abuf, astride, grid,
                                    counters, s);
         if (e != cudaSuccess) return e;
         const int nmax = 5 * net.ng - 1;
+        const size_t hsm = hess_smem_bytes(nmax);
+        e = cudaFuncSetAttribute(hess_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+        if (e != cudaSuccess) return e;
+        const int gh = 2 * (int)std::min<int64_t>((int64_t)std::max(1, sms / 2), a.n);
+        hess_cluster_kernel<<<gh, kHsThreads, hsm, s>>>(a, o, abuf, astride, hbuf, hstride, nmax, counters + 3);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
         const size_t qsm = qr_smem_bytes(nmax);
         e = cudaFuncSetAttribute(hqr_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
         if (e != cudaSuccess) return e;
@@ -1040,7 +1193,7 @@ cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double da
         e = launch_mode<DYN_RERUN>(net, a, o, damping_min, scratch, scratch_per_cta, L, nullptr, 0, grid,
                                    counters + 2, s);
         if (e != cudaSuccess) return e;
-        *launches = 3;
+        *launches = 4;
     } else if (precision == CS_PREC_MIXED) {
         e = launch_mode<DYN_MIXED_INLINE>(net, a, o, damping_min, scratch, scratch_per_cta, L, nullptr, 0, grid,
                                           counters, s);
