@@ -35,7 +35,7 @@ enum {
     CS_OK = 0,
     CS_PENDING = 1,            /* cs_poll: the request has not finished yet */
     CS_E_ARG = -1,             /* invalid argument (sizes, ids, ranges, NULL) */
-    CS_E_NOMEM = -2,           /* device or host allocation failed */
+    CS_E_NOMEM = -2,           /* allocation failed, or opt.hbm_budget would be exceeded */
     CS_E_BASE_INSECURE = -3,   /* base case not secure and the options require it */
     CS_E_TIMEOUT = -4,         /* a bounded device wait gave up */
     CS_E_CUDA = -5,            /* a CUDA runtime call failed */
@@ -78,9 +78,14 @@ typedef struct {
     int32_t ctas_per_sm;       /* resident scenario blocks per SM; 0 = automatic */
     int32_t chunk;             /* scenarios per internal batch; 0 = automatic */
     int32_t precision;         /* CS_PREC_FP64 (default) or CS_PREC_MIXED */
+    int64_t hbm_budget;        /* device bytes the context may hold (networks, workspaces,
+                                  request buffers); 0 = no limit */
+    int32_t serve_slots;       /* batches in flight on the serving path (1..8, default 2) */
+    int32_t batch_cap;         /* scenarios per serving batch (default 16384) */
 } cs_options;
 
-/* Fills *opt with the defaults (damping_min 0.05, opf_tol 1e-8, opf_max_it 50). */
+/* Fills *opt with the defaults (damping_min 0.05, opf_tol 1e-8, opf_max_it 50,
+ * FP64 form, no device-memory budget, 2 serving slots, batches of 16384). */
 void cs_default_options(cs_options* opt);
 
 /* Raw network data in structure-of-arrays form, host memory, copied by
@@ -163,18 +168,34 @@ cs_status cs_evaluate_device(cs_ctx* ctx, int32_t net_id, int32_t level,
  * (invalid element ids, bounded-wait time-outs). */
 cs_status cs_sync(cs_ctx* ctx, void* stream);
 
-/* Non-blocking submission with HOST buffers (copied before return).  The
- * library copies inputs to the device, evaluates and copies results back on
- * its own stream; cs_poll retrieves them. */
+/* Non-blocking submission with HOST buffers (copied before return); the
+ * serving path.  A scheduler thread of the context batches queued requests
+ * continuously: the oldest request together with every later queued request
+ * for the same (net_id, level), in arrival order, up to opt.batch_cap
+ * scenarios, on one of opt.serve_slots streams with its own workspace, so
+ * batches of different networks run side by side.  A batch starts only when
+ * its device footprint fits opt.hbm_budget next to everything the context
+ * holds (its chunk shrinks first, then it waits for a running batch).
+ * Severities are recorded in the context's severity tables as for
+ * cs_evaluate_device.  cs_poll retrieves the results. */
 cs_status cs_submit_contingencies(cs_ctx* ctx, int32_t net_id, int32_t level,
                                   const int32_t* elem_i, const int32_t* elem_j, int64_t n,
                                   uint64_t* request_id);
 
 /* Copy the results of a finished request into the HOST record `out` (n
- * records of the request).  Waits at most timeout_us microseconds (0 = just
- * test); returns CS_PENDING if the request is still running.  A finished
- * request is released by the successful poll. */
+ * records of the request; NULL fields are skipped, Vm/Va are not returned on
+ * this path).  Waits at most timeout_us microseconds (0 = just test); returns
+ * CS_PENDING if the request is still queued or running.  A finished request
+ * is released by the successful poll; a failed one returns its error
+ * (CS_E_NOMEM when its batch cannot fit opt.hbm_budget) and is released. */
 cs_status cs_poll(cs_ctx* ctx, uint64_t request_id, int32_t timeout_us, const cs_result* out);
+
+/* Counters of the serving path (no counterpart in the paper): stats[0..8] =
+ * batches launched, requests completed, requests that joined another
+ * request's batch, batch starts deferred by the memory budget, requests failed
+ * for memory, peak device bytes held, device bytes held now, requests queued,
+ * batches in flight.  The first n_stats entries are written (HOST array). */
+cs_status cs_serving_stats(cs_ctx* ctx, int64_t* stats, int32_t n_stats);
 
 /* Risk Index (Section II-C, Eq. 3) of every element from the context's
  * severity table of (net_id, level): R_i = lambda_i S_i + m * sum_j

@@ -20,6 +20,7 @@ from . import build as _build
 _LIB = None
 
 CS_OK, CS_PENDING = 0, 1
+CS_E_ARG, CS_E_NOMEM, CS_E_UNKNOWN_ID = -1, -2, -6
 ERRORS = {-1: "CS_E_ARG", -2: "CS_E_NOMEM", -3: "CS_E_BASE_INSECURE", -4: "CS_E_TIMEOUT",
           -5: "CS_E_CUDA", -6: "CS_E_UNKNOWN_ID", -7: "CS_E_NUMERIC"}
 CLASSES = ("SECURE", "ISLANDED", "OPF_NONCONV", "LIMIT", "SS_UNSTABLE", "SS_POORLY_DAMPED", "EIG_FAIL")
@@ -30,7 +31,7 @@ EXPORTS = ("cs_default_options", "cs_create", "cs_destroy", "cs_load_network", "
            "cs_base_result", "cs_evaluate_device", "cs_sync", "cs_submit_contingencies", "cs_poll",
            "cs_risk_index", "cs_risk_reduce_device", "cs_enumerate_pairs_device", "cs_last_error",
            "cs_last_launch_count", "cs_set_timing", "cs_kernel_times", "cs_alu_peak", "cs_eigen_reruns",
-           "cs_risk_index_static", "cs_network_stats")
+           "cs_risk_index_static", "cs_network_stats", "cs_serving_stats")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -39,7 +40,8 @@ _ip = ctypes.POINTER(ctypes.c_int32)
 class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("damping_min", ctypes.c_double), ("opf_tol", ctypes.c_double),
                 ("opf_max_it", ctypes.c_int32), ("require_secure_base", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("hbm_budget", ctypes.c_int64), ("serve_slots", ctypes.c_int32), ("batch_cap", ctypes.c_int32)]
 
 
 class NetworkDesc(ctypes.Structure):
@@ -97,6 +99,7 @@ def load_library(build_if_missing: bool = True):
         "cs_risk_index": (i32, [P, i32, i32, P, i32, P, ctypes.POINTER(i64)]),
         "cs_risk_index_static": (i32, [P, i32, i32, P, i32, P, ctypes.POINTER(i64)]),
         "cs_network_stats": (i32, [P, i32, P, i32]),
+        "cs_serving_stats": (i32, [P, P, i32]),
         "cs_risk_reduce_device": (i32, [i32, P, P, P, i32, P, P]),
         "cs_enumerate_pairs_device": (i32, [i32, i64, i64, P, P, P]),
         "cs_last_error": (ctypes.c_char_p, [P]),
@@ -288,6 +291,14 @@ class Context:
         if out is None:
             raise CSError(-4, "request did not finish in time")
         return out
+
+    def serving_stats(self) -> dict:
+        """Counters of the serving path (cs_serving_stats)."""
+        v = np.zeros(9, np.int64)
+        self._check(self.lib.cs_serving_stats(self.h, _ptr(v), 9), "cs_serving_stats")
+        keys = ("batches", "completed", "merged", "admission_waits", "nomem", "peak_bytes", "bytes_now",
+                "queued", "in_flight")
+        return dict(zip(keys, (int(x) for x in v)))
 
     def network_stats(self, net_id: int) -> dict:
         """Sizes of a loaded network and its symbolic analysis (cs_network_stats)."""

@@ -1,96 +1,17 @@
 // C ABI of libcs: context, network residency, evaluation, requests, Risk Index.
 #include <algorithm>
-#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <map>
 #include <memory>
-#include <mutex>
 #include <string>
-#include <thread>
 #include <vector>
 
-#include "cs_internal.h"
-#include "symbolic.h"
+#include "ctx.h"
 
-namespace {
+using namespace csi;
 
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-    ~DevBuf() {
-        if (p) cudaFree(p);
-    }
-    cudaError_t ensure(size_t nbytes) {
-        if (nbytes <= bytes) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-        cudaError_t e = cudaMalloc(&p, nbytes);
-        if (e == cudaSuccess) bytes = nbytes;
-        return e;
-    }
-};
-
-struct Network {
-    int id = 0;
-    DevNet dev{};
-    DevBuf blob;                      // all static device arrays
-    Symbolic sym;
-    int nlev = 0;
-    std::vector<std::unique_ptr<DevBuf>> sev_n1, sev_pairs;   // per level
-    // base-case results per level (host)
-    std::vector<uint8_t> base_klass, base_severe;
-    std::vector<int16_t> base_isl, base_iters;
-    std::vector<double> base_cost, base_maxre, base_minz;
-};
-
-struct Request {
-    uint64_t id = 0;
-    int64_t n = 0;
-    int nb = 0;
-    cudaEvent_t done = nullptr;
-    DevBuf d_in, d_out;
-    void* h_out = nullptr;            // pinned staging
-    size_t h_out_bytes = 0;
-    ~Request() {
-        if (done) cudaEventDestroy(done);
-        if (h_out) cudaFreeHost(h_out);
-    }
-};
-
-}  // namespace
-
-struct cs_ctx {
-    std::mutex mu;
-    cs_options opt{};
-    int device = 0;
-    int sms = 0;
-    std::string err;
-    std::map<int, std::unique_ptr<Network>> nets;
-    int next_net = 1;
-    uint64_t next_req = 1;
-    std::map<uint64_t, std::unique_ptr<Request>> reqs;
-    std::vector<std::unique_ptr<Request>> pool;     // finished requests kept for buffer reuse
-    cudaStream_t req_stream = nullptr;
-    // workspace
-    DevBuf scratch, isl, opfx, opfst, counters, err_word, hbuf, abuf;
-    // the workspace above is shared by every evaluation of the context: each one waits
-    // for the previous one (whatever its stream) through this event
-    cudaEvent_t ws_free = nullptr;
-    bool ws_used = false;
-    int64_t launches = 0;
-    // optional per-kernel timing (cs_set_timing): events around each launch
-    bool timing = false;
-    std::vector<cudaEvent_t> ev;      // pairs (start, stop) per kernel launch, reused
-    std::vector<int> ev_kind;         // 0 islands, 1 opf, 2 dyn (+record)
-    size_t ev_used = 0;
-    double kernel_ms[3] = {0.0, 0.0, 0.0};
-    int64_t kernel_launches[3] = {0, 0, 0};
-};
-
-namespace {
+namespace csi {
 
 cs_status fail(cs_ctx* c, cs_status st, const std::string& msg) {
     if (c) c->err = msg;
@@ -101,11 +22,63 @@ cs_status cuda_fail(cs_ctx* c, cudaError_t e, const char* where) {
     return fail(c, CS_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-#define CS_CUDA(call)                                       \
-    do {                                                    \
-        cudaError_t e_ = (call);                            \
-        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
-    } while (0)
+int64_t default_chunk(const cs_ctx* ctx) { return ctx->opt.chunk > 0 ? ctx->opt.chunk : 16384; }
+
+namespace {
+struct Grids {
+    int g_opf, g_dyn;
+    size_t per_opf, per_dyn;
+};
+Grids grids(const cs_ctx* ctx, const DevNet& dn, int64_t cn) {
+    // persistent kernels sized from occupancy, capped per SM
+    const int cap_opf = ctx->opt.ctas_per_sm > 0 ? ctx->opt.ctas_per_sm : opf_ctas_per_sm();
+    const int cap_dyn = ctx->opt.ctas_per_sm > 0 ? ctx->opt.ctas_per_sm : 2;
+    Grids g;
+    g.g_opf = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->sms * cap_opf, cn));
+    g.g_dyn = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->sms * cap_dyn, cn));
+    g.per_opf = opf_scratch_doubles(dn);
+    g.per_dyn = dyn_scratch_doubles(dn);
+    return g;
+}
+bool split_path(const cs_ctx* ctx, const DevNet& dn) {
+    return ctx->opt.precision == CS_PREC_MIXED && dyn_split_fits(dn, ctx->device);
+}
+}  // namespace
+
+size_t workspace_bytes(const cs_ctx* ctx, const Network& net, int64_t chunk) {
+    const DevNet& dn = net.dev;
+    const int64_t cn = std::max<int64_t>(1, chunk);
+    const Grids g = grids(ctx, dn, cn);
+    size_t b = std::max(g.per_opf * g.g_opf, g.per_dyn * g.g_dyn) * sizeof(double);
+    b += sizeof(int) * cn + sizeof(double) * (2 * dn.nb + 2 * dn.ng) * cn + sizeof(int) * cn + sizeof(int) * 5;
+    if (split_path(ctx, dn)) b += sizeof(float) * (dyn_hbuf_stride(dn) + dyn_abuf_stride(dn)) * cn;
+    return b;
+}
+
+size_t reserved_bytes(const cs_ctx* ctx) {
+    size_t b = ctx->direct.bytes() + ctx->err_word.bytes;
+    for (auto& kv : ctx->nets) b += kv.second->resident_bytes();
+    for (auto& sl : ctx->slots) b += sl->device_bytes();
+    return b;
+}
+
+size_t result_bytes(int64_t n) { return (size_t)n * (8 * 3 + 2 + 2 + 1 + 1); }
+
+void result_layout(char* base, int64_t n, cs_result* r) {
+    r->cost = (double*)base;                         // doubles first for alignment
+    r->max_re = r->cost + n;
+    r->min_zeta = r->max_re + n;
+    r->n_islands = (int16_t*)(r->min_zeta + n);
+    r->opf_iters = r->n_islands + n;
+    r->klass = (uint8_t*)(r->opf_iters + n);
+    r->severe = r->klass + n;
+    r->Vm = nullptr;
+    r->Va = nullptr;
+}
+
+}  // namespace csi
+
+namespace {
 
 // pack host vectors into one device blob
 struct Packer {
@@ -120,39 +93,38 @@ struct Packer {
     size_t add(const std::vector<T>& v) { return add(v.data(), v.size() * sizeof(T)); }
 };
 
-cs_status evaluate_impl(cs_ctx* ctx, Network* net, int level, const int32_t* ei, const int32_t* ej,
-                        int64_t n, const cs_result* out, cudaStream_t s, bool record) {
+}  // namespace
+
+cs_status csi::evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level, const int32_t* ei,
+                             const int32_t* ej, int64_t n, const cs_result* out, cudaStream_t s, bool record,
+                             int64_t chunk) {
     if (n <= 0) return CS_OK;
     const DevNet& dn = net->dev;
     const int nx = 2 * dn.nb + 2 * dn.ng;
-    const int64_t chunk = ctx->opt.chunk > 0 ? ctx->opt.chunk : 16384;
+    chunk = std::max<int64_t>(1, chunk);
     const int64_t cn = std::min<int64_t>(n, chunk);
-    // grids: persistent kernels sized from occupancy, capped per SM
-    const int cap_opf = ctx->opt.ctas_per_sm > 0 ? ctx->opt.ctas_per_sm : opf_ctas_per_sm();
-    const int cap_dyn = ctx->opt.ctas_per_sm > 0 ? ctx->opt.ctas_per_sm : 2;
-    const int g_opf = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->sms * cap_opf, cn));
-    const int g_dyn = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->sms * cap_dyn, cn));
-    const size_t per_opf = opf_scratch_doubles(dn);
-    const size_t per_dyn = dyn_scratch_doubles(dn);
+    const Grids gr = grids(ctx, dn, cn);
+    const int g_opf = gr.g_opf, g_dyn = gr.g_dyn;
+    const size_t per_opf = gr.per_opf, per_dyn = gr.per_dyn;
     const size_t need = std::max(per_opf * g_opf, per_dyn * g_dyn) * sizeof(double);
-    CS_CUDA(ctx->scratch.ensure(need));
-    CS_CUDA(ctx->isl.ensure(sizeof(int) * cn));
-    CS_CUDA(ctx->opfx.ensure(sizeof(double) * nx * cn));
-    CS_CUDA(ctx->opfst.ensure(sizeof(int) * cn));
-    CS_CUDA(ctx->counters.ensure(sizeof(int) * 5));
-    // packed Hessenberg matrices between the two halves of the FP32 screen
-    const bool split = ctx->opt.precision == CS_PREC_MIXED && dyn_split_fits(dn, ctx->device);
+    CS_CUDA(ws.scratch.ensure(need));
+    CS_CUDA(ws.isl.ensure(sizeof(int) * cn));
+    CS_CUDA(ws.opfx.ensure(sizeof(double) * nx * cn));
+    CS_CUDA(ws.opfst.ensure(sizeof(int) * cn));
+    CS_CUDA(ws.counters.ensure(sizeof(int) * 5));
+    // balanced and packed Hessenberg matrices between the kernels of the FP32 screen
+    const bool split = split_path(ctx, dn);
     if (split) {
-        CS_CUDA(ctx->hbuf.ensure(sizeof(float) * dyn_hbuf_stride(dn) * cn));
-        CS_CUDA(ctx->abuf.ensure(sizeof(float) * dyn_abuf_stride(dn) * cn));
+        CS_CUDA(ws.hbuf.ensure(sizeof(float) * dyn_hbuf_stride(dn) * cn));
+        CS_CUDA(ws.abuf.ensure(sizeof(float) * dyn_abuf_stride(dn) * cn));
     }
     if (!ctx->err_word.p) {
         CS_CUDA(ctx->err_word.ensure(sizeof(int) * 2));
         CS_CUDA(cudaMemset(ctx->err_word.p, 0, sizeof(int) * 2));
     }
-    int* counters = (int*)ctx->counters.p;
-    if (!ctx->ws_free) CS_CUDA(cudaEventCreateWithFlags(&ctx->ws_free, cudaEventDisableTiming));
-    if (ctx->ws_used) CS_CUDA(cudaStreamWaitEvent(s, ctx->ws_free, 0));
+    int* counters = (int*)ws.counters.p;
+    if (!ws.free) CS_CUDA(cudaEventCreateWithFlags(&ws.free, cudaEventDisableTiming));
+    if (ws.used) CS_CUDA(cudaStreamWaitEvent(s, ws.free, 0));
     for (int64_t c0 = 0; c0 < n; c0 += chunk) {
         const int64_t m = std::min(chunk, n - c0);
         EvalArgs a{};
@@ -174,7 +146,7 @@ cs_status evaluate_impl(cs_ctx* ctx, Network* net, int level, const int32_t* ei,
         a.sev_pairs = record ? (uint8_t*)net->sev_pairs[level]->p : nullptr;
         a.err = (int*)ctx->err_word.p;
         a.reruns = (int*)ctx->err_word.p + 1;
-        OpfOut o{(double*)ctx->opfx.p, (int*)ctx->opfst.p};
+        OpfOut o{(double*)ws.opfx.p, (int*)ws.opfst.p};
         CS_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * 5, s));
         auto mark = [&](int kind) -> cudaError_t {     // start event of a timed launch
             if (!ctx->timing) return cudaSuccess;
@@ -195,27 +167,25 @@ cs_status evaluate_impl(cs_ctx* ctx, Network* net, int level, const int32_t* ei,
             return r;
         };
         CS_CUDA(mark(0));
-        CS_CUDA(launch_islands(dn, a, (int*)ctx->isl.p, s));
+        CS_CUDA(launch_islands(dn, a, (int*)ws.isl.p, s));
         CS_CUDA(done());
         CS_CUDA(mark(1));
-        CS_CUDA(launch_opf(dn, a, (const int*)ctx->isl.p, o, ctx->opt.opf_tol, ctx->opt.opf_max_it,
-                           (double*)ctx->scratch.p, per_opf, std::min<int64_t>(g_opf, m), counters, s));
+        CS_CUDA(launch_opf(dn, a, (const int*)ws.isl.p, o, ctx->opt.opf_tol, ctx->opt.opf_max_it,
+                           (double*)ws.scratch.p, per_opf, std::min<int64_t>(g_opf, m), counters, s));
         CS_CUDA(done());
         CS_CUDA(mark(2));
         int nl = 0;
-        CS_CUDA(launch_dyn(dn, a, o, ctx->opt.damping_min, ctx->opt.precision, (double*)ctx->scratch.p, per_dyn,
-                           std::min<int64_t>(g_dyn, m), split ? (float*)ctx->abuf.p : nullptr,
-                           split ? (float*)ctx->hbuf.p : nullptr, ctx->sms,
+        CS_CUDA(launch_dyn(dn, a, o, ctx->opt.damping_min, ctx->opt.precision, (double*)ws.scratch.p, per_dyn,
+                           std::min<int64_t>(g_dyn, m), split ? (float*)ws.abuf.p : nullptr,
+                           split ? (float*)ws.hbuf.p : nullptr, ctx->sms,
                            counters + 1, &nl, s));
         CS_CUDA(done());
         ctx->launches += 2 + nl;
     }
-    CS_CUDA(cudaEventRecord(ctx->ws_free, s));
-    ctx->ws_used = true;
+    CS_CUDA(cudaEventRecord(ws.free, s));
+    ws.used = true;
     return CS_OK;
 }
-
-}  // namespace
 
 extern "C" {
 
@@ -229,6 +199,9 @@ void cs_default_options(cs_options* o) {
     o->ctas_per_sm = 0;
     o->chunk = 0;
     o->precision = CS_PREC_FP64;
+    o->hbm_budget = 0;
+    o->serve_slots = 2;
+    o->batch_cap = 16384;
 }
 
 cs_status cs_create(const cs_options* opt, cs_ctx** out) {
@@ -238,6 +211,8 @@ cs_status cs_create(const cs_options* opt, cs_ctx** out) {
     if (opt) c->opt = *opt; else cs_default_options(&c->opt);
     if (c->opt.opf_max_it < 0 || c->opt.opf_max_it > 10000 || !(c->opt.opf_tol > 0.0)) return CS_E_ARG;
     if (c->opt.precision != CS_PREC_FP64 && c->opt.precision != CS_PREC_MIXED) return CS_E_ARG;
+    if (c->opt.hbm_budget < 0 || c->opt.serve_slots < 1 || c->opt.serve_slots > 8 || c->opt.batch_cap < 1)
+        return CS_E_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return CS_E_CUDA;
     if (c->opt.device < 0 || c->opt.device >= ndev) return CS_E_ARG;
@@ -251,13 +226,13 @@ cs_status cs_create(const cs_options* opt, cs_ctx** out) {
 
 cs_status cs_destroy(cs_ctx* ctx) {
     if (!ctx) return CS_E_ARG;
+    serve_shutdown(ctx);
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    ctx->reqs.clear();
-    ctx->pool.clear();
+    ctx->sreqs.clear();
+    ctx->slots.clear();
     ctx->nets.clear();
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
-    if (ctx->ws_free) cudaEventDestroy(ctx->ws_free);
     if (ctx->req_stream) cudaStreamDestroy(ctx->req_stream);
     delete ctx;
     return CS_OK;
@@ -410,6 +385,13 @@ cs_status cs_load_network(cs_ctx* ctx, const cs_network_desc* d, int32_t* net_id
            o_lp = P.add(S.lev_ptr), o_lc = P.add(S.lev_col), o_tp = P.add(S.tgt_ptr), o_tg = P.add(S.tgt),
            o_up = P.add(S.upd_ptr), o_ua = P.add(S.upd_a), o_ub = P.add(S.upd_b), o_bbrp = P.add(S.blk_br_ptr),
            o_bbr = P.add(S.blk_br);
+    if (ctx->opt.hbm_budget > 0) {                    // admission by device footprint
+        const int64_t ne = (int64_t)nbr + ng;
+        const size_t add = P.host.size() + (size_t)nlev * (size_t)(ne + ne * (ne - 1) / 2);
+        if (reserved_bytes(ctx) + add > (size_t)ctx->opt.hbm_budget)
+            return fail(ctx, CS_E_NOMEM, "network would exceed hbm_budget: " + std::to_string(reserved_bytes(ctx) + add) +
+                                             " > " + std::to_string(ctx->opt.hbm_budget) + " bytes");
+    }
     CS_CUDA(net->blob.ensure(P.host.size()));
     CS_CUDA(cudaMemcpy(net->blob.p, P.host.data(), P.host.size(), cudaMemcpyHostToDevice));
     char* base = (char*)net->blob.p;
@@ -466,7 +448,8 @@ cs_status cs_load_network(cs_ctx* ctx, const cs_network_desc* d, int32_t* net_id
         r.klass = (uint8_t*)(ob + 28);
         r.severe = (uint8_t*)(ob + 29);
         for (int l = 0; l < nlev; ++l) {
-            cs_status st = evaluate_impl(ctx, net.get(), l, (const int*)din.p, (const int*)din.p + 1, 1, &r, 0, false);
+            cs_status st = evaluate_impl(ctx, ctx->direct, net.get(), l, (const int*)din.p, (const int*)din.p + 1, 1,
+                                         &r, 0, false, 1);
             if (st != CS_OK) return st;
             CS_CUDA(cudaDeviceSynchronize());
             char hb[32];
@@ -501,6 +484,7 @@ cs_status cs_unload_network(cs_ctx* ctx, int32_t net_id) {
     std::lock_guard<std::mutex> lock(ctx->mu);
     auto it = ctx->nets.find(net_id);
     if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
+    if (serve_uses_network(ctx, net_id)) return fail(ctx, CS_E_ARG, "network has queued or running requests");
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     ctx->nets.erase(it);
@@ -552,8 +536,15 @@ cs_status cs_evaluate_device(cs_ctx* ctx, int32_t net_id, int32_t level, const i
         !out->max_re || !out->min_zeta)
         return fail(ctx, CS_E_ARG, "NULL buffer");
     CS_CUDA(cudaSetDevice(ctx->device));
+    const int64_t chunk = default_chunk(ctx);
+    if (ctx->opt.hbm_budget > 0) {
+        const size_t want = workspace_bytes(ctx, *net, std::min<int64_t>(n, chunk));
+        if (want > ctx->direct.bytes() &&
+            reserved_bytes(ctx) - ctx->direct.bytes() + want > (size_t)ctx->opt.hbm_budget)
+            return fail(ctx, CS_E_NOMEM, "workspace would exceed hbm_budget");
+    }
     ctx->launches = 0;
-    return evaluate_impl(ctx, net, level, ei, ej, n, out, (cudaStream_t)stream, true);
+    return evaluate_impl(ctx, ctx->direct, net, level, ei, ej, n, out, (cudaStream_t)stream, true, chunk);
 }
 
 cs_status cs_sync(cs_ctx* ctx, void* stream) {
@@ -574,120 +565,6 @@ cs_status cs_sync(cs_ctx* ctx, void* stream) {
 }
 
 // ------------------------------------------------------------ requests ----
-static size_t result_bytes(int64_t n, int nb, bool volt) {
-    size_t b = (size_t)n * (1 + 1 + 2 + 2 + 8 * 3);
-    if (volt) b += (size_t)n * nb * 16;
-    return b;
-}
-
-static void carve(char* base, int64_t n, int nb, cs_result* r) {
-    // doubles first for alignment
-    r->cost = (double*)base;
-    r->max_re = r->cost + n;
-    r->min_zeta = r->max_re + n;
-    r->n_islands = (int16_t*)(r->min_zeta + n);
-    r->opf_iters = r->n_islands + n;
-    r->klass = (uint8_t*)(r->opf_iters + n);
-    r->severe = r->klass + n;
-    r->Vm = nullptr;
-    r->Va = nullptr;
-    (void)nb;
-}
-
-cs_status cs_submit_contingencies(cs_ctx* ctx, int32_t net_id, int32_t level, const int32_t* ei, const int32_t* ej,
-                                  int64_t n, uint64_t* request_id) {
-    if (!ctx) return CS_E_ARG;
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    if (!request_id || (n > 0 && (!ei || !ej))) return fail(ctx, CS_E_ARG, "NULL argument");
-    auto it = ctx->nets.find(net_id);
-    if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
-    Network* net = it->second.get();
-    if (level < 0 || level >= net->nlev) return fail(ctx, CS_E_ARG, "level out of range");
-    if (n < 0 || n > (int64_t)1 << 31) return fail(ctx, CS_E_ARG, "n out of range");
-    const int nE = net->dev.nE;
-    for (int64_t q = 0; q < n; ++q) {
-        const int a = ei[q], b = ej[q];
-        if (a < -1 || a >= nE || b < -1 || b >= nE || (a < 0 && b >= 0))
-            return fail(ctx, CS_E_ARG, "element id out of range at record " + std::to_string(q));
-    }
-    CS_CUDA(cudaSetDevice(ctx->device));
-    const size_t ob = result_bytes(std::max<int64_t>(n, 1), net->dev.nb, false);
-    const size_t ib = sizeof(int) * 2 * std::max<int64_t>(n, 1);
-    std::unique_ptr<Request> r;
-    for (size_t q = 0; q < ctx->pool.size(); ++q) {          // reuse buffers of a finished request
-        if (ctx->pool[q]->h_out_bytes >= ob && ctx->pool[q]->d_in.bytes >= ib) {
-            r = std::move(ctx->pool[q]);
-            ctx->pool.erase(ctx->pool.begin() + q);
-            break;
-        }
-    }
-    if (!r) {
-        r.reset(new Request());
-        CS_CUDA(r->d_in.ensure(ib));
-        CS_CUDA(r->d_out.ensure(ob));
-        CS_CUDA(cudaMallocHost(&r->h_out, ob));
-        r->h_out_bytes = ob;
-        CS_CUDA(cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming));
-    }
-    r->id = ctx->next_req++;
-    r->n = n;
-    r->nb = net->dev.nb;
-    cudaStream_t s = ctx->req_stream;
-    int* din = (int*)r->d_in.p;
-    if (n > 0) {
-        CS_CUDA(cudaMemcpyAsync(din, ei, sizeof(int) * n, cudaMemcpyHostToDevice, s));
-        CS_CUDA(cudaMemcpyAsync(din + n, ej, sizeof(int) * n, cudaMemcpyHostToDevice, s));
-        cs_result dr{};
-        carve((char*)r->d_out.p, n, net->dev.nb, &dr);
-        ctx->launches = 0;
-        cs_status st = evaluate_impl(ctx, net, level, din, din + n, n, &dr, s, true);
-        if (st != CS_OK) return st;
-        CS_CUDA(cudaMemcpyAsync(r->h_out, r->d_out.p, result_bytes(n, net->dev.nb, false), cudaMemcpyDeviceToHost, s));
-    }
-    CS_CUDA(cudaEventRecord(r->done, s));
-    *request_id = r->id;
-    ctx->reqs[r->id] = std::move(r);
-    return CS_OK;
-}
-
-cs_status cs_poll(cs_ctx* ctx, uint64_t request_id, int32_t timeout_us, const cs_result* out) {
-    if (!ctx) return CS_E_ARG;
-    Request* r = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(ctx->mu);
-        auto it = ctx->reqs.find(request_id);
-        if (it == ctx->reqs.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown request");
-        r = it->second.get();
-    }
-    const auto t0 = std::chrono::steady_clock::now();
-    for (;;) {
-        cudaError_t q = cudaEventQuery(r->done);
-        if (q == cudaSuccess) break;
-        if (q != cudaErrorNotReady) return cuda_fail(ctx, q, "cudaEventQuery");
-        const auto us = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
-        if (us >= timeout_us) return CS_PENDING;
-        std::this_thread::sleep_for(std::chrono::microseconds(std::min<long long>(50, timeout_us - us)));
-    }
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    const int64_t n = r->n;
-    if (n > 0) {
-        if (!out) return fail(ctx, CS_E_ARG, "NULL out");
-        cs_result h{};
-        carve((char*)r->h_out, n, r->nb, &h);
-        if (out->klass) std::memcpy(out->klass, h.klass, n);
-        if (out->severe) std::memcpy(out->severe, h.severe, n);
-        if (out->n_islands) std::memcpy(out->n_islands, h.n_islands, 2 * n);
-        if (out->opf_iters) std::memcpy(out->opf_iters, h.opf_iters, 2 * n);
-        if (out->cost) std::memcpy(out->cost, h.cost, 8 * n);
-        if (out->max_re) std::memcpy(out->max_re, h.max_re, 8 * n);
-        if (out->min_zeta) std::memcpy(out->min_zeta, h.min_zeta, 8 * n);
-    }
-    auto it2 = ctx->reqs.find(request_id);
-    if (ctx->pool.size() < 64) ctx->pool.push_back(std::move(it2->second));
-    ctx->reqs.erase(it2);
-    return CS_OK;
-}
-
 // ---------------------------------------------------------- Risk Index ----
 cs_status cs_risk_index(cs_ctx* ctx, int32_t net_id, int32_t level, const double* lambda, int32_t mode,
                         double* R_out, int64_t* n_missing) {
