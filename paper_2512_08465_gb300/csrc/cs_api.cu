@@ -56,7 +56,7 @@ size_t workspace_bytes(const cs_ctx* ctx, const Network& net, int64_t chunk) {
 }
 
 size_t reserved_bytes(const cs_ctx* ctx) {
-    size_t b = ctx->direct.bytes() + ctx->err_word.bytes;
+    size_t b = ctx->direct.bytes() + ctx->direct2.bytes() + ctx->err_word.bytes;
     for (auto& kv : ctx->nets) b += kv.second->resident_bytes();
     for (auto& sl : ctx->slots) b += sl->device_bytes();
     return b;
@@ -220,6 +220,9 @@ cs_status cs_create(const cs_options* opt, cs_ctx** out) {
     if (cudaSetDevice(c->device) != cudaSuccess) return CS_E_CUDA;
     if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) return CS_E_CUDA;
     if (cudaStreamCreateWithFlags(&c->req_stream, cudaStreamNonBlocking) != cudaSuccess) return CS_E_CUDA;
+    if (cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking) != cudaSuccess) return CS_E_CUDA;
+    if (cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess) return CS_E_CUDA;
+    if (cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) return CS_E_CUDA;
     *out = c.release();
     return CS_OK;
 }
@@ -234,6 +237,9 @@ cs_status cs_destroy(cs_ctx* ctx) {
     ctx->nets.clear();
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     if (ctx->req_stream) cudaStreamDestroy(ctx->req_stream);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
     delete ctx;
     return CS_OK;
 }
@@ -538,13 +544,41 @@ cs_status cs_evaluate_device(cs_ctx* ctx, int32_t net_id, int32_t level, const i
     CS_CUDA(cudaSetDevice(ctx->device));
     const int64_t chunk = default_chunk(ctx);
     if (ctx->opt.hbm_budget > 0) {
-        const size_t want = workspace_bytes(ctx, *net, std::min<int64_t>(n, chunk));
-        if (want > ctx->direct.bytes() &&
-            reserved_bytes(ctx) - ctx->direct.bytes() + want > (size_t)ctx->opt.hbm_budget)
+        const size_t want = workspace_bytes(ctx, *net, std::min<int64_t>(n, chunk)) * (n > chunk ? 2 : 1);
+        const size_t have = ctx->direct.bytes() + ctx->direct2.bytes();
+        if (want > have && reserved_bytes(ctx) - have + want > (size_t)ctx->opt.hbm_budget)
             return fail(ctx, CS_E_NOMEM, "workspace would exceed hbm_budget");
     }
     ctx->launches = 0;
-    return evaluate_impl(ctx, ctx->direct, net, level, ei, ej, n, out, (cudaStream_t)stream, true, chunk);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n <= chunk) return evaluate_impl(ctx, ctx->direct, net, level, ei, ej, n, out, s, true, chunk);
+    // Several chunks: they alternate between two workspaces on the caller's stream and
+    // a second stream, so that one chunk's kernels fill the SMs its predecessor's tail
+    // leaves idle.  The second stream starts after the caller's prior work and the
+    // caller's stream resumes after the last chunk of either.
+    CS_CUDA(cudaEventRecord(ctx->fork_ev, s));
+    CS_CUDA(cudaStreamWaitEvent(ctx->aux_stream, ctx->fork_ev, 0));
+    int q = 0;
+    for (int64_t c0 = 0; c0 < n; c0 += chunk, ++q) {
+        const int64_t m = std::min(chunk, n - c0);
+        cs_result o = *out;
+        o.klass = out->klass + c0;
+        o.severe = out->severe + c0;
+        o.n_islands = out->n_islands + c0;
+        o.opf_iters = out->opf_iters + c0;
+        o.cost = out->cost + c0;
+        o.max_re = out->max_re + c0;
+        o.min_zeta = out->min_zeta + c0;
+        o.Vm = out->Vm ? out->Vm + c0 * net->dev.nb : nullptr;
+        o.Va = out->Va ? out->Va + c0 * net->dev.nb : nullptr;
+        const bool second = (q & 1) != 0;
+        cs_status st = evaluate_impl(ctx, second ? ctx->direct2 : ctx->direct, net, level, ei + c0, ej + c0, m, &o,
+                                     second ? ctx->aux_stream : s, true, chunk);
+        if (st != CS_OK) return st;
+    }
+    CS_CUDA(cudaEventRecord(ctx->join_ev, ctx->aux_stream));
+    CS_CUDA(cudaStreamWaitEvent(s, ctx->join_ev, 0));
+    return CS_OK;
 }
 
 cs_status cs_sync(cs_ctx* ctx, void* stream) {

@@ -128,7 +128,9 @@ struct cs_ctx {
     std::map<int, std::unique_ptr<csi::Network>> nets;
     int next_net = 1;
     cudaStream_t req_stream = nullptr;            // library stream (risk index, base cases)
-    csi::Workspace direct;                        // workspace of cs_evaluate_device and base cases
+    csi::Workspace direct, direct2;               // workspaces of cs_evaluate_device (chunks alternate) and base cases
+    cudaStream_t aux_stream = nullptr;            // second stream of cs_evaluate_device
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     csi::DevBuf err_word;                         // [0] device error bits, [1] FP64 re-run count
     int64_t launches = 0;
     // serving: request queue, batch slots, scheduler thread
