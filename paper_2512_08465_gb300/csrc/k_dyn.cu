@@ -85,8 +85,8 @@ __device__ __forceinline__ void st(double* p, cplx v) { p[0] = v.re; p[1] = v.im
 struct DShared {
     double red[2][kThreads];
     int ired[kThreads];
-    double x[3];
-    double xs[2][3];                 // next bulge column, double-buffered by step parity
+    double x[3];                     // next bulge column
+    double u[4];                     // reflector of the current step: u0, u1, u2, beta
     double part[2][kThreads / 32];   // per-warp partial sums, double-buffered
     int lo, hi, its, fail, scen, m, nn;
     double hmax;
@@ -341,16 +341,30 @@ __device__ void hqr_global(T* A, const int n, double* wr, double* wi, DShared& s
             sh.x[2] = h10 * h21;
         }
         __syncthreads();
-        double x0 = sh.x[0], x1 = sh.x[1], x2 = sh.x[2];
+        // The reflector of each step is computed once, by thread 0, and broadcast: on this
+        // GPU a warp-wide FP64 instruction costs the FP64 pipe the same whatever its active
+        // lanes, so every warp computing it would multiply that cost by the warp count.
         for (int k = lo; k <= hi - 1; ++k) {
             const int len = (k + 2 <= hi) ? 3 : 2;
-            const double t2 = x1 * x1 + (len == 3 ? x2 * x2 : 0.0);
             const bool more = (k + 1 <= hi - 1);
-            if (t2 != 0.0) {
-                const double nrm = sqrt(x0 * x0 + t2);
-                const double al = (x0 >= 0.0) ? -nrm : nrm;
-                const T u0 = (T)(x0 - al), u1 = (T)x1, u2 = (len == 3) ? (T)x2 : (T)0;
-                const T bt = (T)(2.0 / ((x0 - al) * (x0 - al) + t2));
+            if (tid == 0) {
+                const double x0 = sh.x[0], x1 = sh.x[1], x2 = (len == 3) ? sh.x[2] : 0.0;
+                const double t2 = x1 * x1 + x2 * x2;
+                if (t2 != 0.0) {
+                    const double nrm = sqrt(x0 * x0 + t2);
+                    const double al = (x0 >= 0.0) ? -nrm : nrm;
+                    sh.u[0] = x0 - al;
+                    sh.u[1] = x1;
+                    sh.u[2] = x2;
+                    sh.u[3] = 2.0 / ((x0 - al) * (x0 - al) + t2);
+                } else {
+                    sh.u[3] = 0.0;                 // no reflector this step
+                }
+            }
+            __syncthreads();
+            const T bt = (T)sh.u[3];
+            if (bt != (T)0) {
+                const T u0 = (T)sh.u[0], u1 = (T)sh.u[1], u2 = (len == 3) ? (T)sh.u[2] : (T)0;
                 const int c0 = (k > lo) ? k - 1 : lo;
                 for (int j = c0 + tid; j <= hi; j += kThreads) {   // rows k..k+len-1
                     T* p0 = A + (size_t)k * n + j;
@@ -371,19 +385,16 @@ __device__ void hqr_global(T* A, const int n, double* wr, double* wi, DShared& s
                     p0[0] -= d * u0;
                     p0[1] -= d * u1;
                     if (len == 3) p0[2] -= d * u2;
-                    if (i > k && i <= k + 3) sh.xs[k & 1][i - k - 1] = (double)p0[0];   // next bulge column
+                    if (i > k && i <= k + 3) sh.x[i - k - 1] = (double)p0[0];   // next bulge column
                 }
                 __syncthreads();
-                if (more) {
-                    x0 = sh.xs[k & 1][0];
-                    x1 = sh.xs[k & 1][1];
-                    x2 = (k + 3 <= hi) ? sh.xs[k & 1][2] : 0.0;
-                }
             } else if (more) {
-                x0 = A[(size_t)(k + 1) * n + k];
-                x1 = A[(size_t)(k + 2) * n + k];
-                x2 = (k + 3 <= hi) ? (double)A[(size_t)(k + 3) * n + k] : 0.0;
-                __syncthreads();                           // all read before the next step writes column k
+                if (tid == 0) {
+                    sh.x[0] = A[(size_t)(k + 1) * n + k];
+                    sh.x[1] = A[(size_t)(k + 2) * n + k];
+                    sh.x[2] = (k + 3 <= hi) ? (double)A[(size_t)(k + 3) * n + k] : 0.0;
+                }
+                __syncthreads();
             }
         }
         for (int i = lo + 2 + tid; i <= hi; i += kThreads) {
