@@ -158,58 +158,67 @@ __device__ void block_reduce(RedBuf& rb, double (&val)[K], const int (&ops)[K], 
 
 // Inverse of the symmetric part of a 4x4 pivot block: LU factorisation with
 // partial pivoting, forward/back substitution for each column of the identity,
-// then symmetrisation of the result.  (Near the end of
-// the interior-point iteration some pivot blocks are nearly singular; the
-// LU-based inverse keeps the error low-rank, which the iterative refinement
-// removes, where a Gauss-Jordan inverse did not.)  Returns false if a pivot
-// is exactly zero or not finite.
-__device__ bool inv4(const double* A, double* Ainv) {
+// then symmetrisation of the result.  (Near the end of the interior-point
+// iteration some pivot blocks are nearly singular; the LU-based inverse keeps
+// the error low-rank, which the iterative refinement removes, where a
+// Gauss-Jordan inverse did not.)  Four lanes of one warp (q = 0..3, aligned
+// to a multiple of 4) take one pivot: each repeats the factorisation (one
+// instruction stream, so the FP64 pipe pays for it once) and solves for column
+// q.  Returns false, on all four lanes, if a pivot is exactly zero or not
+// finite.
+__device__ bool inv4(const double* A, double* Ainv, int q) {
+    const unsigned grp = 0xFu << (threadIdx.x & 28);
     double a[4][4], dinv[4];
     int piv[4] = {0, 1, 2, 3};
     for (int r = 0; r < 4; ++r)                  // symmetric part of the updated pivot
         for (int c = 0; c < 4; ++c) a[r][c] = 0.5 * (A[4 * r + c] + A[4 * c + r]);
-    for (int c = 0; c < 4; ++c) {
+    bool ok = true;
+    for (int c = 0; c < 4 && ok; ++c) {
         int p = c;
         double best = fabs(a[c][c]);
         for (int r = c + 1; r < 4; ++r)
             if (fabs(a[r][c]) > best) { best = fabs(a[r][c]); p = r; }
-        if (!(best > 0.0) || !isfinite(best)) return false;
+        if (!(best > 0.0) || !isfinite(best)) { ok = false; break; }
         if (p != c) {
-            for (int q = 0; q < 4; ++q) { double t = a[c][q]; a[c][q] = a[p][q]; a[p][q] = t; }
+            for (int k = 0; k < 4; ++k) { double t = a[c][k]; a[c][k] = a[p][k]; a[p][k] = t; }
             int t = piv[c]; piv[c] = piv[p]; piv[p] = t;
         }
         dinv[c] = 1.0 / a[c][c];                  // one division per pivot
         for (int r = c + 1; r < 4; ++r) {
             a[r][c] *= dinv[c];
             const double m = a[r][c];
-            for (int q = c + 1; q < 4; ++q) a[r][q] -= m * a[c][q];
+            for (int k = c + 1; k < 4; ++k) a[r][k] -= m * a[c][k];
         }
     }
-    for (int j = 0; j < 4; ++j) {
-        double y[4];
+    // the group reads A above before any lane of it writes the inverse (A and Ainv
+    // are different arrays, but the symmetrisation below reads what others wrote)
+    double y[4];
+    if (ok) {
         for (int i = 0; i < 4; ++i) {
-            double v = (piv[i] == j) ? 1.0 : 0.0;
-            for (int q = 0; q < i; ++q) v -= a[i][q] * y[q];
+            double v = (piv[i] == q) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) v -= a[i][k] * y[k];
             y[i] = v;
         }
         for (int i = 3; i >= 0; --i) {
             double v = y[i];
-            for (int q = i + 1; q < 4; ++q) v -= a[i][q] * y[q];
+            for (int k = i + 1; k < 4; ++k) v -= a[i][k] * y[k];
             y[i] = v * dinv[i];
         }
-        for (int i = 0; i < 4; ++i) Ainv[4 * i + j] = y[i];
+        for (int i = 0; i < 4; ++i) Ainv[4 * i + q] = y[i];
     }
-    // Symmetrise the inverse.  Only the lower blocks are stored and updated with
-    // L(i,k) U(j,k)^T, which assumes a symmetric pivot inverse; an LU-based inverse of
-    // a nearly singular symmetric block is far from symmetric in rounding, and the
-    // factorisation would then not be a consistent L D L^T (refinement stalls).
-    for (int r = 0; r < 4; ++r)
-        for (int c = r + 1; c < 4; ++c) {
-            const double m = 0.5 * (Ainv[4 * r + c] + Ainv[4 * c + r]);
-            Ainv[4 * r + c] = m;
-            Ainv[4 * c + r] = m;
-        }
-    return true;
+    __syncwarp(grp);
+    // Symmetrise.  Only the lower blocks are stored and updated with L(i,k) U(j,k)^T,
+    // which assumes a symmetric pivot inverse; an LU-based inverse of a nearly singular
+    // symmetric block is far from symmetric in rounding, and the factorisation would
+    // then not be a consistent L D L^T (refinement stalls).
+    double t[4];
+    if (ok)
+        for (int i = 0; i < 4; ++i) t[i] = Ainv[4 * q + i];   // row q, written by lane i
+    __syncwarp(grp);
+    if (ok)
+        for (int i = 0; i < 4; ++i) Ainv[4 * i + q] = 0.5 * (y[i] + t[i]);
+    __syncwarp(grp);
+    return ok;
 }
 
 // One branch at the current iterate: flows, derivatives, weighted Hessian,
@@ -1011,9 +1020,12 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                     A[4 * r + c] = acc;
                 }
                 __syncthreads();
-                for (int w = net.lev_ptr[lev] + tid; w < net.lev_ptr[lev + 1]; w += kThreads) {
-                    const int j = net.lev_col[w];
-                    if (!inv4(W + L.Db + 16 * j, W + L.Di + 16 * j)) sc.fail = 1;
+                {
+                    const int c0 = net.lev_ptr[lev], nc = net.lev_ptr[lev + 1] - c0;
+                    for (int w = tid; w < 4 * nc; w += kThreads) {     // four lanes per pivot
+                        const int j = net.lev_col[c0 + (w >> 2)];
+                        if (!inv4(W + L.Db + 16 * j, W + L.Di + 16 * j, w & 3)) sc.fail = 1;
+                    }
                 }
                 __syncthreads();
                 for (int w = tid; w < 16 * (t1 - t0); w += kThreads) {
