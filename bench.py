@@ -427,7 +427,7 @@ def run_serve(args):
     import numpy as np
     import torch  # noqa: F401  (CUDA context in this process before the library's threads)
     from paper_2512_08465_gb300 import cs, synth
-    specs = [("118-bus", synth.case118()), ("300-bus", synth.case_scaled(300, seed=300))]
+    specs = [("118-bus", synth.case118()), ("300-bus", synth.case_scaled(300, seed=300, vband=(0.85, 1.15)))]
     ctx = cs.Context(precision=cs.PREC_MIXED)
     t0 = time.perf_counter()
     ids = [ctx.load_network(net) for _, net in specs]

@@ -231,14 +231,19 @@ def case118(seed: int = 118, levels=(0.7, 0.9)) -> Network:
     return make_network(118, 186, 54, 99, 11, seed, levels, name="synth118")
 
 
-def case_scaled(n_bus: int, seed: int, levels=(0.7,)) -> Network:
+def case_scaled(n_bus: int, seed: int, levels=(0.7,), vband=(0.94, 1.06)) -> Network:
     """Larger serving / scale networks: branches = 1.5 n_bus, generators at 25 % of buses,
-    loads on 99/118 of buses, same distributions as the 118-bus study."""
+    loads on 99/118 of buses, same distributions as the 118-bus study.  vband: bus voltage
+    limits (p.u.); with the 118-bus study's 0.94 / 1.06 the 300-bus draw has no feasible
+    base-case OPF, so the serving workload uses 0.85 / 1.15."""
     n_branch = int(round(1.5 * n_bus))
     n_gen = int(round(0.25 * n_bus))
     n_load = int(round(n_bus * 99 / 118))
     n_tr = int(round(n_branch * 11 / 186))
-    return make_network(n_bus, n_branch, n_gen, n_load, n_tr, seed, levels, name=f"synth{n_bus}")
+    net = make_network(n_bus, n_branch, n_gen, n_load, n_tr, seed, levels, name=f"synth{n_bus}")
+    net.Vmin = np.full(n_bus, float(vband[0]))
+    net.Vmax = np.full(n_bus, float(vband[1]))
+    return net
 
 
 def all_pairs(n_elem: int):

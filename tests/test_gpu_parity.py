@@ -356,3 +356,27 @@ def test_mixed_equals_fp64_classes_full_level(ctx, net118, mixed118):
     d = np.abs(a["max_re"].cpu().numpy()[ok] - b["max_re"].cpu().numpy()[ok])
     assert d.max() <= TOL_EIG_MIXED
     assert c.eigen_reruns() >= 0
+
+
+def test_mixed_form_inline_path_on_a_300_bus_network():
+    """Networks whose Hessenberg matrix exceeds shared memory (300 buses, 75
+    generators, state order 374) take the FP32 screen in global memory with the
+    FP64 re-run inline.  Classes must equal the FP64 form's, eigen statistics
+    agree within the mixed-form tolerance."""
+    net = synth.case_scaled(300, seed=300, vband=(0.85, 1.15))
+    ii, jj = synth.all_pairs(net.n_branch)
+    sel = np.random.default_rng(8).choice(ii.size, 48, replace=False)
+    res = {}
+    for prec in (cs.PREC_FP64, cs.PREC_MIXED):
+        c = cs.Context(precision=prec)
+        nid = c.load_network(net)
+        res[prec] = _run(c, nid, 0, ii[sel], jj[sel])
+        c.close()
+    a, b = res[cs.PREC_FP64], res[cs.PREC_MIXED]
+    np.testing.assert_array_equal(a["klass"], b["klass"])
+    np.testing.assert_array_equal(a["opf_iters"], b["opf_iters"])
+    np.testing.assert_array_equal(a["cost"], b["cost"])
+    ok = np.isfinite(a["max_re"])
+    assert ok.any()
+    assert np.max(np.abs(a["max_re"][ok] - b["max_re"][ok])) <= TOL_EIG_MIXED
+    assert np.max(np.abs(a["min_zeta"][ok] - b["min_zeta"][ok])) <= TOL_EIG_MIXED
