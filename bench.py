@@ -271,14 +271,14 @@ def run_ours(args):
         kms, kcnt = ctx.kernel_times()
         ctx.set_timing(False)
         ms = sum(step_ms) / len(step_ms)
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        from paper_2512_08465_gb300 import shard
+        ms_max = shard.max_over_ranks(ms, device=dev)            # replicas: the slowest rank sets the step
         if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             torch.distributed.barrier()
         klass = [outs[lv][0]["klass"].cpu().numpy() for lv in (0, 1)]
         stats = {f: [outs[lv][0][f].cpu().numpy() for lv in (0, 1)] for f in ("max_re", "min_zeta")}
         iters = sum(int(outs[lv][q]["opf_iters"].to(torch.int64).sum().item()) for lv in (0, 1) for q in (0, 1))
-        return dict(ms=float(t.item()), wall=wall, kms=kms, kcnt=kcnt, clocks=clk, launches=launches[0],
+        return dict(ms=ms_max, wall=wall, kms=kms, kcnt=kcnt, clocks=clk, launches=launches[0],
                     klass=klass, iters=iters, stats=stats)
 
     ctx_m, nid_m = make(cs.PREC_MIXED)
