@@ -319,9 +319,20 @@ def run_ours(args):
                 "work": "10 n^3 flops per converged scenario, n = 5 x in-service generators - 1",
                 "achieved": _algorithmic_flops(net, mixed["klass"], E) / (kms["dyn"] / args.steps / 1e3) / 1e12},
     }
+    # DRAM traffic per launch: bytes per scenario from the ncu captures of the same kernels on
+    # the first 2,048 pairs (profiles/*_118bus_2048pairs.md: OPF 44.2 GB for 1,877 OPFs; front
+    # 4.35 GB + cluster Hessenberg 0.73 GB + QR 0.26 GB for 1,742 converged scenarios), scaled
+    # by the scenarios an average launch of this step processes
+    n_opf = sum(int(np.sum(k != 1)) for k in mixed["klass"])
+    n_conv = sum(int(np.sum((k == 0) | (k == 4) | (k == 5) | (k == 6))) for k in mixed["klass"])
+    per_scen = {"opf": (44.2e9 / 1877, n_opf), "dyn": ((4.354e9 + 0.726e9 + 0.263e9) / 1742, n_conv)}
     for k, r in roofs.items():
+        launches = max(1.0, kcnt[k] / args.steps)
+        b_per, units = per_scen[k]
         r.update({"launches_per_step": kcnt[k] / args.steps, "avg_launch_ms": kms[k] / max(1, kcnt[k]),
-                  "traffic": None})
+                  "traffic": b_per * units / launches,
+                  "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum on 2,048 pairs, scaled "
+                                    "per scenario to an average launch of the step (profiles/)"})
     dominant = max(("opf", "dyn"), key=lambda k: kms[k])
     roof = roofs[dominant]
     roof_other = roofs["dyn" if dominant == "opf" else "opf"]
