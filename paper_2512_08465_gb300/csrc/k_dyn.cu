@@ -901,6 +901,8 @@ hess_cluster_kernel(EvalArgs a, OpfOut o, const float* __restrict__ abuf, size_t
 #define CS_QR_THREADS 256
 #endif
 constexpr int kQrThreads = CS_QR_THREADS;
+// the column phase of a bulge step covers at most 2 kQrThreads rows (orders up to 32 kHsCols + 1)
+static_assert(2 * kQrThreads > 32 * kHsCols + 1, "QR column phase: at most two rows per thread");
 
 __device__ __forceinline__ void eig2f(float p, float q, float r, float s, float* re, float* im) {
     const float hm = 0.5f * (p - s);
@@ -1031,6 +1033,10 @@ hqr_smem_kernel(EvalArgs a, OpfOut o, const float* __restrict__ hbuf, size_t hst
                 x2 = h10 * h21;
             }
             __syncthreads();              // every warp has read the block and the shifts before the sweep writes
+            // rows this thread updates in the column phase (fixed for the sweep; the order is
+            // at most 2 * kQrThreads on this path), and their packed offsets
+            const int rbi0 = (lo + tid <= hi) ? rb[lo + tid] : 0;
+            const int rbi1 = (lo + tid + kQrThreads <= hi) ? rb[lo + tid + kQrThreads] : 0;
             for (int k = lo; k <= hi - 1; ++k) {
                 const int len = (k + 2 <= hi) ? 3 : 2;
                 const float t2 = x1 * x1 + (len == 3 ? x2 * x2 : 0.0f);
@@ -1052,8 +1058,8 @@ hqr_smem_kernel(EvalArgs a, OpfOut o, const float* __restrict__ hbuf, size_t hst
                     }
                     __syncthreads();
                     const int r1 = (k + 3 < hi) ? k + 3 : hi;
-                    for (int i = lo + tid; i <= r1; i += kQrThreads) {     // columns k..k+len-1
-                        float* p = H + rb[i] + k;
+                    for (int i = lo + tid, m = 0; i <= r1; i += kQrThreads, ++m) {   // columns k..k+len-1
+                        float* p = H + (m == 0 ? rbi0 : rbi1) + k;
                         const float q0 = p[0], q1 = p[1];
                         const float q2 = (len == 3) ? p[2] : 0.0f;
                         const float d = (q0 * u0 + q1 * u1 + q2 * u2) * bt;
