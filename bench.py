@@ -284,6 +284,26 @@ def run_ours(args):
     ctx_m, nid_m = make(cs.PREC_MIXED)
     mixed = measure(ctx_m, nid_m, args.warmup, args.steps, clocks=True)
     reruns = ctx_m.eigen_reruns()
+    # Monte-Carlo Risk Index (uncertain failure rates): 10,000 seeded rate vectors against the
+    # level-0 tables of this step, exact per sample; outside the timed step
+    gen = torch.Generator(device=dev).manual_seed(2512)
+    lam_mc = 0.01 + 0.99 * torch.rand((10000, E), dtype=torch.float64, device=dev, generator=gen)
+    r_mc = torch.empty_like(lam_mc)
+    ctx_m.risk_index_batch(nid_m, 0, lam_mc, r_mc, cs.RISK_ORDERED, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx_m.risk_index_batch(nid_m, 0, lam_mc, r_mc, cs.RISK_ORDERED, stream)
+    e1.record(stream)
+    e1.synchronize()
+    ctx_m.sync(stream)
+    mc_ms = e0.elapsed_time(e1)
+    mc = {"samples": int(lam_mc.shape[0]), "elements": E, "ms": mc_ms,
+          "samples_per_s": lam_mc.shape[0] / (mc_ms / 1e3),
+          "R_p50_p95_of_max_element": [float(x) for x in torch.quantile(r_mc.max(dim=1).values,
+                                                                          torch.tensor([0.5, 0.95], device=dev,
+                                                                                       dtype=torch.float64)).cpu()]}
+    del lam_mc, r_mc
     ctx_d, nid_d = make(cs.PREC_FP64)
     fp64 = measure(ctx_d, nid_d, 1, args.steps)
     same = all(np.array_equal(a, b) for a, b in zip(mixed["klass"], fp64["klass"]))
@@ -384,6 +404,7 @@ def run_ours(args):
                           "mixed_max_abs_dev": dev},
             "roofline": roof,
             "roofline_other": roof_other,
+            "risk_index_monte_carlo": mc,
             "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
             "kernel_share": share,
             "e2e": {"value": 2 * npair * world / (e2e_step / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -222,6 +222,18 @@ cs_status cs_risk_reduce_device(int32_t n_elem, const uint8_t* S1, const uint8_t
 cs_status cs_enumerate_pairs_device(int32_t n_elem, int64_t first, int64_t count,
                                     int32_t* elem_i, int32_t* elem_j, void* stream);
 
+/* Monte-Carlo form of the Risk Index over uncertain failure rates (the
+ * paper's outlook, Section VI): R for n_samples rate vectors against the
+ * context's severity tables of (net_id, level), each sample exactly as
+ * cs_risk_index computes it (bit-identical), pairs never evaluated counting 0.
+ * lambda: DEVICE array [n_samples * (n_branch + n_gen)], sample-major; R:
+ * DEVICE array of the same shape.  Asynchronous on `stream` after a device
+ * synchronisation (the tables may have been written on any stream).  A rate
+ * outside [2^-30, 2^10] makes that entry NaN and the next cs_sync return
+ * CS_E_ARG. */
+cs_status cs_risk_index_batch(cs_ctx* ctx, int32_t net_id, int32_t level, const double* lambda,
+                              int64_t n_samples, int32_t mode, double* R, void* stream);
+
 /* cs_risk_index without any device allocation (the paper has no counterpart:
  * this is a deployment variant of the Eq. 3 reduction).  Same arguments,
  * result and errors as cs_risk_index, bit for bit.  For callers that must not

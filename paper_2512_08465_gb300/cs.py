@@ -31,7 +31,7 @@ EXPORTS = ("cs_default_options", "cs_create", "cs_destroy", "cs_load_network", "
            "cs_base_result", "cs_evaluate_device", "cs_sync", "cs_submit_contingencies", "cs_poll",
            "cs_risk_index", "cs_risk_reduce_device", "cs_enumerate_pairs_device", "cs_last_error",
            "cs_last_launch_count", "cs_set_timing", "cs_kernel_times", "cs_alu_peak", "cs_eigen_reruns",
-           "cs_risk_index_static", "cs_network_stats", "cs_serving_stats")
+           "cs_risk_index_static", "cs_network_stats", "cs_serving_stats", "cs_risk_index_batch")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -100,6 +100,7 @@ def load_library(build_if_missing: bool = True):
         "cs_risk_index_static": (i32, [P, i32, i32, P, i32, P, ctypes.POINTER(i64)]),
         "cs_network_stats": (i32, [P, i32, P, i32]),
         "cs_serving_stats": (i32, [P, P, i32]),
+        "cs_risk_index_batch": (i32, [P, i32, i32, P, i64, i32, P, P]),
         "cs_risk_reduce_device": (i32, [i32, P, P, P, i32, P, P]),
         "cs_enumerate_pairs_device": (i32, [i32, i64, i64, P, P, P]),
         "cs_last_error": (ctypes.c_char_p, [P]),
@@ -315,6 +316,12 @@ class Context:
         st = self.lib.cs_risk_index(self.h, net_id, level, _ptr(lam), mode, _ptr(R), ctypes.byref(miss))
         self._check(st, "cs_risk_index")
         return R, miss.value
+
+    def risk_index_batch(self, net_id: int, level: int, lam, R, mode: int = RISK_ORDERED, stream=None):
+        """cs_risk_index_batch: R[s, i] for device rate samples lam[s, i] (float64, sample-major)."""
+        st = self.lib.cs_risk_index_batch(self.h, net_id, level, _ptr(lam), lam.shape[0], mode, _ptr(R),
+                                          _stream_handle(stream))
+        self._check(st, "cs_risk_index_batch")
 
     def risk_index_static(self, net_id: int, level: int, lam, mode: int = RISK_ORDERED):
         """cs_risk_index_static: the same reduction with its device scratch in a

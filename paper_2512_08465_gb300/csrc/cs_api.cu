@@ -592,6 +592,8 @@ cs_status cs_sync(cs_ctx* ctx, void* stream) {
         if (e) {
             CS_CUDA(cudaMemset(ctx->err_word.p, 0, sizeof(int)));
             if (e & ERR_BAD_ELEMENT) return fail(ctx, CS_E_ARG, "element id out of range (record marked 255)");
+            if (e & ERR_BAD_RATE)
+                return fail(ctx, CS_E_ARG, "failure rate outside [2^-30, 2^10] in a batched Risk Index (entry NaN)");
             return fail(ctx, CS_E_NUMERIC, "device error word " + std::to_string(e));
         }
     }
@@ -629,6 +631,32 @@ cs_status cs_risk_index(cs_ctx* ctx, int32_t net_id, int32_t level, const double
     CS_CUDA(cudaMemcpyAsync(&miss, dm.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CS_CUDA(cudaStreamSynchronize(s));
     if (n_missing) *n_missing = miss;
+    return CS_OK;
+}
+
+cs_status cs_risk_index_batch(cs_ctx* ctx, int32_t net_id, int32_t level, const double* lambda, int64_t n_samples,
+                              int32_t mode, double* R, void* stream) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    auto it = ctx->nets.find(net_id);
+    if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
+    Network* net = it->second.get();
+    if (level < 0 || level >= net->nlev || n_samples < 0 || (n_samples > 0 && (!lambda || !R)) ||
+        (mode != CS_RISK_EQ3 && mode != CS_RISK_ORDERED))
+        return fail(ctx, CS_E_ARG, "bad level, sample count, mode or NULL");
+    if (n_samples == 0) return CS_OK;
+    CS_CUDA(cudaSetDevice(ctx->device));
+    if (!ctx->err_word.p) {
+        CS_CUDA(ctx->err_word.ensure(sizeof(int) * 2));
+        CS_CUDA(cudaMemset(ctx->err_word.p, 0, sizeof(int) * 2));
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // severity tables are written by evaluations on any stream of the context
+    CS_CUDA(cudaDeviceSynchronize());
+    CS_CUDA(launch_risk_batch(net->dev.nE, (const uint8_t*)net->sev_n1[level]->p,
+                              (const uint8_t*)net->sev_pairs[level]->p, lambda, n_samples, mode, R,
+                              (int*)ctx->err_word.p, 2, s));
+    ctx->launches = 1;
     return CS_OK;
 }
 

@@ -166,8 +166,10 @@ size_t dyn_abuf_stride(const DevNet& net);
 bool dyn_split_fits(const DevNet& net, int device);
 cudaError_t launch_risk(int nE, const uint8_t* S1, const uint8_t* S2, const double* lam, int mode,
                         double* R, int64_t* missing, cudaStream_t s);
+cudaError_t launch_risk_batch(int nE, const uint8_t* S1, const uint8_t* S2, const double* lam, long long ns,
+                              int mode, double* R, int* err, int bad_bit, cudaStream_t s);
 cudaError_t launch_enumerate(int nE, int64_t first, int64_t count, int* ei, int* ej,
                              cudaStream_t s);
 
 // error bits of the device error word
-enum { ERR_BAD_ELEMENT = 1, ERR_SCRATCH = 2 };
+enum { ERR_BAD_ELEMENT = 1, ERR_SCRATCH = 2, ERR_BAD_RATE = 4 };

@@ -145,7 +145,71 @@ __global__ void risk_kernel(int E, const uint8_t* S1, const uint8_t* S2, const d
     }
 }
 
+// Monte-Carlo form: R for n_samples rate vectors (sample-major lam[s * E + i]) against
+// the same severity tables.  One CTA per element i keeps its partner severities in
+// shared memory (not-evaluated pairs count 0); its warps take the samples.  Each
+// sample's R_i is the same exact fixed-point sum, rounded once, as risk_kernel's.  A
+// rate outside [2^-30, 2^10] gives NaN for that entry and sets bit `bad_bit` of *err.
+__global__ void risk_batch_kernel(int E, const uint8_t* __restrict__ S1, const uint8_t* __restrict__ S2,
+                                  const double* __restrict__ lam, long long ns, int mode, double* __restrict__ R,
+                                  int* err, int bad_bit) {
+    extern __shared__ uint8_t srow[];                 // [E] severities of the pairs (i, j)
+    const int i = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = threadIdx.x; j < E; j += blockDim.x) {
+        uint8_t v = 0;
+        if (j != i) {
+            const long long k = (i < j) ? pair_index(i, j, E) : pair_index(j, i, E);
+            v = (S2[k] == 1) ? 1 : 0;
+        }
+        srow[j] = v;
+    }
+    __syncthreads();
+    const uint8_t s1 = (S1[i] == 1) ? 1 : 0;
+    const double lo = 0x1p-30, hi = 0x1p10;
+    for (long long sm = warp; sm < ns; sm += nw) {
+        const double* ls = lam + sm * E;
+        const double li = ls[i];
+        U192 acc{0ull, 0ull, 0ull};
+        bool bad = !(li >= lo && li <= hi);
+        for (int j = lane; j < E; j += 32) {
+            const double lj = ls[j];
+            if (!(lj >= lo && lj <= hi)) bad = true;
+            if (srow[j]) add192(acc, to_fixed(li * lj));
+        }
+        for (int off = 16; off; off >>= 1) {
+            U192 o;
+            o.w0 = __shfl_xor_sync(0xffffffffu, acc.w0, off);
+            o.w1 = __shfl_xor_sync(0xffffffffu, acc.w1, off);
+            o.w2 = __shfl_xor_sync(0xffffffffu, acc.w2, off);
+            add192(acc, o);
+        }
+        bad = __any_sync(0xffffffffu, bad);
+        if (lane == 0) {
+            if (bad) {
+                R[sm * E + i] = __longlong_as_double(0x7ff8000000000000ll);
+                atomicOr(err, 1 << bad_bit);
+                continue;
+            }
+            if (mode == CS_RISK_ORDERED) {   // exact doubling of the pair sum
+                acc.w2 = (acc.w2 << 1) | (acc.w1 >> 63);
+                acc.w1 = (acc.w1 << 1) | (acc.w0 >> 63);
+                acc.w0 = acc.w0 << 1;
+            }
+            if (s1) add192(acc, to_fixed(li));
+            R[sm * E + i] = round_fixed(acc);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_risk_batch(int nE, const uint8_t* S1, const uint8_t* S2, const double* lam, long long ns,
+                              int mode, double* R, int* err, int bad_bit, cudaStream_t s) {
+    if (nE <= 0 || ns <= 0) return cudaSuccess;
+    risk_batch_kernel<<<nE, 256, (size_t)nE, s>>>(nE, S1, S2, lam, ns, mode, R, err, bad_bit);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_risk(int nE, const uint8_t* S1, const uint8_t* S2, const double* lam, int mode,
                         double* R, int64_t* missing, cudaStream_t s) {

@@ -380,3 +380,42 @@ def test_mixed_form_inline_path_on_a_300_bus_network():
     assert ok.any()
     assert np.max(np.abs(a["max_re"][ok] - b["max_re"][ok])) <= TOL_EIG_MIXED
     assert np.max(np.abs(a["min_zeta"][ok] - b["min_zeta"][ok])) <= TOL_EIG_MIXED
+
+
+def test_risk_index_batch_equals_single_and_oracle():
+    """Monte-Carlo Risk Index over sampled failure rates: every sample equals the
+    single-vector reduction and the exact oracle, bit for bit."""
+    net = synth.make_network(14, 20, 5, 11, 1, seed=3, levels=(0.5,))
+    c = cs.Context(precision=cs.PREC_MIXED)
+    nid = c.load_network(net)
+    E = net.n_elem
+    ii, jj = synth.all_pairs(E)
+    got = _run(c, nid, 0, np.concatenate([np.arange(E), ii]), np.concatenate([-np.ones(E, np.int32), jj]))
+    S1 = got["severe"][:E]
+    S2 = np.zeros((E, E), np.uint8)
+    S2[ii, jj] = got["severe"][E:]
+    S2 = S2 + S2.T
+    rng = np.random.default_rng(21)
+    lam = rng.uniform(0.01, 1.0, (32, E))
+    for mode in (cs.RISK_EQ3, cs.RISK_ORDERED):
+        L = torch.as_tensor(lam, device=DEV)
+        R = torch.empty_like(L)
+        c.risk_index_batch(nid, 0, L, R, mode)
+        c.sync()
+        Rh = R.cpu().numpy()
+        for s in range(lam.shape[0]):
+            single, missing = c.risk_index(nid, 0, lam[s], mode)
+            assert missing == 0
+            np.testing.assert_array_equal(Rh[s], single)
+        for s in (0, 17):
+            np.testing.assert_array_equal(Rh[s], risk.risk_index(lam[s], S1, S2, risk.ORDERED if mode else risk.EQ3))
+    bad = lam[:4].copy()
+    bad[1, 3] = 0.0                                   # outside [2^-30, 2^10]
+    L = torch.as_tensor(bad, device=DEV)
+    R = torch.empty_like(L)
+    c.risk_index_batch(nid, 0, L, R, cs.RISK_EQ3)
+    with pytest.raises(cs.CSError):
+        c.sync()
+    Rh = R.cpu().numpy()
+    assert np.isnan(Rh[1]).all() and np.isfinite(Rh[[0, 2, 3]]).all()
+    c.close()
