@@ -26,10 +26,11 @@ class Scenario:
     gen: np.ndarray           # indices of in-service generators
 
 
-def make_scenario(net, level: int, i: int = -1, j: int = -1) -> Scenario:
-    """Scenario with elements i and j out (-1 = none).  Element ids: [0, n_branch)
-    are branches, [n_branch, n_branch + n_gen) generators (Section II-A)."""
-    out = tuple(sorted({e for e in (i, j) if e >= 0}))
+def make_scenario(net, level: int, i: int = -1, j: int = -1, k: int = -1) -> Scenario:
+    """Scenario with elements i, j and k out (-1 = none; k gives the N-3 extension of
+    the enumeration, a repeated id counts once).  Element ids: [0, n_branch) are
+    branches, [n_branch, n_branch + n_gen) generators (Section II-A)."""
+    out = tuple(sorted({e for e in (i, j, k) if e >= 0}))
     for e in out:
         if e >= net.n_elem:
             raise ValueError("element id out of range")

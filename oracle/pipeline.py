@@ -27,9 +27,9 @@ DAMPING_MIN = 0.05
 
 
 def evaluate(net, level: int, i: int = -1, j: int = -1, damping_min: float = DAMPING_MIN,
-             keep_state: bool = False):
-    """Evaluate scenario (level, i, j).  Returns a dict of plain values."""
-    sc = grid.make_scenario(net, level, i, j)
+             keep_state: bool = False, k: int = -1):
+    """Evaluate scenario (level, i, j[, k]).  Returns a dict of plain values."""
+    sc = grid.make_scenario(net, level, i, j, k)
     nisl = grid.count_islands(net.n_bus, net.f[sc.br], net.t[sc.br])
     out = dict(level=level, i=i, j=j, n_islands=nisl, opf_iters=0, converged=False,
                cost=np.nan, max_re=np.nan, min_zeta=np.nan, eig_sweeps=0)

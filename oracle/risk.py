@@ -54,6 +54,29 @@ def risk_index(lam, S1, S2, mode: int = ORDERED):
     return out
 
 
+def risk_index_pair_freq(lam, F, S1, S2, mode: int = ORDERED):
+    """R with explicit pair frequencies: R_i = lambda_i S_i + m sum_{j != i} F_ij S_ij.
+
+    The extension to common-cause pair frequencies named in the paper's outlook
+    (Section VI): F_ij (per year, row i used for element i) replaces the
+    independent-failure product of Eq. 2.  Exact over the given doubles, rounded
+    once; with F_ij = fl(lambda_i lambda_j) it is ``risk_index``."""
+    lam = [float(v) for v in lam]
+    E = len(lam)
+    F = np.asarray(F, dtype=np.float64)
+    S2 = np.asarray(S2)
+    mult = 2 if mode == ORDERED else 1
+    out = np.zeros(E)
+    for i in range(E):
+        acc = Fraction(lam[i]) if int(S1[i]) else Fraction(0)
+        pair = Fraction(0)
+        for j in range(E):
+            if j != i and int(S2[i, j]):
+                pair += Fraction(float(F[i, j]))
+        out[i] = float(acc + mult * pair)
+    return out
+
+
 def risk_index_ordered_list(lam, S1, ordered_pairs):
     """Brute-force form: Eq. 3 summed over an explicit list of ordered N-2
     scenarios (i, j, S_ij) in which i is the first outage; the pair frequency

@@ -40,3 +40,24 @@ def test_pair_order_irrelevant(net):
     a = pipeline.evaluate(net, 0, 3, net.n_branch + 2)
     b = pipeline.evaluate(net, 0, net.n_branch + 2, 3)
     assert a["klass"] == b["klass"] and a["cost"] == b["cost"]
+
+
+def test_n3_scenarios_reduce_to_n2_and_are_order_free():
+    """N-3 extension of the enumeration: a triple with a repeated or absent third
+    element is the pinned N-2 scenario, and the result does not depend on the order
+    of the three elements."""
+    from oracle import grid, pipeline
+    from paper_2512_08465_gb300 import synth
+    net = synth.make_network(9, 12, 3, 6, 0, seed=5, levels=(0.5,))
+    a = pipeline.evaluate(net, 0, 1, 7)
+    for k in (-1, 1, 7):
+        b = pipeline.evaluate(net, 0, 1, 7, k=k)
+        assert b["klass"] == a["klass"] and b["n_islands"] == a["n_islands"] and b["opf_iters"] == a["opf_iters"]
+    sc = grid.make_scenario(net, 0, 2, 9, 13)
+    assert sc.out_elems == (2, 9, 13) and 13 - net.n_branch not in sc.gen and 2 not in sc.br
+    r0 = pipeline.evaluate(net, 0, 2, 9, k=13)
+    for (i, j, k) in ((13, 2, 9), (9, 13, 2)):
+        r = pipeline.evaluate(net, 0, i, j, k=k)
+        assert r["klass"] == r0["klass"] and r["opf_iters"] == r0["opf_iters"]
+        if r0["converged"]:
+            assert r["cost"] == r0["cost"]

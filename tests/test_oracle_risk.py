@@ -55,3 +55,33 @@ def test_exact_against_fsum_and_brute_force_lists():
 def test_zero_severity_gives_zero():
     lam = np.full(5, 0.3)
     np.testing.assert_array_equal(risk.risk_index(lam, np.zeros(5), np.zeros((5, 5))), 0.0)
+
+
+def test_pair_frequency_form_reduces_to_eq3_and_matches_brute_force():
+    """Explicit pair frequencies (common-cause extension): with F_ij = fl(l_i l_j)
+    it is Eq. 3 exactly; for a general F it is the exact rational sum, rounded once."""
+    from fractions import Fraction
+    import numpy as np
+    from oracle import risk
+    rng = np.random.default_rng(9)
+    E = 11
+    lam = rng.uniform(0.01, 1.0, E)
+    S1 = rng.integers(0, 2, E)
+    S2 = np.triu(rng.integers(0, 2, (E, E)), 1)
+    S2 = S2 + S2.T
+    Fprod = np.outer(lam, lam)                        # fl(l_i l_j) elementwise
+    for mode in (risk.EQ3, risk.ORDERED):
+        np.testing.assert_array_equal(risk.risk_index_pair_freq(lam, Fprod, S1, S2, mode),
+                                      risk.risk_index(lam, S1, S2, mode))
+    F = rng.uniform(1e-4, 0.3, (E, E))                # e.g. a common-cause model, not a product
+    F = 0.5 * (F + F.T)
+    got = risk.risk_index_pair_freq(lam, F, S1, S2, risk.EQ3)
+    for i in range(E):
+        want = (Fraction(lam[i]) if S1[i] else Fraction(0)) + sum(
+            (Fraction(F[i, j]) for j in range(E) if j != i and S2[i, j]), Fraction(0))
+        assert got[i] == float(want)
+    got2 = risk.risk_index_pair_freq(lam, F, S1, S2, risk.ORDERED)
+    for i in range(E):                                # ordered = Eq. 3 pair term counted twice, exactly
+        want = (Fraction(lam[i]) if S1[i] else Fraction(0)) + 2 * sum(
+            (Fraction(F[i, j]) for j in range(E) if j != i and S2[i, j]), Fraction(0))
+        assert got2[i] == float(want)
