@@ -222,6 +222,31 @@ cs_status cs_risk_reduce_device(int32_t n_elem, const uint8_t* S1, const uint8_t
 cs_status cs_enumerate_pairs_device(int32_t n_elem, int64_t first, int64_t count,
                                     int32_t* elem_i, int32_t* elem_j, void* stream);
 
+/* N-3 extension of the enumeration (the paper's outlook, Section VI): as
+ * cs_evaluate_device with a third DEVICE id array elem_k ([n] int32; -1 = none,
+ * repeated ids count once).  Each id is -1 (none) or in [0, n_branch + n_gen),
+ * and a -1 may only be followed by -1s (an invalid record is marked as in
+ * cs_evaluate_device).  Records of scenarios with
+ * three distinct elements are not written to the N-2 severity tables; N-1 and
+ * N-2 records are, as in cs_evaluate_device. */
+cs_status cs_evaluate_device_n3(cs_ctx* ctx, int32_t net_id, int32_t level,
+                                const int32_t* elem_i, const int32_t* elem_j, const int32_t* elem_k,
+                                int64_t n, const cs_result* out, void* stream);
+
+/* Unordered triples i < j < k of n_elem >= 3 elements in lexicographic order:
+ * writes `count` triples starting at rank `first` into DEVICE arrays (int32).
+ * CS_E_ARG if the range exceeds C(n_elem, 3). */
+cs_status cs_enumerate_triples_device(int32_t n_elem, int64_t first, int64_t count,
+                                      int32_t* elem_i, int32_t* elem_j, int32_t* elem_k, void* stream);
+
+/* Risk Index with explicit pair frequencies (common-cause extension of Eq. 2,
+ * the paper's outlook): R_i = lambda_i S_i + m * sum_j F_ij S_ij, F a HOST
+ * array [E * E], row i used for element i, every entry 0 or in [2^-60, 2^20]
+ * (else CS_E_ARG); exact and rounded once like cs_risk_index, which it equals
+ * bit for bit when F_ij = fl(lambda_i lambda_j).  lambda, R_out: HOST [E]. */
+cs_status cs_risk_index_pair_freq(cs_ctx* ctx, int32_t net_id, int32_t level, const double* lambda,
+                                  const double* F, int32_t mode, double* R_out, int64_t* n_missing);
+
 /* Monte-Carlo form of the Risk Index over uncertain failure rates (the
  * paper's outlook, Section VI): R for n_samples rate vectors against the
  * context's severity tables of (net_id, level), each sample exactly as

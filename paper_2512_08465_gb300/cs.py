@@ -31,7 +31,8 @@ EXPORTS = ("cs_default_options", "cs_create", "cs_destroy", "cs_load_network", "
            "cs_base_result", "cs_evaluate_device", "cs_sync", "cs_submit_contingencies", "cs_poll",
            "cs_risk_index", "cs_risk_reduce_device", "cs_enumerate_pairs_device", "cs_last_error",
            "cs_last_launch_count", "cs_set_timing", "cs_kernel_times", "cs_alu_peak", "cs_eigen_reruns",
-           "cs_risk_index_static", "cs_network_stats", "cs_serving_stats", "cs_risk_index_batch")
+           "cs_risk_index_static", "cs_network_stats", "cs_serving_stats", "cs_risk_index_batch",
+           "cs_evaluate_device_n3", "cs_enumerate_triples_device", "cs_risk_index_pair_freq")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -101,6 +102,9 @@ def load_library(build_if_missing: bool = True):
         "cs_network_stats": (i32, [P, i32, P, i32]),
         "cs_serving_stats": (i32, [P, P, i32]),
         "cs_risk_index_batch": (i32, [P, i32, i32, P, i64, i32, P, P]),
+        "cs_evaluate_device_n3": (i32, [P, i32, i32, P, P, P, i64, ctypes.POINTER(Result), P]),
+        "cs_enumerate_triples_device": (i32, [i32, i64, i64, P, P, P, P]),
+        "cs_risk_index_pair_freq": (i32, [P, i32, i32, P, P, i32, P, ctypes.POINTER(i64)]),
         "cs_risk_reduce_device": (i32, [i32, P, P, P, i32, P, P]),
         "cs_enumerate_pairs_device": (i32, [i32, i64, i64, P, P, P]),
         "cs_last_error": (ctypes.c_char_p, [P]),
@@ -240,6 +244,14 @@ class Context:
                                          _stream_handle(stream))
         self._check(st, "cs_evaluate_device")
 
+    def evaluate_device_n3(self, net_id: int, level: int, ei, ej, ek, out: dict, stream=None):
+        """N-3 extension: like evaluate_device with a third element per scenario (-1 = none)."""
+        n = int(ei.numel())
+        R = self._result_struct(out)
+        st = self.lib.cs_evaluate_device_n3(self.h, net_id, level, _ptr(ei), _ptr(ej), _ptr(ek), n,
+                                            ctypes.byref(R), _stream_handle(stream))
+        self._check(st, "cs_evaluate_device_n3")
+
     def sync(self, stream=None):
         self._check(self.lib.cs_sync(self.h, _stream_handle(stream)), "cs_sync")
 
@@ -317,6 +329,17 @@ class Context:
         self._check(st, "cs_risk_index")
         return R, miss.value
 
+    def risk_index_pair_freq(self, net_id: int, level: int, lam, F, mode: int = RISK_ORDERED):
+        """cs_risk_index_pair_freq: Eq. 3 with explicit pair frequencies F (E x E, host)."""
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        R = np.empty_like(lam)
+        miss = ctypes.c_int64()
+        st = self.lib.cs_risk_index_pair_freq(self.h, net_id, level, _ptr(lam), _ptr(F), mode, _ptr(R),
+                                              ctypes.byref(miss))
+        self._check(st, "cs_risk_index_pair_freq")
+        return R, miss.value
+
     def risk_index_batch(self, net_id: int, level: int, lam, R, mode: int = RISK_ORDERED, stream=None):
         """cs_risk_index_batch: R[s, i] for device rate samples lam[s, i] (float64, sample-major)."""
         st = self.lib.cs_risk_index_batch(self.h, net_id, level, _ptr(lam), lam.shape[0], mode, _ptr(R),
@@ -348,6 +371,13 @@ def alu_peak(device: int = 0):
     if st != CS_OK:
         raise CSError(st, "cs_alu_peak")
     return a.value, b.value
+
+
+def enumerate_triples_device(n_elem: int, first: int, count: int, ei, ej, ek, stream=None):
+    st = load_library().cs_enumerate_triples_device(n_elem, first, count, _ptr(ei), _ptr(ej), _ptr(ek),
+                                                    _stream_handle(stream))
+    if st != CS_OK:
+        raise CSError(st, "cs_enumerate_triples_device")
 
 
 def enumerate_pairs_device(n_elem: int, first: int, count: int, ei, ej, stream=None):

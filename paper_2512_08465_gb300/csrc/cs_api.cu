@@ -97,7 +97,7 @@ struct Packer {
 
 cs_status csi::evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level, const int32_t* ei,
                              const int32_t* ej, int64_t n, const cs_result* out, cudaStream_t s, bool record,
-                             int64_t chunk) {
+                             int64_t chunk, const int32_t* ek) {
     if (n <= 0) return CS_OK;
     const DevNet& dn = net->dev;
     const int nx = 2 * dn.nb + 2 * dn.ng;
@@ -130,6 +130,7 @@ cs_status csi::evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level
         EvalArgs a{};
         a.ei = ei + c0;
         a.ej = ej + c0;
+        a.ek = ek ? ek + c0 : nullptr;
         a.n = (int)m;
         a.level = level;
         a.out = *out;
@@ -626,6 +627,73 @@ cs_status cs_risk_index(cs_ctx* ctx, int32_t net_id, int32_t level, const double
     CS_CUDA(cudaMemsetAsync(dm.p, 0, sizeof(int64_t), s));
     CS_CUDA(launch_risk(nE, (const uint8_t*)net->sev_n1[level]->p, (const uint8_t*)net->sev_pairs[level]->p,
                         (const double*)dl.p, mode, (double*)dr.p, (int64_t*)dm.p, s));
+    CS_CUDA(cudaMemcpyAsync(R_out, dr.p, sizeof(double) * nE, cudaMemcpyDeviceToHost, s));
+    int64_t miss = 0;
+    CS_CUDA(cudaMemcpyAsync(&miss, dm.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CS_CUDA(cudaStreamSynchronize(s));
+    if (n_missing) *n_missing = miss;
+    return CS_OK;
+}
+
+cs_status cs_evaluate_device_n3(cs_ctx* ctx, int32_t net_id, int32_t level, const int32_t* ei, const int32_t* ej,
+                                const int32_t* ek, int64_t n, const cs_result* out, void* stream) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    auto it = ctx->nets.find(net_id);
+    if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
+    Network* net = it->second.get();
+    if (level < 0 || level >= net->nlev) return fail(ctx, CS_E_ARG, "level out of range");
+    if (n < 0 || n > (int64_t)1 << 31) return fail(ctx, CS_E_ARG, "n out of range");
+    if (n == 0) return CS_OK;
+    if (!ei || !ej || !ek || !out || !out->klass || !out->severe || !out->n_islands || !out->opf_iters ||
+        !out->cost || !out->max_re || !out->min_zeta)
+        return fail(ctx, CS_E_ARG, "NULL buffer");
+    CS_CUDA(cudaSetDevice(ctx->device));
+    ctx->launches = 0;
+    return evaluate_impl(ctx, ctx->direct, net, level, ei, ej, n, out, (cudaStream_t)stream, true,
+                         default_chunk(ctx), ek);
+}
+
+cs_status cs_enumerate_triples_device(int32_t n_elem, int64_t first, int64_t count, int32_t* ei, int32_t* ej,
+                                      int32_t* ek, void* stream) {
+    const int64_t E = n_elem;
+    const int64_t total = E < 3 ? 0 : E * (E - 1) * (E - 2) / 6;
+    if (n_elem < 3 || n_elem > 32767 || first < 0 || count < 0 || first + count > total ||
+        (count > 0 && (!ei || !ej || !ek)))
+        return CS_E_ARG;
+    cudaError_t e = launch_enumerate3(n_elem, first, count, ei, ej, ek, (cudaStream_t)stream);
+    return e == cudaSuccess ? CS_OK : CS_E_CUDA;
+}
+
+cs_status cs_risk_index_pair_freq(cs_ctx* ctx, int32_t net_id, int32_t level, const double* lambda, const double* F,
+                                  int32_t mode, double* R_out, int64_t* n_missing) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    auto it = ctx->nets.find(net_id);
+    if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
+    Network* net = it->second.get();
+    if (level < 0 || level >= net->nlev || !lambda || !F || !R_out || (mode != CS_RISK_EQ3 && mode != CS_RISK_ORDERED))
+        return fail(ctx, CS_E_ARG, "bad level, mode or NULL");
+    const int nE = net->dev.nE;
+    for (int i = 0; i < nE; ++i)
+        if (!(lambda[i] >= std::ldexp(1.0, -30) && lambda[i] <= std::ldexp(1.0, 10)))
+            return fail(ctx, CS_E_ARG, "lambda outside [2^-30, 2^10]");
+    for (int64_t q = 0; q < (int64_t)nE * nE; ++q)
+        if (!(F[q] == 0.0 || (F[q] >= std::ldexp(1.0, -60) && F[q] <= std::ldexp(1.0, 20))))
+            return fail(ctx, CS_E_ARG, "pair frequency outside {0} U [2^-60, 2^20]");
+    CS_CUDA(cudaSetDevice(ctx->device));
+    DevBuf dl, dF, dr, dm;
+    CS_CUDA(dl.ensure(sizeof(double) * nE));
+    CS_CUDA(dF.ensure(sizeof(double) * (size_t)nE * nE));
+    CS_CUDA(dr.ensure(sizeof(double) * nE));
+    CS_CUDA(dm.ensure(sizeof(int64_t)));
+    cudaStream_t s = ctx->req_stream;
+    CS_CUDA(cudaDeviceSynchronize());      // tables written by earlier evaluations on any stream
+    CS_CUDA(cudaMemcpyAsync(dl.p, lambda, sizeof(double) * nE, cudaMemcpyHostToDevice, s));
+    CS_CUDA(cudaMemcpyAsync(dF.p, F, sizeof(double) * (size_t)nE * nE, cudaMemcpyHostToDevice, s));
+    CS_CUDA(cudaMemsetAsync(dm.p, 0, sizeof(int64_t), s));
+    CS_CUDA(launch_risk(nE, (const uint8_t*)net->sev_n1[level]->p, (const uint8_t*)net->sev_pairs[level]->p,
+                        (const double*)dl.p, mode, (double*)dr.p, (int64_t*)dm.p, s, (const double*)dF.p));
     CS_CUDA(cudaMemcpyAsync(R_out, dr.p, sizeof(double) * nE, cudaMemcpyDeviceToHost, s));
     int64_t miss = 0;
     CS_CUDA(cudaMemcpyAsync(&miss, dm.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));

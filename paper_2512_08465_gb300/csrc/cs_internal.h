@@ -101,27 +101,35 @@ struct DevNet {
 
 // scenario masks: up to two outaged elements
 struct Outage {
-    int br0, br1;   // outaged branches (-1 none)
-    int g0, g1;     // outaged generators (-1 none)
+    int br0, br1, br2;   // outaged branches (-1 none)
+    int g0, g1, g2;      // outaged generators (-1 none)
 };
 
-CS_HD Outage decode_outage(int nbr, int ng, int ei, int ej) {
-    Outage o{-1, -1, -1, -1};
-    int e[2] = {ei, ej};
-    for (int q = 0; q < 2; ++q) {
+// Outage set of a scenario from up to three element ids (-1 = none; a repeated id
+// counts once; the third id is the N-3 extension).
+CS_HD Outage decode_outage(int nbr, int ng, int ei, int ej, int ek = -1) {
+    Outage o{-1, -1, -1, -1, -1, -1};
+    int e[3] = {ei, ej, ek};
+    for (int q = 0; q < 3; ++q) {
         int v = e[q];
         if (v < 0) continue;
         if (v < nbr) {
-            if (o.br0 < 0) o.br0 = v; else if (v != o.br0) o.br1 = v;
+            if (o.br0 < 0) o.br0 = v;
+            else if (v != o.br0 && o.br1 < 0) o.br1 = v;
+            else if (v != o.br0 && v != o.br1) o.br2 = v;
         } else if (v < nbr + ng) {
             int g = v - nbr;
-            if (o.g0 < 0) o.g0 = g; else if (g != o.g0) o.g1 = g;
+            if (o.g0 < 0) o.g0 = g;
+            else if (g != o.g0 && o.g1 < 0) o.g1 = g;
+            else if (g != o.g0 && g != o.g1) o.g2 = g;
         }
     }
     return o;
 }
-CS_HD bool br_out(const Outage& o, int b) { return b == o.br0 || b == o.br1; }
-CS_HD bool gen_out(const Outage& o, int g) { return g == o.g0 || g == o.g1; }
+CS_HD bool br_out(const Outage& o, int b) { return b == o.br0 || b == o.br1 || b == o.br2; }
+CS_HD bool gen_out(const Outage& o, int g) { return g == o.g0 || g == o.g1 || g == o.g2; }
+CS_HD int n_br_out(const Outage& o) { return (o.br0 >= 0) + (o.br1 >= 0) + (o.br2 >= 0); }
+CS_HD int n_gen_out(const Outage& o) { return (o.g0 >= 0) + (o.g1 >= 0) + (o.g2 >= 0); }
 
 // ------------------------------------------------------------ kernel API ----
 // Per-scenario intermediate state written by the OPF kernel, read by the
@@ -142,6 +150,7 @@ struct EvalArgs {
     uint8_t* sev_pairs;     // [nE*(nE-1)/2]
     int* err;               // device error word
     int* reruns;            // device counter: FP64 eigen re-runs of the mixed-precision screen
+    const int* ek;          // [n] third outage element (N-3), or nullptr
 };
 
 // launch wrappers (return cudaError_t)
@@ -165,11 +174,13 @@ size_t dyn_hbuf_stride(const DevNet& net);
 size_t dyn_abuf_stride(const DevNet& net);
 bool dyn_split_fits(const DevNet& net, int device);
 cudaError_t launch_risk(int nE, const uint8_t* S1, const uint8_t* S2, const double* lam, int mode,
-                        double* R, int64_t* missing, cudaStream_t s);
+                        double* R, int64_t* missing, cudaStream_t s, const double* F = nullptr);
 cudaError_t launch_risk_batch(int nE, const uint8_t* S1, const uint8_t* S2, const double* lam, long long ns,
                               int mode, double* R, int* err, int bad_bit, cudaStream_t s);
 cudaError_t launch_enumerate(int nE, int64_t first, int64_t count, int* ei, int* ej,
                              cudaStream_t s);
+cudaError_t launch_enumerate3(int nE, int64_t first, int64_t count, int* ei, int* ej, int* ek,
+                              cudaStream_t s);
 
 // error bits of the device error word
 enum { ERR_BAD_ELEMENT = 1, ERR_SCRATCH = 2, ERR_BAD_RATE = 4 };

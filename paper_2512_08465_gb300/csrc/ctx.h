@@ -176,7 +176,7 @@ size_t reserved_bytes(const cs_ctx* ctx);
 // Requires ctx->mu held.
 cs_status evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level, const int32_t* ei,
                         const int32_t* ej, int64_t n, const cs_result* out, cudaStream_t s, bool record,
-                        int64_t chunk);
+                        int64_t chunk, const int32_t* ek = nullptr);
 
 // Result records of n scenarios as one SoA block (doubles first): byte size and
 // the pointers into a block at base.

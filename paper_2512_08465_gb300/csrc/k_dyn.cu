@@ -472,7 +472,7 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
             __syncthreads();
             continue;
         }
-        const Outage out = decode_outage(nbr, ng, a.ei[s], a.ej[s]);
+        const Outage out = decode_outage(nbr, ng, a.ei[s], a.ej[s], a.ek ? a.ek[s] : -1);
         const double* xs = o.x + (size_t)s * nx;
         if (tid == 0) {
             int m = 0;
@@ -741,6 +741,7 @@ __global__ void record_kernel(int nbr, int nE, EvalArgs a) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.n; s += gridDim.x * blockDim.x) {
         const int ei = a.ei[s], ej = a.ej[s];
         if (ei < 0 || ei >= nE || ej >= nE || ej < -1) continue;
+        if (a.ek && a.ek[s] >= 0 && a.ek[s] != ei && a.ek[s] != ej) continue;   // N-3: not in the N-2 tables
         const uint8_t S = a.out.severe[s] ? 1 : 0;
         if (ej < 0 || ej == ei) {
             a.sev_n1[ei] = S;

@@ -25,8 +25,9 @@ __global__ void islands_kernel(DevNet net, EvalArgs a, int* islanded) {
     int* parent = sh_parent + warp * net.nb;
     const int nwarps_total = gridDim.x * kWarpsPerBlock;
     for (int s = blockIdx.x * kWarpsPerBlock + warp; s < a.n; s += nwarps_total) {
-        const int ei = a.ei[s], ej = a.ej[s];
-        const bool bad = ei < -1 || ej < -1 || ei >= net.nE || ej >= net.nE || (ei < 0 && ej >= 0);
+        const int ei = a.ei[s], ej = a.ej[s], ek = a.ek ? a.ek[s] : -1;
+        const bool bad = ei < -1 || ej < -1 || ek < -1 || ei >= net.nE || ej >= net.nE || ek >= net.nE ||
+                         (ei < 0 && ej >= 0) || (ej < 0 && ek >= 0);
         if (bad) {
             if (lane == 0) {
                 atomicOr(a.err, ERR_BAD_ELEMENT);
@@ -41,7 +42,7 @@ __global__ void islands_kernel(DevNet net, EvalArgs a, int* islanded) {
             }
             continue;
         }
-        const Outage o = decode_outage(net.nbr, net.ng, ei, ej);
+        const Outage o = decode_outage(net.nbr, net.ng, ei, ej, ek);
         for (int u = lane; u < net.nb; u += 32) parent[u] = u;
         __syncwarp();
         if (lane == 0) {
@@ -102,6 +103,42 @@ cudaError_t launch_islands(const DevNet& net, const EvalArgs& a, int* islanded, 
     int blocks = (a.n + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks > 4096) blocks = 4096;
     islands_kernel<<<blocks, 32 * kWarpsPerBlock, smem, s>>>(net, a, islanded);
+    return cudaGetLastError();
+}
+
+// Triples i < j < k in lexicographic order (the N-3 extension): the triples before
+// those starting with i number C(E,3) - C(E-i,3); within i, (j, k) is the pair of
+// rank r among the E-1-i elements after i.
+__device__ __forceinline__ long long choose3(long long x) { return x < 3 ? 0 : x * (x - 1) * (x - 2) / 6; }
+
+__global__ void enumerate3_kernel(int E, long long first, long long count, int* ei, int* ej, int* ek) {
+    const long long total = choose3(E);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long t = first + q;
+        long long lo = 0, hi = E - 3;           // largest i with total - C(E-i,3) <= t
+        while (lo < hi) {
+            long long mid = (lo + hi + 1) >> 1;
+            if (total - choose3(E - mid) <= t) lo = mid; else hi = mid - 1;
+        }
+        const long long r = t - (total - choose3(E - lo));
+        const long long m = E - 1 - lo;         // elements after i
+        long long a = 0, b = m - 2;             // largest p with pair_start(p, m) <= r
+        while (a < b) {
+            long long mid = (a + b + 1) >> 1;
+            if (pair_start(mid, m) <= r) a = mid; else b = mid - 1;
+        }
+        ei[q] = (int)lo;
+        ej[q] = (int)(lo + 1 + a);
+        ek[q] = (int)(lo + 1 + (r - pair_start(a, m) + a + 1));
+    }
+}
+
+cudaError_t launch_enumerate3(int nE, int64_t first, int64_t count, int* ei, int* ej, int* ek, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    long long blocks = (count + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    enumerate3_kernel<<<(int)blocks, 256, 0, s>>>(nE, (long long)first, (long long)count, ei, ej, ek);
     return cudaGetLastError();
 }
 

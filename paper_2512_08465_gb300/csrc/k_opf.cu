@@ -771,9 +771,9 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
             __syncthreads();
             continue;
         }
-        const Outage out = decode_outage(nbr, ng, a.ei[s], a.ej[s]);
-        const int nbr_act = nbr - (out.br0 >= 0) - (out.br1 >= 0);
-        const int ng_act = ng - (out.g0 >= 0) - (out.g1 >= 0);
+        const Outage out = decode_outage(nbr, ng, a.ei[s], a.ej[s], a.ek ? a.ek[s] : -1);
+        const int nbr_act = nbr - n_br_out(out);
+        const int ng_act = ng - n_gen_out(out);
         const double niq = 2.0 * nbr_act + 2.0 * nb + 4.0 * ng_act;
 
         // ---------------- initial point ----------------

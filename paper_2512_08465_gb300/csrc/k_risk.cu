@@ -10,7 +10,9 @@
 // [2^-60, 2^20], whose least significant bit is at least 2^-112, and the sum of
 // up to 2^20 elements times 2 stays below 2^64.
 //
-// One warp per element i; lanes stride over partners j.
+// One warp per element i; lanes stride over partners j.  With F (E x E, row i for
+// element i) the pair terms are explicit pair frequencies F_ij instead of the
+// products fl(lambda_i lambda_j) (common-cause extension).
 #include "cs_internal.h"
 
 namespace {
@@ -106,8 +108,8 @@ __device__ __forceinline__ long long pair_index(long long i, long long j, long l
     return i * E - (i * (i + 1)) / 2 + (j - i - 1);
 }
 
-__global__ void risk_kernel(int E, const uint8_t* S1, const uint8_t* S2, const double* lam, int mode,
-                            double* R, unsigned long long* missing) {
+__global__ void risk_kernel(int E, const uint8_t* S1, const uint8_t* S2, const double* lam, const double* F,
+                            int mode, double* R, unsigned long long* missing) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -120,7 +122,7 @@ __global__ void risk_kernel(int E, const uint8_t* S1, const uint8_t* S2, const d
             const long long k = (i < j) ? pair_index(i, j, E) : pair_index(j, i, E);
             const uint8_t s = S2[k];
             if (s == 255) { if (i < j) ++miss; continue; }   // each missing pair once
-            if (s) add192(acc, to_fixed(li * lam[j]));
+            if (s) add192(acc, to_fixed(F ? F[(long long)i * E + j] : li * lam[j]));   // F: explicit pair frequencies
         }
         for (int off = 16; off; off >>= 1) {
             U192 o;
@@ -212,10 +214,10 @@ cudaError_t launch_risk_batch(int nE, const uint8_t* S1, const uint8_t* S2, cons
 }
 
 cudaError_t launch_risk(int nE, const uint8_t* S1, const uint8_t* S2, const double* lam, int mode,
-                        double* R, int64_t* missing, cudaStream_t s) {
+                        double* R, int64_t* missing, cudaStream_t s, const double* F) {
     if (nE <= 0) return cudaSuccess;
     int blocks = (nE * 32 + 255) / 256;
     if (blocks > 1024) blocks = 1024;
-    risk_kernel<<<blocks, 256, 0, s>>>(nE, S1, S2, lam, mode, R, (unsigned long long*)missing);
+    risk_kernel<<<blocks, 256, 0, s>>>(nE, S1, S2, lam, F, mode, R, (unsigned long long*)missing);
     return cudaGetLastError();
 }
