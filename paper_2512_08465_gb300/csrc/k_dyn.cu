@@ -835,11 +835,18 @@ hess_cluster_kernel(EvalArgs a, OpfOut o, const float* __restrict__ abuf, size_t
             const float alpha = (x0 >= 0.0f) ? -nrm : nrm;
             const float v0 = x0 - alpha;
             const float beta = 2.0f / (v0 * v0 + tail);
+            // this CTA's copy of the reflector takes v0 in place of x0 (the peer writes only the
+            // other parity's copy during this column)
+            __syncthreads();
+            if (tid == 0) v[0] = v0;
+            __syncthreads();
             float* w_own = wb + (par * 2 + rank) * nmax;
             float* w_peer = peer_wb + (par * 2 + rank) * nmax;
             for (int j = k + 1 + tid; j < n; j += kHsThreads) {   // partial v^T A over own rows
                 float acc = 0.0f;
-                for (int i = i0; i < r1; ++i) acc += ((i == k + 1) ? v0 : v[i - k - 1]) * As[(i - r0) * n + j];
+                const float* col = As + (i0 - r0) * n + j;
+                const float* vv = v + (i0 - k - 1);
+                for (int i = 0; i < r1 - i0; ++i) acc += vv[i] * col[i * n];
                 w_own[j] = acc;
                 w_peer[j] = acc;
             }
@@ -855,12 +862,12 @@ hess_cluster_kernel(EvalArgs a, OpfOut o, const float* __restrict__ abuf, size_t
             for (int t = 0; t < kHsCols; ++t) {
                 const int jj = lane + 32 * t;             // offset from column k+1
                 wr_[t] = (jj < mm) ? beta * (w0[k + 1 + jj] + w1[k + 1 + jj]) : 0.0f;
-                vr_[t] = (jj < mm) ? (jj == 0 ? v0 : v[jj]) : 0.0f;
+                vr_[t] = (jj < mm) ? v[jj] : 0.0f;
             }
             for (int i = warp; i < nr; i += kHsWarps) {
                 float* row = As + i * n + k + 1;
                 const int gi = r0 + i;
-                const float vi = (gi >= k + 1) ? ((gi == k + 1) ? v0 : v[gi - k - 1]) : 0.0f;
+                const float vi = (gi >= k + 1) ? v[gi - k - 1] : 0.0f;
                 float x[kHsCols];
                 float acc = 0.0f;
 #pragma unroll
