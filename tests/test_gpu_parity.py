@@ -419,3 +419,23 @@ def test_risk_index_batch_equals_single_and_oracle():
     Rh = R.cpu().numpy()
     assert np.isnan(Rh[1]).all() and np.isfinite(Rh[[0, 2, 3]]).all()
     c.close()
+
+
+def test_chunks_alternating_over_two_streams_equal_one_chunk():
+    """Chunks of 1000 over 2500 scenarios (a ragged tail of 500) alternate between the
+    caller's stream and the context's second stream: every record equals the
+    single-chunk evaluation, and the severity tables receive every record."""
+    net = synth.case118()
+    ii, jj = synth.all_pairs(net.n_elem)
+    sel = np.random.default_rng(13).choice(ii.size, 2500, replace=False)
+    res = {}
+    for chunk in (0, 1000):
+        c = cs.Context(precision=cs.PREC_MIXED, chunk=chunk)
+        nid = c.load_network(net)
+        res[chunk] = _run(c, nid, 1, ii[sel], jj[sel])
+        R, missing = c.risk_index(nid, 1, synth.failure_rates(net.n_elem, 2), cs.RISK_ORDERED)
+        res[chunk]["R"], res[chunk]["missing"] = R, missing
+        c.close()
+    for k in ("klass", "severe", "n_islands", "opf_iters", "cost", "max_re", "min_zeta", "R"):
+        np.testing.assert_array_equal(res[0][k], res[1000][k], err_msg=k)
+    assert res[0]["missing"] == res[1000]["missing"] == ii.size - sel.size + net.n_elem
