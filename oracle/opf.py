@@ -259,6 +259,23 @@ def solve(net, sc: grid.Scenario, tol=TOL, max_it=MAX_IT, xi=XI, sigma=SIGMA, tr
                 lam=lam, mu=mu, z=z, h=h, g=g, Lx=Lx, conds=conds, hist=hist, prob=prob)
 
 
+def severity_indices(res):
+    """Non-binary severity of a converged point (an extension the paper names in its
+    outlook, Section VI): the smallest voltage margin min_i min(Vm_i - Vmin_i,
+    Vmax_i - Vm_i) in p.u., and the largest branch loading max |S| / Smax over both
+    ends of the in-service branches."""
+    prob = res["prob"]
+    Vm = res["Vm"]
+    nl = prob.nl
+    h = res["h"]
+    smax = np.sqrt(prob.Smax2)
+    sf = np.sqrt(np.maximum(h[:nl] + prob.Smax2, 0.0))
+    st = np.sqrt(np.maximum(h[nl:2 * nl] + prob.Smax2, 0.0))
+    margin = float(min(np.min(Vm - prob.Vmin), np.min(prob.Vmax - Vm)))
+    loading = float(max(np.max(sf / smax), np.max(st / smax))) if nl else 0.0
+    return margin, loading
+
+
 def limit_violation(res, tol=LIMIT_TOL) -> bool:
     """Section II-B-1 operational limits at a converged point: thermal (|S| above
     Smax) and voltage / generator bounds, each beyond ``tol`` per unit."""

@@ -32,7 +32,7 @@ def evaluate(net, level: int, i: int = -1, j: int = -1, damping_min: float = DAM
     sc = grid.make_scenario(net, level, i, j, k)
     nisl = grid.count_islands(net.n_bus, net.f[sc.br], net.t[sc.br])
     out = dict(level=level, i=i, j=j, n_islands=nisl, opf_iters=0, converged=False,
-               cost=np.nan, max_re=np.nan, min_zeta=np.nan, eig_sweeps=0)
+               cost=np.nan, max_re=np.nan, min_zeta=np.nan, eig_sweeps=0, v_margin=np.nan, max_loading=np.nan)
     if nisl > 1:
         out["klass"] = ISLANDED
         out["severe"] = 1
@@ -44,6 +44,7 @@ def evaluate(net, level: int, i: int = -1, j: int = -1, damping_min: float = DAM
         out["klass"] = OPF_NONCONV
         out["severe"] = 1
         return out
+    out["v_margin"], out["max_loading"] = opf.severity_indices(r)
     if opf.limit_violation(r):
         out["klass"] = LIMIT
         out["severe"] = 1

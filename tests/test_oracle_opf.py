@@ -137,3 +137,24 @@ def test_infeasible_scenario_does_not_converge():
     net = _two_bus(0.01, 0.05, 1500.0, 100.0, [(0, 1000.0, 0.01, 20.0)])
     r = opf.solve(net, grid.make_scenario(net, 0))
     assert not r["converged"]
+
+
+def test_severity_indices_at_binding_limits():
+    """Non-binary severity indices pinned by optimality: a cheap generator behind a
+    line rated below the load must push that line to its limit (loading 1), and a
+    lossy line feeding a load from one generator drives the generator bus to Vmax
+    (losses fall with voltage), so the voltage margin is 0."""
+    from oracle import grid
+    # congestion: cheap generator at bus 0, expensive at bus 1, load 300 MW at bus 1, rating 200 MVA
+    net = _two_bus(0.0, 0.05, 300.0, 0.0, [(0, 500.0, 0.01, 10.0), (1, 500.0, 0.01, 40.0)])
+    net.rate[:] = 200.0
+    r = opf.solve(net, grid.make_scenario(net, 0))
+    assert r["converged"]
+    margin, loading = opf.severity_indices(r)
+    assert abs(loading - 1.0) <= 1e-6 and margin >= -1e-8
+    # losses: one generator, lossy line, load at the far end; Vm0 goes to Vmax
+    net = _two_bus(0.02, 0.06, 150.0, 30.0, [(0, 500.0, 0.01, 20.0)])
+    r = opf.solve(net, grid.make_scenario(net, 0))
+    assert r["converged"]
+    margin, loading = opf.severity_indices(r)
+    assert abs(r["Vm"][0] - net.Vmax[0]) <= 1e-6 and abs(margin) <= 1e-6 and loading < 1.0
