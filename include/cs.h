@@ -108,7 +108,8 @@ typedef struct {
 
 /* Per-scenario results, structure of arrays with n records.  Which memory
  * (device or host) each entry point expects is stated at the entry point.
- * Vm / Va are optional ([n * n_bus], NULL = not written). */
+ * Vm / Va, v_margin / max_loading are optional (NULL = not written; the request
+ * path cs_poll returns the first seven fields only). */
 typedef struct {
     uint8_t* klass;            /* CS_SECURE .. CS_EIG_FAIL */
     uint8_t* severe;           /* S_c in {0, 1} */
@@ -119,6 +120,11 @@ typedef struct {
     double* min_zeta;          /* smallest damping ratio (NaN if not run) */
     double* Vm;                /* optional [n * n_bus] */
     double* Va;                /* optional [n * n_bus] */
+    /* optional non-binary severity of the converged OPF point (an extension named in
+     * the paper's outlook, Section VI; NULL = not written, NaN when the OPF did not
+     * converge or was not run): */
+    double* v_margin;          /* min over buses of min(Vm - Vmin, Vmax - Vm), p.u. */
+    double* max_loading;       /* max over in-service branch ends of |S| / Smax */
 } cs_result;
 
 /* Create / destroy a context on opt->device (NULL = defaults).  cs_create

@@ -58,7 +58,8 @@ class NetworkDesc(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("klass", ctypes.c_void_p), ("severe", ctypes.c_void_p), ("n_islands", ctypes.c_void_p),
                 ("opf_iters", ctypes.c_void_p), ("cost", ctypes.c_void_p), ("max_re", ctypes.c_void_p),
-                ("min_zeta", ctypes.c_void_p), ("Vm", ctypes.c_void_p), ("Va", ctypes.c_void_p)]
+                ("min_zeta", ctypes.c_void_p), ("Vm", ctypes.c_void_p), ("Va", ctypes.c_void_p),
+                ("v_margin", ctypes.c_void_p), ("max_loading", ctypes.c_void_p)]
 
 
 RESULT_FIELDS = (("klass", np.uint8), ("severe", np.uint8), ("n_islands", np.int16), ("opf_iters", np.int16),
@@ -216,25 +217,30 @@ class Context:
 
     def base_result(self, net_id: int, level: int) -> dict:
         out = {k: np.zeros(1, dt) for k, dt in RESULT_FIELDS}
-        R = Result(*[_ptr(out[k]) for k, _ in RESULT_FIELDS], None, None)
+        R = Result(*[_ptr(out[k]) for k, _ in RESULT_FIELDS], None, None, None, None)
         self._check(self.lib.cs_base_result(self.h, net_id, level, ctypes.byref(R)), "cs_base_result")
         return {k: v[0] for k, v in out.items()}
 
     # ------------------------------------------------------------ evaluation --
     @staticmethod
-    def alloc_results(n: int, device="cuda", n_bus: int = 0):
-        """Result tensors for n records (torch, on ``device``); Vm/Va if n_bus > 0."""
+    def alloc_results(n: int, device="cuda", n_bus: int = 0, indices: bool = False):
+        """Result tensors for n records (torch, on ``device``); Vm/Va if n_bus > 0; the
+        non-binary severity indices (v_margin, max_loading) if indices."""
         import torch
         tmap = {np.uint8: torch.uint8, np.int16: torch.int16, np.float64: torch.float64}
         out = {k: torch.empty(n, dtype=tmap[dt], device=device) for k, dt in RESULT_FIELDS}
         if n_bus:
             out["Vm"] = torch.empty(n * n_bus, dtype=torch.float64, device=device)
             out["Va"] = torch.empty(n * n_bus, dtype=torch.float64, device=device)
+        if indices:
+            out["v_margin"] = torch.empty(n, dtype=torch.float64, device=device)
+            out["max_loading"] = torch.empty(n, dtype=torch.float64, device=device)
         return out
 
     @staticmethod
     def _result_struct(out):
-        return Result(*[_ptr(out[k]) for k, _ in RESULT_FIELDS], _ptr(out.get("Vm")), _ptr(out.get("Va")))
+        return Result(*[_ptr(out[k]) for k, _ in RESULT_FIELDS], _ptr(out.get("Vm")), _ptr(out.get("Va")),
+                      _ptr(out.get("v_margin")), _ptr(out.get("max_loading")))
 
     def evaluate_device(self, net_id: int, level: int, ei, ej, out: dict, stream=None):
         """Asynchronous evaluation of len(ei) scenarios with device tensors."""
@@ -289,7 +295,7 @@ class Context:
         n = self._keep.get(request_id, 0)
         if out is None:
             out = {k: np.empty(n, dt) for k, dt in RESULT_FIELDS}
-        R = Result(*[_ptr(out[k]) for k, _ in RESULT_FIELDS], None, None)
+        R = Result(*[_ptr(out[k]) for k, _ in RESULT_FIELDS], None, None, None, None)
         st = self.lib.cs_poll(self.h, request_id, int(timeout_us), ctypes.byref(R))
         if st == CS_PENDING:
             return None

@@ -74,6 +74,8 @@ void result_layout(char* base, int64_t n, cs_result* r) {
     r->severe = r->klass + n;
     r->Vm = nullptr;
     r->Va = nullptr;
+    r->v_margin = nullptr;
+    r->max_loading = nullptr;
 }
 
 }  // namespace csi
@@ -143,6 +145,8 @@ cs_status csi::evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level
         a.out.min_zeta = out->min_zeta + c0;
         a.out.Vm = out->Vm ? out->Vm + c0 * dn.nb : nullptr;
         a.out.Va = out->Va ? out->Va + c0 * dn.nb : nullptr;
+        a.out.v_margin = out->v_margin ? out->v_margin + c0 : nullptr;
+        a.out.max_loading = out->max_loading ? out->max_loading + c0 : nullptr;
         a.sev_n1 = record ? (uint8_t*)net->sev_n1[level]->p : nullptr;
         a.sev_pairs = record ? (uint8_t*)net->sev_pairs[level]->p : nullptr;
         a.err = (int*)ctx->err_word.p;
@@ -572,6 +576,8 @@ cs_status cs_evaluate_device(cs_ctx* ctx, int32_t net_id, int32_t level, const i
         o.min_zeta = out->min_zeta + c0;
         o.Vm = out->Vm ? out->Vm + c0 * net->dev.nb : nullptr;
         o.Va = out->Va ? out->Va + c0 * net->dev.nb : nullptr;
+        o.v_margin = out->v_margin ? out->v_margin + c0 : nullptr;
+        o.max_loading = out->max_loading ? out->max_loading + c0 : nullptr;
         const bool second = (q & 1) != 0;
         cs_status st = evaluate_impl(ctx, second ? ctx->direct2 : ctx->direct, net, level, ei + c0, ej + c0, m, &o,
                                      second ? ctx->aux_stream : s, true, chunk);

@@ -37,6 +37,8 @@ __global__ void islands_kernel(DevNet net, EvalArgs a, int* islanded) {
                 a.out.n_islands[s] = 0;
                 a.out.opf_iters[s] = 0;
                 a.out.cost[s] = __longlong_as_double(0x7ff8000000000000ll);
+                if (a.out.v_margin) a.out.v_margin[s] = __longlong_as_double(0x7ff8000000000000ll);
+                if (a.out.max_loading) a.out.max_loading[s] = __longlong_as_double(0x7ff8000000000000ll);
                 a.out.max_re[s] = __longlong_as_double(0x7ff8000000000000ll);
                 a.out.min_zeta[s] = __longlong_as_double(0x7ff8000000000000ll);
             }
@@ -68,6 +70,8 @@ __global__ void islands_kernel(DevNet net, EvalArgs a, int* islanded) {
                 a.out.opf_iters[s] = 0;
                 const double nan = __longlong_as_double(0x7ff8000000000000ll);
                 a.out.cost[s] = nan;
+                if (a.out.v_margin) a.out.v_margin[s] = nan;
+                if (a.out.max_loading) a.out.max_loading[s] = nan;
                 a.out.max_re[s] = nan;
                 a.out.min_zeta[s] = nan;
             }

@@ -1204,7 +1204,7 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
             evaluate(false);
         }
         // ---------------- outputs ----------------
-        double viol = 0.0;
+        double viol = 0.0, load_max = 0.0, vmarg = INFINITY;
         const bool converged = sc.conv && !sc.fail;
         if (converged) {
             for (int b = tid; b < nbr; b += kThreads) {
@@ -1213,10 +1213,12 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                 const double sf = sqrt(fmax(W[L.hf + b] + net.smax2[b], 0.0));
                 const double st = sqrt(fmax(W[L.ht + b] + net.smax2[b], 0.0));
                 if (sf - sm > kLimitTol || st - sm > kLimitTol) viol = 1.0;
+                load_max = fmax(load_max, fmax(sf, st) / sm);
             }
             for (int i = tid; i < nb; i += kThreads) {
                 const double Vm = W[L.Vm + i];
                 if (Vm - net.vmax[i] > kLimitTol || net.vmin[i] - Vm > kLimitTol) viol = 1.0;
+                vmarg = fmin(vmarg, fmin(Vm - net.vmin[i], net.vmax[i] - Vm));
             }
             for (int k = tid; k < ng; k += kThreads) {
                 if (gen_out(out, k)) continue;
@@ -1226,9 +1228,9 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
             }
         }
         {
-            double v1[1] = {viol};
-            const int ops1[1] = {0};
-            block_reduce<1>(rb, v1, ops1, sc.red);
+            double v3[3] = {viol, load_max, vmarg};   // non-binary severity: loading, voltage margin
+            const int ops3[3] = {0, 0, 2};
+            block_reduce<3>(rb, v3, ops3, sc.red);
         }
         double* xs = o.x + (size_t)s * nx;
         for (int i = tid; i < nb; i += kThreads) {
@@ -1245,6 +1247,8 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
             const double nan = __longlong_as_double(0x7ff8000000000000ll);
             a.out.opf_iters[s] = (int16_t)it;
             a.out.cost[s] = converged ? sc.f : nan;
+            if (a.out.max_loading) a.out.max_loading[s] = converged ? sc.red[1] : nan;
+            if (a.out.v_margin) a.out.v_margin[s] = converged ? sc.red[2] : nan;
             if (!converged || sc.red[0] != 0.0) {
                 o.status[s] = 2;
                 a.out.klass[s] = converged ? CS_LIMIT : CS_OPF_NONCONV;
