@@ -28,6 +28,9 @@ Module map (paper passages in parentheses):
 * ``pipeline``  one scenario end to end and the severity class (Sections II-A,
                  II-B).
 * ``risk``      the Risk Index of Eq. 3 computed exactly with rationals.
+* ``island``    main-island OPF of an islanded scenario with the reference
+                 re-assigned, and its load shed (Sections II-A, V-A, VI: the
+                 extension those passages point to).
 
 Parity status per function is listed in each module header.
 """

@@ -1,0 +1,157 @@
+"""Main-island OPF of an islanded scenario, with slack re-assignment (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Section II-B-3 marks every islanded scenario severe.  Section II-A remarks that,
+once a network splits, only the main island (the one tied to the largest
+generation) should be taken as reference, and Section V-A traces most of the
+study's ~1,390 failed cases to a slack bus that is isolated or inside an
+island.  The outlook (Section VI) names the load shed in MW as a non-binary
+severity.  This module is the extension that follows those three remarks; the
+binary severity of an islanded scenario stays 1.
+
+Readings (the paper gives the idea, not the rules):
+  * main island: the connected component whose in-service generators have the
+    largest total Pmax (summed in per unit, in generator order); among equal
+    totals, the component holding the lowest-numbered bus.  No component with
+    a positive total: no main island, the OPF is not run;
+  * reference: the original reference bus if it lies in the main island, else
+    the bus of the main island's in-service generator with the largest Pmax
+    (the lowest generator index among equals);
+  * load shed: the active load (MW) of every bus outside the main island;
+  * the main island's OPF is the unchanged OPF (``opf.solve``) of the network
+    made of the main island alone: its buses renumbered in increasing order,
+    the in-service branches and generators inside it, the new reference.  Its
+    class: SECURE (0) if it converges within every limit, OPF_NONCONV (2), or
+    LIMIT (3).  Bus voltages outside the main island are reported as 0
+    (de-energised).
+
+Pins (``tests/test_oracle_island.py``): two networks built apart and joined by
+one tie branch; with the tie out, the main island's OPF equals the standalone
+OPF of the network with the larger generation (cost, magnitudes, angles up to
+the reference shift), the shed is the other network's load, and swapping the
+generation swaps the choice; equal generation picks the island of bus 0.
+"""
+from __future__ import annotations
+
+import copy
+
+import numpy as np
+
+from . import grid, opf
+
+SECURE, OPF_NONCONV, LIMIT = 0, 2, 3
+NOT_ISLANDED = 255
+
+
+def island_labels(n_bus: int, f, t) -> np.ndarray:
+    """Component label of every bus, by breadth-first search from the lowest
+    unlabelled bus; labels therefore increase with each component's lowest bus."""
+    adj = [[] for _ in range(n_bus)]
+    for a, b in zip(f, t):
+        adj[int(a)].append(int(b))
+        adj[int(b)].append(int(a))
+    lab = np.full(n_bus, -1, np.int64)
+    nxt = 0
+    for s in range(n_bus):
+        if lab[s] >= 0:
+            continue
+        lab[s] = nxt
+        q = [s]
+        while q:
+            u = q.pop()
+            for w in adj[u]:
+                if lab[w] < 0:
+                    lab[w] = nxt
+                    q.append(w)
+        nxt += 1
+    return lab
+
+
+def main_island(net, sc: grid.Scenario):
+    """(live bus mask, reference bus, load shed in MW) of scenario sc; the mask is
+    None when no component has positive generation capacity."""
+    B = net.base_mva
+    lab = island_labels(net.n_bus, net.f[sc.br], net.t[sc.br])
+    ncomp = int(lab.max()) + 1
+    cap = [0.0] * ncomp
+    for k in sc.gen:                                   # generator order, per unit
+        cap[lab[net.gbus[k]]] += net.Pmax[k] / B
+    main, best = -1, 0.0
+    for c in range(ncomp):                             # lowest bus first: ties keep the earlier
+        if cap[c] > best:
+            main, best = c, cap[c]
+    Pd = net.Pd[sc.level]
+    if main < 0:
+        shed = 0.0
+        for i in range(net.n_bus):
+            shed += Pd[i] / B
+        return None, -1, B * shed
+    live = lab == main
+    if live[net.ref_bus]:
+        ref = int(net.ref_bus)
+    else:
+        kbest, pbest = -1, -np.inf
+        for k in sc.gen:
+            if live[net.gbus[k]] and net.Pmax[k] / B > pbest:
+                kbest, pbest = int(k), net.Pmax[k] / B
+        ref = int(net.gbus[kbest])
+    shed = 0.0
+    for i in range(net.n_bus):
+        if not live[i]:
+            shed += Pd[i] / B
+    return live, ref, B * shed
+
+
+def sub_network(net, sc: grid.Scenario, live: np.ndarray, ref: int):
+    """The main island as a network of its own: live buses renumbered in
+    increasing order, the in-service branches and generators inside it."""
+    new = np.full(net.n_bus, -1, np.int64)
+    new[live] = np.arange(int(live.sum()))
+    br = np.array([b for b in sc.br if live[net.f[b]]], np.int64)
+    gen = np.array([k for k in sc.gen if live[net.gbus[k]]], np.int64)
+    sub = copy.copy(net)
+    for name in ("Vmin", "Vmax", "Gs", "Bs", "Pd_shape", "Qd_shape"):
+        setattr(sub, name, np.asarray(getattr(net, name))[live].copy())
+    sub.Pd = np.asarray(net.Pd)[:, live].copy()
+    sub.Qd = np.asarray(net.Qd)[:, live].copy()
+    sub.f = new[net.f[br]]
+    sub.t = new[net.t[br]]
+    for name in ("r", "x", "b", "rate", "tap", "kind"):
+        setattr(sub, name, np.asarray(getattr(net, name))[br].copy())
+    sub.gbus = new[net.gbus[gen]]
+    for name in ("Pmin", "Pmax", "Qmin", "Qmax", "c2", "c1", "c0", "H", "D",
+                 "xd", "xq", "xdp", "Td0p", "Tq0p", "KA", "TA"):
+        v = getattr(net, name, None)
+        if v is not None:
+            setattr(sub, name, np.asarray(v)[gen].copy())
+    sub.ref_bus = int(new[ref])
+    return sub, grid.make_scenario(sub, sc.level)
+
+
+def evaluate_main_island(net, level: int, i: int = -1, j: int = -1, k: int = -1):
+    """Main-island result of scenario (level, i, j[, k]).  A scenario that does not
+    split gets main_klass NOT_ISLANDED and no OPF (the ordinary path covers it)."""
+    sc = grid.make_scenario(net, level, i, j, k)
+    nan = float("nan")
+    out = dict(main_klass=NOT_ISLANDED, shed_mw=0.0, opf_iters=0, converged=False, cost=nan,
+               v_margin=nan, max_loading=nan, ref=-1, live=None, Va=None, Vm=None)
+    if grid.count_islands(net.n_bus, net.f[sc.br], net.t[sc.br]) <= 1:
+        return out
+    live, ref, shed = main_island(net, sc)
+    out.update(shed_mw=shed, main_klass=OPF_NONCONV, ref=ref, live=live)
+    if live is None:
+        return out
+    sub, subsc = sub_network(net, sc, live, ref)
+    r = opf.solve(sub, subsc)
+    Va = np.zeros(net.n_bus)
+    Vm = np.zeros(net.n_bus)
+    Va[live] = r["Va"]
+    Vm[live] = r["Vm"]
+    out.update(opf_iters=r["iterations"], converged=r["converged"], Va=Va, Vm=Vm)
+    if not r["converged"]:
+        return out
+    out["cost"] = r["cost"]
+    out["v_margin"], out["max_loading"] = opf.severity_indices(r)
+    out["main_klass"] = LIMIT if opf.limit_violation(r) else SECURE
+    return out

@@ -1,0 +1,133 @@
+"""Pins of the main-island oracle (oracle/island.py).
+
+Two networks are built apart and joined here by one tie branch, by a
+construction of this test's own.  With the tie out, the main island is the
+network with the larger generation: its OPF must be that network's standalone
+OPF, and the shed must be the other network's load.  The reference is
+re-assigned when it falls outside the main island; the angles then move by one
+constant and nothing else changes.
+"""
+import copy
+
+import numpy as np
+import pytest
+
+from paper_2512_08465_gb300 import synth
+from oracle import grid, island, opf
+
+
+def _join(A, Bn, a_bus, b_bus, ref):
+    """A and B side by side (B's buses after A's), plus one tie branch a_bus - (nA + b_bus)."""
+    nA = A.n_bus
+    J = copy.copy(A)
+    for k in ("Vmin", "Vmax", "Gs", "Bs", "Pd_shape", "Qd_shape"):
+        setattr(J, k, np.concatenate([getattr(A, k), getattr(Bn, k)]))
+    J.Pd = np.concatenate([A.Pd, Bn.Pd], axis=1)
+    J.Qd = np.concatenate([A.Qd, Bn.Qd], axis=1)
+    J.f = np.concatenate([A.f, Bn.f + nA, [a_bus]]).astype(np.int32)
+    J.t = np.concatenate([A.t, Bn.t + nA, [nA + b_bus]]).astype(np.int32)
+    tie = dict(r=0.01, x=0.05, b=0.0, rate=300.0, tap=1.0, kind=synth.KIND_LINE)
+    for k, v in tie.items():
+        J.__dict__[k] = np.concatenate([getattr(A, k), getattr(Bn, k), [v]]).astype(getattr(A, k).dtype)
+    J.gbus = np.concatenate([A.gbus, Bn.gbus + nA]).astype(np.int32)
+    for k in ("Pmin", "Pmax", "Qmin", "Qmax", "c2", "c1", "c0", "H", "D",
+              "xd", "xq", "xdp", "Td0p", "Tq0p", "KA", "TA"):
+        setattr(J, k, np.concatenate([getattr(A, k), getattr(Bn, k)]))
+    J.ref_bus = int(ref)
+    return J
+
+
+def _nets():
+    A = synth.make_network(14, 20, 5, 11, 1, seed=3, levels=(0.5,))
+    Bn = synth.make_network(9, 12, 3, 6, 0, seed=5, levels=(0.5,))
+    return A, Bn
+
+
+def _standalone(net):
+    return opf.solve(net, grid.make_scenario(net, 0))
+
+
+def _check_equal_opf(r, ref_net, live_slice, same_ref):
+    s = _standalone(ref_net)
+    assert s["converged"] and r["converged"]
+    assert abs(r["cost"] - s["cost"]) <= 1e-6 * abs(s["cost"])
+    np.testing.assert_allclose(r["Vm"][live_slice], s["Vm"], atol=1e-6)
+    d = r["Va"][live_slice] - s["Va"]
+    if same_ref:
+        np.testing.assert_allclose(d, 0.0, atol=1e-6)
+    else:
+        assert np.ptp(d) < 1e-6                      # one constant: the reference moved
+
+
+def test_labels_are_components_in_lowest_bus_order():
+    for seed in range(5):
+        net = synth.make_network(20, 22, 4, 10, 0, seed=seed)
+        rng = np.random.default_rng(seed)
+        keep = rng.random(net.n_branch) > 0.25
+        f, t = net.f[keep], net.t[keep]
+        lab = island.island_labels(net.n_bus, f, t)
+        assert np.all(lab[f] == lab[t])
+        assert lab.max() + 1 == grid.count_islands(net.n_bus, f, t)
+        first = [int(np.flatnonzero(lab == c)[0]) for c in range(lab.max() + 1)]
+        assert first == sorted(first)
+
+
+def test_tie_out_larger_generation_is_main_and_slack_moves():
+    A, Bn = _nets()
+    assert A.Pmax.sum() > Bn.Pmax.sum()
+    J = _join(A, Bn, 2, 4, ref=A.n_bus + Bn.ref_bus)          # reference inside B
+    tie = J.n_branch - 1
+    r = island.evaluate_main_island(J, 0, tie)
+    nA = A.n_bus
+    assert r["live"][:nA].all() and not r["live"][nA:].any()
+    assert r["ref"] == int(A.gbus[np.argmax(A.Pmax)])          # largest unit of the main island
+    assert abs(r["Va"][r["ref"]]) < 1e-12 and np.all(r["Vm"][nA:] == 0.0)
+    assert abs(r["shed_mw"] - Bn.Pd[0].sum()) <= 1e-9 * Bn.Pd[0].sum()
+    _check_equal_opf(r, A, slice(0, nA), same_ref=False)
+    assert r["main_klass"] in (island.SECURE, island.LIMIT)
+
+
+def test_reference_kept_when_inside_main_island():
+    A, Bn = _nets()
+    J = _join(A, Bn, 2, 4, ref=A.ref_bus)
+    r = island.evaluate_main_island(J, 0, J.n_branch - 1)
+    assert r["ref"] == A.ref_bus
+    _check_equal_opf(r, A, slice(0, A.n_bus), same_ref=True)
+
+
+def test_swapping_generation_swaps_the_main_island():
+    A, Bn = _nets()
+    Bn = copy.copy(Bn)
+    for k in ("Pmax", "Qmax", "Qmin"):
+        setattr(Bn, k, 10.0 * getattr(Bn, k))
+    assert Bn.Pmax.sum() > A.Pmax.sum()
+    J = _join(A, Bn, 2, 4, ref=A.ref_bus)
+    r = island.evaluate_main_island(J, 0, J.n_branch - 1)
+    nA = A.n_bus
+    assert r["live"][nA:].all() and not r["live"][:nA].any()
+    assert r["ref"] == nA + int(Bn.gbus[np.argmax(Bn.Pmax)])
+    assert abs(r["shed_mw"] - A.Pd[0].sum()) <= 1e-9 * A.Pd[0].sum()
+    _check_equal_opf(r, Bn, slice(nA, J.n_bus), same_ref=False)
+
+
+def test_equal_generation_picks_the_island_of_bus_zero():
+    A, _ = _nets()
+    J = _join(A, A, 1, 1, ref=A.n_bus + A.ref_bus)
+    r = island.evaluate_main_island(J, 0, J.n_branch - 1)
+    assert r["live"][:A.n_bus].all() and not r["live"][A.n_bus:].any()
+
+
+def test_connected_scenario_is_not_islanded():
+    A, _ = _nets()
+    r = island.evaluate_main_island(A, 0)
+    assert r["main_klass"] == island.NOT_ISLANDED and r["shed_mw"] == 0.0 and r["opf_iters"] == 0
+
+
+def test_no_generation_anywhere_means_no_main_island():
+    net = synth.make_network(9, 9, 1, 6, 0, seed=5, levels=(0.5,))
+    bridges = [b for b in range(net.n_branch)
+               if grid.count_islands(net.n_bus, np.delete(net.f, b), np.delete(net.t, b)) > 1]
+    assert bridges
+    r = island.evaluate_main_island(net, 0, bridges[0], net.n_branch)    # the only generator out too
+    assert r["live"] is None and r["main_klass"] == island.OPF_NONCONV
+    assert abs(r["shed_mw"] - net.Pd[0].sum()) <= 1e-9 * net.Pd[0].sum()
