@@ -217,8 +217,8 @@ def run_ours(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def make(prec):
-        ctx = cs.Context(device=local, precision=prec)
+    def make(prec, **opt):
+        ctx = cs.Context(device=local, precision=prec, **opt)
         nid = ctx.load_network(net)
         return ctx, nid
 
@@ -228,8 +228,9 @@ def run_ours(args):
     n1i = torch.arange(E, dtype=torch.int32, device=dev)
     n1j = torch.full((E,), -1, dtype=torch.int32, device=dev)
 
-    def measure(ctx, nid, warmup, steps, clocks=False):
-        outs = {lv: (ctx.alloc_results(npair, dev), ctx.alloc_results(E, dev)) for lv in (0, 1)}
+    def measure(ctx, nid, warmup, steps, clocks=False, main=False):
+        outs = {lv: (ctx.alloc_results(npair, dev, main_island=main), ctx.alloc_results(E, dev, main_island=main))
+                for lv in (0, 1)}
         launches = [0]
 
         def step():
@@ -278,8 +279,10 @@ def run_ours(args):
         klass = [outs[lv][0]["klass"].cpu().numpy() for lv in (0, 1)]
         stats = {f: [outs[lv][0][f].cpu().numpy() for lv in (0, 1)] for f in ("max_re", "min_zeta")}
         iters = sum(int(outs[lv][q]["opf_iters"].to(torch.int64).sum().item()) for lv in (0, 1) for q in (0, 1))
+        mk = [outs[lv][0]["main_klass"].cpu().numpy() for lv in (0, 1)] if main else None
+        shed = [outs[lv][0]["shed_mw"].cpu().numpy() for lv in (0, 1)] if main else None
         return dict(ms=ms_max, wall=wall, kms=kms, kcnt=kcnt, clocks=clk, launches=launches[0],
-                    klass=klass, iters=iters, stats=stats)
+                    klass=klass, iters=iters, stats=stats, main_klass=mk, shed=shed)
 
     ctx_m, nid_m = make(cs.PREC_MIXED)
     mixed = measure(ctx_m, nid_m, args.warmup, args.steps, clocks=True)
@@ -309,11 +312,26 @@ def run_ours(args):
     same = all(np.array_equal(a, b) for a, b in zip(mixed["klass"], fp64["klass"]))
     # largest deviation of the mixed form's eigen statistics from the FP64 form's (FP32 screen
     # outside the guard band; scenarios re-run in FP64 agree to rounding)
-    dev = {}
+    mdev = {}
     for f in ("max_re", "min_zeta"):
         d = [np.abs(a - b)[np.isfinite(a) & np.isfinite(b)] for a, b in zip(mixed["stats"][f], fp64["stats"][f])]
-        dev[f] = float(max((x.max() if x.size else 0.0) for x in d))
+        mdev[f] = float(max((x.max() if x.size else 0.0) for x in d))
     ctx_d.close()
+    # main-island form: every islanded pair also gets its main island's OPF (classes unchanged)
+    ctx_i, nid_i = make(cs.PREC_MIXED, main_island=1)
+    isl = measure(ctx_i, nid_i, 1, min(2, args.steps), main=True)
+    ctx_i.close()
+    mk = np.concatenate(isl["main_klass"])
+    shed = np.concatenate(isl["shed"])
+    n_isl = int((mk != 255).sum())
+    main_form = {"value": 2 * npair * world / (isl["ms"] / 1e3), "ms_per_step": isl["ms"], "steps": min(2, args.steps),
+                 "kernel_ms_per_step": {k: v / min(2, args.steps) for k, v in isl["kms"].items()},
+                 "classes_identical_to_mixed": bool(all(np.array_equal(a, b) for a, b in
+                                                        zip(mixed["klass"], isl["klass"]))),
+                 "main_island_opfs_per_step": n_isl,
+                 "main_klass_counts": {"secure": int((mk == 0).sum()), "opf_nonconv": int((mk == 2).sum()),
+                                       "limit": int((mk == 3).sum())},
+                 "shed_mw_mean_over_islanded": float(shed[mk != 255].mean()) if n_isl else None}
 
     n2 = 2 * npair * world
     value = n2 / (mixed["ms"] / 1e3)
@@ -401,7 +419,8 @@ def run_ours(args):
             "fp64_form": {"value": n2 / (fp64["ms"] / 1e3), "ms_per_step": fp64["ms"],
                           "kernel_ms_per_step": {k: v / args.steps for k, v in fp64["kms"].items()},
                           "classes_identical_to_mixed": bool(same),
-                          "mixed_max_abs_dev": dev},
+                          "mixed_max_abs_dev": mdev},
+            "main_island_form": main_form,
             "roofline": roof,
             "roofline_other": roof_other,
             "risk_index_monte_carlo": mc,

@@ -82,10 +82,13 @@ typedef struct {
                                   request buffers); 0 = no limit */
     int32_t serve_slots;       /* batches in flight on the serving path (1..8, default 2) */
     int32_t batch_cap;         /* scenarios per serving batch (default 16384) */
+    int32_t main_island;       /* 1: an islanded scenario also gets the OPF of its main island
+                                  (see cs_result.main_klass); 0 (default): not run, as in the paper */
 } cs_options;
 
 /* Fills *opt with the defaults (damping_min 0.05, opf_tol 1e-8, opf_max_it 50,
- * FP64 form, no device-memory budget, 2 serving slots, batches of 16384). */
+ * FP64 form, no device-memory budget, 2 serving slots, batches of 16384, no
+ * main-island OPF). */
 void cs_default_options(cs_options* opt);
 
 /* Raw network data in structure-of-arrays form, host memory, copied by
@@ -108,8 +111,8 @@ typedef struct {
 
 /* Per-scenario results, structure of arrays with n records.  Which memory
  * (device or host) each entry point expects is stated at the entry point.
- * Vm / Va, v_margin / max_loading are optional (NULL = not written; the request
- * path cs_poll returns the first seven fields only). */
+ * Vm / Va, v_margin / max_loading, shed_mw / main_klass are optional (NULL = not
+ * written; the request path cs_poll returns the first seven fields only). */
 typedef struct {
     uint8_t* klass;            /* CS_SECURE .. CS_EIG_FAIL */
     uint8_t* severe;           /* S_c in {0, 1} */
@@ -125,6 +128,21 @@ typedef struct {
      * converge or was not run): */
     double* v_margin;          /* min over buses of min(Vm - Vmin, Vmax - Vm), p.u. */
     double* max_loading;       /* max over in-service branch ends of |S| / Smax */
+    /* optional main-island result of an islanded scenario (NULL = not written).  Section II-A
+     * takes the island tied to the largest generation as the reference once a network
+     * splits, Section V-A ties most failed cases to an isolated slack bus and Section VI
+     * names load shed as a severity; with cs_options.main_island = 1 an islanded scenario
+     * (klass and severe stay CS_ISLANDED and 1) gets the OPF of its main island: the
+     * component whose in-service generators have the largest total Pmax (equal totals:
+     * the component of the lowest-numbered bus), with the reference bus moved to the
+     * island's largest in-service unit (lowest index among equals) when the original one
+     * lies outside.  opf_iters, cost, v_margin, max_loading, Vm and Va then describe that
+     * OPF (Vm = Va = 0 at buses outside the main island); no eigenvalue screen is run. */
+    double* shed_mw;           /* active load outside the main island, MW (0 if not islanded,
+                                  NaN if islanded and main_island = 0) */
+    uint8_t* main_klass;       /* CS_SECURE, CS_OPF_NONCONV (also: no component has generation)
+                                  or CS_LIMIT for the main island; 255 if not islanded or
+                                  main_island = 0 */
 } cs_result;
 
 /* Create / destroy a context on opt->device (NULL = defaults).  cs_create

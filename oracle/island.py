@@ -155,3 +155,42 @@ def evaluate_main_island(net, level: int, i: int = -1, j: int = -1, k: int = -1)
     out["v_margin"], out["max_loading"] = opf.severity_indices(r)
     out["main_klass"] = LIMIT if opf.limit_violation(r) else SECURE
     return out
+
+
+# ---- many scenarios in spawned worker processes (tests) ----
+
+_NET = None
+
+
+def _init_worker(net):
+    global _NET
+    _NET = net
+
+
+def _eval_one(args):
+    level, i, j = args
+    return evaluate_main_island(_NET, level, i, j)
+
+
+def evaluate_main_island_many(net, scenarios, processes: int | None = None):
+    """evaluate_main_island over a list of (level, i, j) in spawned workers (one BLAS
+    thread each; spawned, never forked, so it is safe after CUDA use)."""
+    import multiprocessing as mp
+    import os
+    args = [(int(l), int(i), int(j)) for (l, i, j) in scenarios]
+    procs = min(processes or os.cpu_count() or 1, max(1, len(args)))
+    if procs <= 1:
+        _init_worker(net)
+        return [_eval_one(a) for a in args]
+    old = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in old:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(procs, initializer=_init_worker, initargs=(net,)) as pool:
+            return pool.map(_eval_one, args, chunksize=max(1, len(args) // (4 * procs)))
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v

@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("damping_min", ctypes.c_double), ("opf_tol", ctypes.c_double),
                 ("opf_max_it", ctypes.c_int32), ("require_secure_base", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("hbm_budget", ctypes.c_int64), ("serve_slots", ctypes.c_int32), ("batch_cap", ctypes.c_int32)]
+                ("hbm_budget", ctypes.c_int64), ("serve_slots", ctypes.c_int32), ("batch_cap", ctypes.c_int32),
+                ("main_island", ctypes.c_int32)]
 
 
 class NetworkDesc(ctypes.Structure):
@@ -59,7 +60,8 @@ class Result(ctypes.Structure):
     _fields_ = [("klass", ctypes.c_void_p), ("severe", ctypes.c_void_p), ("n_islands", ctypes.c_void_p),
                 ("opf_iters", ctypes.c_void_p), ("cost", ctypes.c_void_p), ("max_re", ctypes.c_void_p),
                 ("min_zeta", ctypes.c_void_p), ("Vm", ctypes.c_void_p), ("Va", ctypes.c_void_p),
-                ("v_margin", ctypes.c_void_p), ("max_loading", ctypes.c_void_p)]
+                ("v_margin", ctypes.c_void_p), ("max_loading", ctypes.c_void_p),
+                ("shed_mw", ctypes.c_void_p), ("main_klass", ctypes.c_void_p)]
 
 
 RESULT_FIELDS = (("klass", np.uint8), ("severe", np.uint8), ("n_islands", np.int16), ("opf_iters", np.int16),
@@ -223,9 +225,10 @@ class Context:
 
     # ------------------------------------------------------------ evaluation --
     @staticmethod
-    def alloc_results(n: int, device="cuda", n_bus: int = 0, indices: bool = False):
+    def alloc_results(n: int, device="cuda", n_bus: int = 0, indices: bool = False, main_island: bool = False):
         """Result tensors for n records (torch, on ``device``); Vm/Va if n_bus > 0; the
-        non-binary severity indices (v_margin, max_loading) if indices."""
+        non-binary severity indices (v_margin, max_loading) if indices; the main-island
+        fields (shed_mw, main_klass) if main_island."""
         import torch
         tmap = {np.uint8: torch.uint8, np.int16: torch.int16, np.float64: torch.float64}
         out = {k: torch.empty(n, dtype=tmap[dt], device=device) for k, dt in RESULT_FIELDS}
@@ -235,12 +238,16 @@ class Context:
         if indices:
             out["v_margin"] = torch.empty(n, dtype=torch.float64, device=device)
             out["max_loading"] = torch.empty(n, dtype=torch.float64, device=device)
+        if main_island:
+            out["shed_mw"] = torch.empty(n, dtype=torch.float64, device=device)
+            out["main_klass"] = torch.empty(n, dtype=torch.uint8, device=device)
         return out
 
     @staticmethod
     def _result_struct(out):
         return Result(*[_ptr(out[k]) for k, _ in RESULT_FIELDS], _ptr(out.get("Vm")), _ptr(out.get("Va")),
-                      _ptr(out.get("v_margin")), _ptr(out.get("max_loading")))
+                      _ptr(out.get("v_margin")), _ptr(out.get("max_loading")),
+                      _ptr(out.get("shed_mw")), _ptr(out.get("main_klass")))
 
     def evaluate_device(self, net_id: int, level: int, ei, ej, out: dict, stream=None):
         """Asynchronous evaluation of len(ei) scenarios with device tensors."""

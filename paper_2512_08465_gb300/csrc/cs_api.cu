@@ -64,6 +64,24 @@ size_t reserved_bytes(const cs_ctx* ctx) {
 
 size_t result_bytes(int64_t n) { return (size_t)n * (8 * 3 + 2 + 2 + 1 + 1); }
 
+cs_result result_at(const cs_result& r, int64_t c0, int nb) {
+    cs_result o = r;
+    o.klass = r.klass + c0;
+    o.severe = r.severe + c0;
+    o.n_islands = r.n_islands + c0;
+    o.opf_iters = r.opf_iters + c0;
+    o.cost = r.cost + c0;
+    o.max_re = r.max_re + c0;
+    o.min_zeta = r.min_zeta + c0;
+    o.Vm = r.Vm ? r.Vm + c0 * nb : nullptr;
+    o.Va = r.Va ? r.Va + c0 * nb : nullptr;
+    o.v_margin = r.v_margin ? r.v_margin + c0 : nullptr;
+    o.max_loading = r.max_loading ? r.max_loading + c0 : nullptr;
+    o.shed_mw = r.shed_mw ? r.shed_mw + c0 : nullptr;
+    o.main_klass = r.main_klass ? r.main_klass + c0 : nullptr;
+    return o;
+}
+
 void result_layout(char* base, int64_t n, cs_result* r) {
     r->cost = (double*)base;                         // doubles first for alignment
     r->max_re = r->cost + n;
@@ -76,6 +94,8 @@ void result_layout(char* base, int64_t n, cs_result* r) {
     r->Va = nullptr;
     r->v_margin = nullptr;
     r->max_loading = nullptr;
+    r->shed_mw = nullptr;
+    r->main_klass = nullptr;
 }
 
 }  // namespace csi
@@ -135,18 +155,8 @@ cs_status csi::evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level
         a.ek = ek ? ek + c0 : nullptr;
         a.n = (int)m;
         a.level = level;
-        a.out = *out;
-        a.out.klass = out->klass + c0;
-        a.out.severe = out->severe + c0;
-        a.out.n_islands = out->n_islands + c0;
-        a.out.opf_iters = out->opf_iters + c0;
-        a.out.cost = out->cost + c0;
-        a.out.max_re = out->max_re + c0;
-        a.out.min_zeta = out->min_zeta + c0;
-        a.out.Vm = out->Vm ? out->Vm + c0 * dn.nb : nullptr;
-        a.out.Va = out->Va ? out->Va + c0 * dn.nb : nullptr;
-        a.out.v_margin = out->v_margin ? out->v_margin + c0 : nullptr;
-        a.out.max_loading = out->max_loading ? out->max_loading + c0 : nullptr;
+        a.out = result_at(*out, c0, dn.nb);
+        a.main_island = ctx->opt.main_island != 0;
         a.sev_n1 = record ? (uint8_t*)net->sev_n1[level]->p : nullptr;
         a.sev_pairs = record ? (uint8_t*)net->sev_pairs[level]->p : nullptr;
         a.err = (int*)ctx->err_word.p;
@@ -207,6 +217,7 @@ void cs_default_options(cs_options* o) {
     o->hbm_budget = 0;
     o->serve_slots = 2;
     o->batch_cap = 16384;
+    o->main_island = 0;
 }
 
 cs_status cs_create(const cs_options* opt, cs_ctx** out) {
@@ -566,18 +577,7 @@ cs_status cs_evaluate_device(cs_ctx* ctx, int32_t net_id, int32_t level, const i
     int q = 0;
     for (int64_t c0 = 0; c0 < n; c0 += chunk, ++q) {
         const int64_t m = std::min(chunk, n - c0);
-        cs_result o = *out;
-        o.klass = out->klass + c0;
-        o.severe = out->severe + c0;
-        o.n_islands = out->n_islands + c0;
-        o.opf_iters = out->opf_iters + c0;
-        o.cost = out->cost + c0;
-        o.max_re = out->max_re + c0;
-        o.min_zeta = out->min_zeta + c0;
-        o.Vm = out->Vm ? out->Vm + c0 * net->dev.nb : nullptr;
-        o.Va = out->Va ? out->Va + c0 * net->dev.nb : nullptr;
-        o.v_margin = out->v_margin ? out->v_margin + c0 : nullptr;
-        o.max_loading = out->max_loading ? out->max_loading + c0 : nullptr;
+        const cs_result o = result_at(*out, c0, net->dev.nb);
         const bool second = (q & 1) != 0;
         cs_status st = evaluate_impl(ctx, second ? ctx->direct2 : ctx->direct, net, level, ei + c0, ej + c0, m, &o,
                                      second ? ctx->aux_stream : s, true, chunk);

@@ -151,6 +151,7 @@ struct EvalArgs {
     int* err;               // device error word
     int* reruns;            // device counter: FP64 eigen re-runs of the mixed-precision screen
     const int* ek;          // [n] third outage element (N-3), or nullptr
+    bool main_island;       // islanded scenarios also get the OPF of their main island
 };
 
 // launch wrappers (return cudaError_t)

@@ -183,6 +183,9 @@ cs_status evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level, con
 size_t result_bytes(int64_t n);
 void result_layout(char* base, int64_t n, cs_result* r);
 
+// The records of r from scenario c0 on (optional arrays stay NULL; nb = buses per Vm / Va row).
+cs_result result_at(const cs_result& r, int64_t c0, int nb);
+
 // Serving scheduler (serve.cu): stop and join before the context goes away;
 // true if a request in the queue or in flight refers to net_id.
 void serve_shutdown(cs_ctx* ctx);

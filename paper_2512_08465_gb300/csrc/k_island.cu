@@ -39,6 +39,8 @@ __global__ void islands_kernel(DevNet net, EvalArgs a, int* islanded) {
                 a.out.cost[s] = __longlong_as_double(0x7ff8000000000000ll);
                 if (a.out.v_margin) a.out.v_margin[s] = __longlong_as_double(0x7ff8000000000000ll);
                 if (a.out.max_loading) a.out.max_loading[s] = __longlong_as_double(0x7ff8000000000000ll);
+                if (a.out.shed_mw) a.out.shed_mw[s] = __longlong_as_double(0x7ff8000000000000ll);
+                if (a.out.main_klass) a.out.main_klass[s] = 255;
                 a.out.max_re[s] = __longlong_as_double(0x7ff8000000000000ll);
                 a.out.min_zeta[s] = __longlong_as_double(0x7ff8000000000000ll);
             }
@@ -64,6 +66,10 @@ __global__ void islands_kernel(DevNet net, EvalArgs a, int* islanded) {
         if (lane == 0) {
             islanded[s] = cnt > 1 ? 1 : 0;
             a.out.n_islands[s] = (int16_t)(cnt > 32767 ? 32767 : cnt);
+            // main-island fields: the OPF kernel fills them for islanded scenarios
+            // when the main-island form is on
+            if (a.out.shed_mw) a.out.shed_mw[s] = cnt > 1 ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
+            if (a.out.main_klass) a.out.main_klass[s] = 255;
             if (cnt > 1) {
                 a.out.klass[s] = CS_ISLANDED;
                 a.out.severe[s] = 1;

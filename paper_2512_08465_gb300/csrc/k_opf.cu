@@ -34,7 +34,16 @@
 //  * every branch quantity (flows, first and second derivatives of both end
 //    powers, the weighted 4x4 Hessian) is computed once per iteration by one
 //    thread from the branch's own four voltage variables and gathered by
-//    buses and blocks, deterministically (no atomics).
+//    buses and blocks, deterministically (no atomics);
+//  * main-island form (an extension after Sections II-A, V-A and VI): an
+//    islanded scenario gets the OPF of the component whose in-service
+//    generators have the largest total Pmax.  Buses outside it are masked like
+//    outaged elements (identity blocks, no rows, no constraints, their load
+//    shed), so the pattern and the symbolic analysis stay those of the
+//    network; the reference moves to the island's largest unit when the
+//    original one lies outside.  A generator bus carries the generator's
+//    multiplier diagonal, so its reference block stays a regular pivot
+//    wherever it falls in the elimination order.
 #include <cmath>
 
 #include "cs_internal.h"
@@ -81,6 +90,7 @@ struct Lay {
     // KKT: assembled blocks (Kb, Kd) kept for refinement, factor (Ub, Lb, Db, Di), vectors
     int Kb, Kd, Ub, Lb, Db, Di, x, bv, rv, cs;
     int kv, kz, gx0, gxb, gr;   // GMRES: Krylov basis, preconditioned basis, start, best iterate, work
+    int uf, cap, dead;          // main island: union-find parents (int), capacity per root, bus flags (bytes)
     long dense;                 // dense fallback matrix (4nb)^2, -1 if the network is too large
     long total;
 };
@@ -106,6 +116,7 @@ Lay make_layout(const DevNet& n) {
     L.x = take(4 * nb); L.bv = take(4 * nb); L.rv = take(4 * nb); L.cs = take(4 * nb);
     L.kv = take(4 * nb * (kGmresM + 1)); L.kz = take(4 * nb * kGmresM);
     L.gx0 = take(4 * nb); L.gxb = take(4 * nb); L.gr = take(4 * nb);
+    L.uf = take((nb + 1) / 2); L.cap = take(nb); L.dead = take((nb + 7) / 8);
     o = (o + 31) & ~31;
     if (4 * nb <= kDenseMax) {
         L.dense = o;
@@ -743,10 +754,87 @@ __device__ bool dense_solve(const DevNet& net, double* W, const Lay& L, DenseSha
 struct Scal {          // per-scenario scalars in shared memory
     double gamma, f, f_prev, lref, dlref, ap, ad;
     double red[10];
+    double niq, shed;  // number of inequality rows; load outside the main island (p.u.)
     int fail;
     int conv;
     int scen;
+    int ref;           // reference bus of this scenario (-1: no main island)
+    int isl;           // 1: main-island form of an islanded scenario
 };
+
+// In service in this scenario: not outaged and, in the main-island form of an
+// islanded scenario (isl), inside the main island (per-bus flags in the scratch).
+struct Live {
+    const DevNet& net;
+    const Outage& out;
+    const double* W;
+    const Lay& L;
+    const int& isl;        // shared per-scenario flag: the main-island form is on
+    __device__ bool bus(int i) const {
+        return !isl || reinterpret_cast<const unsigned char*>(W + L.dead)[i] == 0;
+    }
+    __device__ bool br(int b) const { return !br_out(out, b) && bus(net.f[b]); }
+    __device__ bool gen(int k) const { return !gen_out(out, k) && bus(net.gbus[k]); }
+};
+
+__device__ int uf_root(int* p, int u) {
+    while (p[u] != u) {
+        p[u] = p[p[u]];
+        u = p[u];
+    }
+    return u;
+}
+
+// Main island of an islanded scenario (one thread; the components are the
+// islanding kernel's, rebuilt here).  Union by the smaller index makes every
+// root its component's lowest bus, so scanning roots in bus order with a
+// strict comparison gives equal totals to the component of the lowest bus.
+// Capacities are summed in per unit in generator order.  Sets the bus flags,
+// sc.ref (-1 if no component has generation), sc.shed and sc.niq.
+__device__ __noinline__ void main_island_setup(const DevNet& net, const Outage& out, const double* Pd, double* W,
+                                  const Lay& L, Scal& sc) {
+    const int nb = net.nb;
+    int* par = reinterpret_cast<int*>(W + L.uf);
+    double* cap = W + L.cap;
+    unsigned char* dead = reinterpret_cast<unsigned char*>(W + L.dead);
+    for (int i = 0; i < nb; ++i) { par[i] = i; cap[i] = 0.0; }
+    for (int b = 0; b < net.nbr; ++b) {
+        if (br_out(out, b)) continue;
+        const int x = uf_root(par, net.f[b]), y = uf_root(par, net.t[b]);
+        if (x != y) {
+            if (x < y) par[y] = x; else par[x] = y;
+        }
+    }
+    for (int k = 0; k < net.ng; ++k)
+        if (!gen_out(out, k)) cap[uf_root(par, net.gbus[k])] += net.pmax[k];
+    int main = -1;
+    double best = 0.0;
+    for (int i = 0; i < nb; ++i)
+        if (par[i] == i && cap[i] > best) { main = i; best = cap[i]; }
+    double shed = 0.0;
+    int nb_live = 0;
+    for (int i = 0; i < nb; ++i) {
+        const bool d = (main < 0) || uf_root(par, i) != main;
+        dead[i] = d ? 1 : 0;
+        if (d) shed += Pd[i]; else ++nb_live;
+    }
+    int ref = -1;
+    if (main >= 0) {
+        if (!dead[net.ref]) {
+            ref = net.ref;
+        } else {
+            double pb = -INFINITY;
+            for (int k = 0; k < net.ng; ++k)
+                if (!gen_out(out, k) && !dead[net.gbus[k]] && net.pmax[k] > pb) { pb = net.pmax[k]; ref = net.gbus[k]; }
+        }
+    }
+    int nbr_live = 0, ng_live = 0;
+    for (int b = 0; b < net.nbr; ++b) nbr_live += (!br_out(out, b) && !dead[net.f[b]]) ? 1 : 0;
+    for (int k = 0; k < net.ng; ++k) ng_live += (!gen_out(out, k) && !dead[net.gbus[k]]) ? 1 : 0;
+    sc.ref = ref;
+    sc.shed = shed;
+    sc.niq = 2.0 * nbr_live + 2.0 * nb_live + 4.0 * ng_live;
+}
 
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, int max_it,
@@ -766,15 +854,42 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
         __syncthreads();
         const int s = sc.scen;
         if (s >= a.n) break;
-        if (islanded[s] != 0) {                // islanded or invalid: nothing to do here
+        const bool isl = islanded[s] == 1 && a.main_island;
+        if (islanded[s] != 0 && !isl) {        // islanded or invalid: nothing to do here
             if (tid == 0) o.status[s] = 3;
             __syncthreads();
             continue;
         }
         const Outage out = decode_outage(nbr, ng, a.ei[s], a.ej[s], a.ek ? a.ek[s] : -1);
-        const int nbr_act = nbr - n_br_out(out);
-        const int ng_act = ng - n_gen_out(out);
-        const double niq = 2.0 * nbr_act + 2.0 * nb + 4.0 * ng_act;
+        if (tid == 0) {
+            sc.isl = isl ? 1 : 0;
+            if (isl) {
+                main_island_setup(net, out, Pd, W, L, sc);
+            } else {
+                sc.ref = net.ref;
+                sc.niq = 2.0 * (nbr - n_br_out(out)) + 2.0 * nb + 4.0 * (ng - n_gen_out(out));
+            }
+        }
+        __syncthreads();
+        if (sc.ref < 0) {                      // no component has generation: nothing to run
+            if (tid == 0) {
+                const double nan = __longlong_as_double(0x7ff8000000000000ll);
+                o.status[s] = 3;
+                a.out.opf_iters[s] = 0;
+                if (a.out.shed_mw) a.out.shed_mw[s] = B * sc.shed;
+                if (a.out.main_klass) a.out.main_klass[s] = CS_OPF_NONCONV;
+                if (a.out.max_loading) a.out.max_loading[s] = nan;
+                if (a.out.v_margin) a.out.v_margin[s] = nan;
+            }
+            for (int i = tid; i < nb; i += kThreads) {
+                if (a.out.Va) a.out.Va[(size_t)s * nb + i] = 0.0;
+                if (a.out.Vm) a.out.Vm[(size_t)s * nb + i] = 0.0;
+            }
+            __syncthreads();
+            continue;
+        }
+        const Live lv{net, out, W, L, sc.isl};
+        const double niq = sc.niq;
 
         // ---------------- initial point ----------------
         if (tid == 0) {
@@ -790,7 +905,7 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
             W[L.lQ + i] = 0.0;
         }
         for (int k = tid; k < ng; k += kThreads) {
-            const bool off = gen_out(out, k);
+            const bool off = !lv.gen(k);
             W[L.Pg + k] = off ? 0.0 : 0.5 * (net.pmin[k] + net.pmax[k]);
             W[L.Qg + k] = 0.0;
         }
@@ -801,7 +916,7 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
         auto evaluate = [&](bool init) {
             const double gamma = init ? 1.0 : sc.gamma;
             for (int b = tid; b < nbr; b += kThreads) {
-                if (br_out(out, b)) {
+                if (!lv.br(b)) {
                     double* rec = W + L.rec + (size_t)kRec * b;
                     for (int q = 0; q < kRec; ++q) rec[q] = 0.0;
                     W[L.zf + b] = 1.0; W[L.zt + b] = 1.0; W[L.muf + b] = 0.0; W[L.mut + b] = 0.0;
@@ -814,7 +929,7 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
             // per-thread partial reductions: maxg, maxh, maxx, maxz, maxmu, maxLx, maxlam, sumzmu, cost, nonfinite
             double v[10] = {0.0, -INFINITY, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
             for (int b = tid; b < nbr; b += kThreads) {
-                if (br_out(out, b)) continue;
+                if (!lv.br(b)) continue;
                 const double zf = W[L.zf + b], zt = W[L.zt + b], mf = W[L.muf + b], mt = W[L.mut + b];
                 v[1] = fmax(v[1], fmax(W[L.hf + b], W[L.ht + b]));
                 v[3] = fmax(v[3], fmax(zf, zt));
@@ -822,6 +937,13 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                 v[7] += zf * mf + zt * mt;
             }
             for (int i = tid; i < nb; i += kThreads) {
+                if (!lv.bus(i)) {              // outside the main island: no rows, no bounds, load shed
+                    if (init) { W[L.zu + i] = 1.0; W[L.zl + i] = 1.0; W[L.muu + i] = 0.0; W[L.mul + i] = 0.0; }
+                    W[L.gP + i] = 0.0; W[L.gQ + i] = 0.0; W[L.LxVa + i] = 0.0; W[L.LxVm + i] = 0.0;
+                    W[L.NVa + i] = 0.0; W[L.NVm + i] = 0.0; W[L.DP + i] = 0.0; W[L.DQ + i] = 0.0;
+                    W[L.rP + i] = 0.0; W[L.rQ + i] = 0.0;
+                    continue;
+                }
                 const double Vm = W[L.Vm + i], Va = W[L.Va + i];
                 const double hu = Vm - net.vmax[i], hl = net.vmin[i] - Vm;
                 double zu, zl, muu, mul;
@@ -839,7 +961,7 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                 for (int e = net.bus_br_ptr[i]; e < net.bus_br_ptr[i + 1]; ++e) {
                     const int code = net.bus_br[e];
                     const int b = code >> 1, side = code & 1;
-                    if (br_out(out, b)) continue;
+                    if (!lv.br(b)) continue;
                     const double* rec = W + L.rec + (size_t)kRec * b;
                     Sre += rec[side ? R_ST : R_SF];
                     Sim += rec[(side ? R_ST : R_SF) + 1];
@@ -849,11 +971,11 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                     NVa += rec[R_NG + p0];
                     NVm += rec[R_NG + p0 + 1];
                 }
-                if (i == net.ref) LxVa += sc.lref;
+                if (i == sc.ref) LxVa += sc.lref;
                 double Pgen = 0.0, Qgen = 0.0, DP = 0.0, DQ = 0.0, rP = 0.0, rQ = 0.0;
                 for (int e = net.bus_gen_ptr[i]; e < net.bus_gen_ptr[i + 1]; ++e) {
                     const int k = net.bus_gen[e];
-                    if (gen_out(out, k)) continue;
+                    if (!lv.gen(k)) continue;
                     const double Pg = W[L.Pg + k], Qg = W[L.Qg + k];
                     const double h4[4] = {Pg - net.pmax[k], net.pmin[k] - Pg, Qg - net.qmax[k], net.qmin[k] - Qg};
                     double z4[4], m4[4];
@@ -943,7 +1065,7 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                     for (int e = net.bus_br_ptr[i]; e < net.bus_br_ptr[i + 1]; ++e) {
                         const int code = net.bus_br[e];
                         const int b = code >> 1, side = code & 1;
-                        if (br_out(out, b)) continue;
+                        if (!lv.br(b)) continue;
                         const double* rec = W + L.rec + (size_t)kRec * b;
                         const int p0 = 2 * side;
                         const double* dS = rec + (side ? R_DST : R_DSF);
@@ -961,18 +1083,23 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                         }
                     blk[10] = -W[L.DP + i];
                     blk[15] = -W[L.DQ + i];
-                    if (i == net.ref) {
+                    if (i == sc.ref) {
                         for (int q = 0; q < 4; ++q) { blk[q] = 0.0; blk[4 * q] = 0.0; }
                         blk[0] = 1.0;
                     }
+                    const bool on = lv.bus(i);
+                    if (!on)                   // outside the main island: identity block, zero step
+                        for (int q = 0; q < 16; ++q) blk[q] = (q % 5 == 0) ? 1.0 : 0.0;
                     double* D = W + L.Kd + 16 * j;
                     double* Dc = W + L.Db + 16 * j;
                     for (int q = 0; q < 16; ++q) { D[q] = blk[q]; Dc[q] = blk[q]; }
-                    double bq[4];
-                    bq[0] = (i == net.ref) ? 0.0 : -W[L.NVa + i];
-                    bq[1] = -W[L.NVm + i];
-                    bq[2] = -W[L.gP + i] - W[L.rP + i];
-                    bq[3] = -W[L.gQ + i] - W[L.rQ + i];
+                    double bq[4] = {0.0, 0.0, 0.0, 0.0};
+                    if (on) {
+                        bq[0] = (i == sc.ref) ? 0.0 : -W[L.NVa + i];
+                        bq[1] = -W[L.NVm + i];
+                        bq[2] = -W[L.gP + i] - W[L.rP + i];
+                        bq[3] = -W[L.gQ + i] - W[L.rQ + i];
+                    }
                     for (int q = 0; q < 4; ++q) { W[L.bv + 4 * j + q] = bq[q]; W[L.x + 4 * j + q] = bq[q]; }
                 } else {
                     const int q = tg - nb;
@@ -980,7 +1107,7 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                     const int Rb = net.perm[Rn], Cb = net.perm[Cn];
                     for (int e = net.blk_br_ptr[q]; e < net.blk_br_ptr[q + 1]; ++e) {
                         const int b = net.blk_br[e];
-                        if (br_out(out, b)) continue;
+                        if (!lv.br(b)) continue;
                         const double* rec = W + L.rec + (size_t)kRec * b;
                         const bool flip = (net.f[b] != Rb);     // stored block is (t row, f col)
                         double K[16];
@@ -996,8 +1123,8 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                         for (int r = 0; r < 4; ++r)
                             for (int c = 0; c < 4; ++c) blk[4 * r + c] += flip ? K[4 * c + r] : K[4 * r + c];
                     }
-                    if (Rb == net.ref) for (int c = 0; c < 4; ++c) blk[c] = 0.0;
-                    if (Cb == net.ref) for (int r = 0; r < 4; ++r) blk[4 * r] = 0.0;
+                    if (Rb == sc.ref) for (int c = 0; c < 4; ++c) blk[c] = 0.0;
+                    if (Cb == sc.ref) for (int r = 0; r < 4; ++r) blk[4 * r] = 0.0;
                     double* U = W + L.Ub + 16 * q;
                     double* Kq = W + L.Kb + 16 * q;
                     for (int c = 0; c < 16; ++c) { U[c] = blk[c]; Kq[c] = blk[c]; }
@@ -1070,7 +1197,7 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
             // ---------------- recover the eliminated steps, dz, dmu, ratios ----------------
             double rp = INFINITY, rd = INFINITY, bad = 0.0;
             for (int k = tid; k < ng; k += kThreads) {
-                if (gen_out(out, k)) continue;
+                if (!lv.gen(k)) continue;
                 const int jn = net.iperm[net.gbus[k]];
                 const double dlP = W[L.x + 4 * jn + 2], dlQ = W[L.x + 4 * jn + 3];
                 const double dPg = (-W[L.NP + k] + dlP) / W[L.MP + k];
@@ -1092,7 +1219,7 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                 }
             }
             for (int b = tid; b < nbr; b += kThreads) {
-                if (br_out(out, b)) continue;
+                if (!lv.br(b)) continue;
                 const double* rec = W + L.rec + (size_t)kRec * b;
                 const int fn = net.iperm[net.f[b]], tn = net.iperm[net.t[b]];
                 const double dx[4] = {W[L.x + 4 * fn], W[L.x + 4 * fn + 1], W[L.x + 4 * tn], W[L.x + 4 * tn + 1]};
@@ -1112,6 +1239,7 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                 if (!isfinite(dzf) || !isfinite(dzt) || !isfinite(dmf) || !isfinite(dmt)) bad = 1.0;
             }
             for (int i = tid; i < nb; i += kThreads) {
+                if (!lv.bus(i)) continue;
                 const int jn = net.iperm[i];
                 const double dVm = W[L.x + 4 * jn + 1];
                 const double Vm = W[L.Vm + i];
@@ -1129,12 +1257,12 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
             }
             if (tid == 0) {
                 // multiplier step of the reference-angle row from its Newton row
-                const int i = net.ref;
+                const int i = sc.ref;
                 double row = 0.0;
                 for (int e = net.bus_br_ptr[i]; e < net.bus_br_ptr[i + 1]; ++e) {
                     const int code = net.bus_br[e];
                     const int b = code >> 1, side = code & 1;
-                    if (br_out(out, b)) continue;
+                    if (!lv.br(b)) continue;
                     const double* rec = W + L.rec + (size_t)kRec * b;
                     const int fn = net.iperm[net.f[b]], tn = net.iperm[net.t[b]];
                     const double dx[4] = {W[L.x + 4 * fn], W[L.x + 4 * fn + 1], W[L.x + 4 * tn], W[L.x + 4 * tn + 1]};
@@ -1161,6 +1289,7 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
             const double ap = sc.ap, ad = sc.ad;
             double zmu = 0.0;
             for (int i = tid; i < nb; i += kThreads) {
+                if (!lv.bus(i)) continue;
                 const int jn = net.iperm[i];
                 W[L.Va + i] += ap * W[L.x + 4 * jn];
                 W[L.Vm + i] += ap * W[L.x + 4 * jn + 1];
@@ -1172,7 +1301,7 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                 zmu += zu * mu_ + zl * ml;
             }
             for (int k = tid; k < ng; k += kThreads) {
-                if (gen_out(out, k)) continue;
+                if (!lv.gen(k)) continue;
                 W[L.Pg + k] += ap * W[L.dPg + k];
                 W[L.Qg + k] += ap * W[L.dQg + k];
                 for (int q = 0; q < 4; ++q) {
@@ -1184,7 +1313,7 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                 }
             }
             for (int b = tid; b < nbr; b += kThreads) {
-                if (br_out(out, b)) continue;
+                if (!lv.br(b)) continue;
                 const double zf = W[L.zf + b] + ap * W[L.dzf + b], zt = W[L.zt + b] + ap * W[L.dzt + b];
                 const double mf = W[L.muf + b] + ad * W[L.dmuf + b], mt = W[L.mut + b] + ad * W[L.dmut + b];
                 W[L.zf + b] = zf; W[L.zt + b] = zt; W[L.muf + b] = mf; W[L.mut + b] = mt;
@@ -1208,7 +1337,7 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
         const bool converged = sc.conv && !sc.fail;
         if (converged) {
             for (int b = tid; b < nbr; b += kThreads) {
-                if (br_out(out, b)) continue;
+                if (!lv.br(b)) continue;
                 const double sm = sqrt(net.smax2[b]);
                 const double sf = sqrt(fmax(W[L.hf + b] + net.smax2[b], 0.0));
                 const double st = sqrt(fmax(W[L.ht + b] + net.smax2[b], 0.0));
@@ -1216,12 +1345,13 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                 load_max = fmax(load_max, fmax(sf, st) / sm);
             }
             for (int i = tid; i < nb; i += kThreads) {
+                if (!lv.bus(i)) continue;
                 const double Vm = W[L.Vm + i];
                 if (Vm - net.vmax[i] > kLimitTol || net.vmin[i] - Vm > kLimitTol) viol = 1.0;
                 vmarg = fmin(vmarg, fmin(Vm - net.vmin[i], net.vmax[i] - Vm));
             }
             for (int k = tid; k < ng; k += kThreads) {
-                if (gen_out(out, k)) continue;
+                if (!lv.gen(k)) continue;
                 const double Pg = W[L.Pg + k], Qg = W[L.Qg + k];
                 if (Pg - net.pmax[k] > kLimitTol || net.pmin[k] - Pg > kLimitTol ||
                     Qg - net.qmax[k] > kLimitTol || net.qmin[k] - Qg > kLimitTol) viol = 1.0;
@@ -1234,10 +1364,11 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
         }
         double* xs = o.x + (size_t)s * nx;
         for (int i = tid; i < nb; i += kThreads) {
+            const bool on = lv.bus(i);         // a bus outside the main island is de-energised
             xs[i] = W[L.Va + i];
             xs[nb + i] = W[L.Vm + i];
-            if (a.out.Va) a.out.Va[(size_t)s * nb + i] = W[L.Va + i];
-            if (a.out.Vm) a.out.Vm[(size_t)s * nb + i] = W[L.Vm + i];
+            if (a.out.Va) a.out.Va[(size_t)s * nb + i] = on ? W[L.Va + i] : 0.0;
+            if (a.out.Vm) a.out.Vm[(size_t)s * nb + i] = on ? W[L.Vm + i] : 0.0;
         }
         for (int k = tid; k < ng; k += kThreads) {
             xs[2 * nb + k] = W[L.Pg + k];
@@ -1249,7 +1380,12 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
             a.out.cost[s] = converged ? sc.f : nan;
             if (a.out.max_loading) a.out.max_loading[s] = converged ? sc.red[1] : nan;
             if (a.out.v_margin) a.out.v_margin[s] = converged ? sc.red[2] : nan;
-            if (!converged || sc.red[0] != 0.0) {
+            if (isl) {                         // main island of an islanded scenario: class unchanged
+                o.status[s] = 3;
+                if (a.out.shed_mw) a.out.shed_mw[s] = B * sc.shed;
+                if (a.out.main_klass)
+                    a.out.main_klass[s] = !converged ? CS_OPF_NONCONV : (sc.red[0] != 0.0 ? CS_LIMIT : CS_SECURE);
+            } else if (!converged || sc.red[0] != 0.0) {
                 o.status[s] = 2;
                 a.out.klass[s] = converged ? CS_LIMIT : CS_OPF_NONCONV;
                 a.out.severe[s] = 1;

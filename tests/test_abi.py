@@ -4,6 +4,8 @@ CPU only: no compute call is made here (the host has no GPU)."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -41,7 +43,30 @@ def test_binding_loads_and_defaults():
     L = cs.load_library()
     o = cs.default_options()
     assert abs(o.damping_min - 0.05) < 1e-15 and abs(o.opf_tol - 1e-8) < 1e-20 and o.opf_max_it == 50
+    assert o.main_island == 0 and o.serve_slots == 2 and o.batch_cap == 16384
     assert L.cs_last_error(None) == b"no context"
+
+
+@pytest.mark.parametrize("cname,py", [("cs_options", cs.Options), ("cs_result", cs.Result),
+                                      ("cs_network_desc", cs.NetworkDesc)])
+def test_struct_layouts_match_the_header(cname, py, tmp_path):
+    """Every field offset and the size of the binding's ctypes mirrors equal the C
+    compiler's for include/cs.h (a C probe compiled with the host compiler)."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = [f'printf("size %zu\\n", sizeof({cname}));']
+    lines += [f'printf("{f} %zu\\n", offsetof({cname}, {f}));' for f, _ in py._fields_]
+    src = tmp_path / "probe.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"cs.h\"\nint main(void) {\n"
+                   + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "probe"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                 text=True).stdout.splitlines())
+    assert int(got["size"]) == ctypes.sizeof(py)
+    for f, _ in py._fields_:
+        assert int(got[f]) == getattr(py, f).offset, f
 
 
 def test_library_is_built_for_sm103a_only():
