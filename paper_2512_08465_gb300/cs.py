@@ -143,9 +143,13 @@ def _stream_handle(stream):
 
 
 def default_options(**kw) -> Options:
+    """cs_default_options with the given fields overridden; an unknown field name raises."""
     o = Options()
     load_library().cs_default_options(ctypes.byref(o))
+    names = {f for f, _ in Options._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown cs_options field {k!r} (known: {', '.join(sorted(names))})")
         setattr(o, k, v)
     return o
 
