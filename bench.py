@@ -358,12 +358,12 @@ def run_ours(args):
                 "achieved": _algorithmic_flops(net, mixed["klass"], E) / (kms["dyn"] / args.steps / 1e3) / 1e12},
     }
     # DRAM traffic per launch: bytes per scenario from the ncu captures of the same kernels on
-    # the first 2,048 pairs (profiles/*_118bus_2048pairs.md: OPF 44.2 GB for 1,877 OPFs; front
+    # the first 2,048 pairs (profiles/*_118bus_2048pairs.md: OPF 44.3 GB for 1,877 OPFs; front
     # 4.35 GB + cluster Hessenberg 0.73 GB + QR 0.26 GB for 1,742 converged scenarios), scaled
     # by the scenarios an average launch of this step processes
     n_opf = sum(int(np.sum(k != 1)) for k in mixed["klass"])
     n_conv = sum(int(np.sum((k == 0) | (k == 4) | (k == 5) | (k == 6))) for k in mixed["klass"])
-    per_scen = {"opf": (44.2e9 / 1877, n_opf), "dyn": ((4.354e9 + 0.726e9 + 0.263e9) / 1742, n_conv)}
+    per_scen = {"opf": (44.30e9 / 1877, n_opf), "dyn": ((4.354e9 + 0.726e9 + 0.263e9) / 1742, n_conv)}
     for k, r in roofs.items():
         launches = max(1.0, kcnt[k] / args.steps)
         b_per, units = per_scen[k]
