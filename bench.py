@@ -400,7 +400,7 @@ def run_ours(args):
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_step = sum(e2e_ms) / len(e2e_ms)
     h2d = 2 * (2 * npair + 2 * E) * 4 + 2 * E * 8
-    d2h = 2 * (npair + E) * (1 + 1 + 2 + 2 + 8 * 3) + 2 * E * 8
+    d2h = 2 * (npair + E) * (1 + 1 + 1 + 2 + 2 + 8 * 6) + 2 * E * 8   # every per-scenario record field + R
     lat.sort()
     ctx_m.close()
 

@@ -112,7 +112,7 @@ typedef struct {
 /* Per-scenario results, structure of arrays with n records.  Which memory
  * (device or host) each entry point expects is stated at the entry point.
  * Vm / Va, v_margin / max_loading, shed_mw / main_klass are optional (NULL = not
- * written; the request path cs_poll returns the first seven fields only). */
+ * written; the request path cs_poll returns every field but Vm / Va). */
 typedef struct {
     uint8_t* klass;            /* CS_SECURE .. CS_EIG_FAIL */
     uint8_t* severe;           /* S_c in {0, 1} */

@@ -66,6 +66,9 @@ class Result(ctypes.Structure):
 
 RESULT_FIELDS = (("klass", np.uint8), ("severe", np.uint8), ("n_islands", np.int16), ("opf_iters", np.int16),
                  ("cost", np.float64), ("max_re", np.float64), ("min_zeta", np.float64))
+# optional per-scenario fields, in Result order after Vm / Va; the request path returns them too
+EXTRA_FIELDS = (("v_margin", np.float64), ("max_loading", np.float64), ("shed_mw", np.float64),
+                ("main_klass", np.uint8))
 
 
 class CSError(RuntimeError):
@@ -302,11 +305,14 @@ class Context:
         return rid.value
 
     def poll(self, request_id: int, timeout_us: int = 0, out: dict | None = None):
-        """Results of a finished request as numpy arrays, or None while pending."""
+        """Results of a finished request as numpy arrays (every per-scenario field: the
+        seven record fields, the severity indices and the main-island fields), or None
+        while pending."""
         n = self._keep.get(request_id, 0)
         if out is None:
-            out = {k: np.empty(n, dt) for k, dt in RESULT_FIELDS}
-        R = Result(*[_ptr(out[k]) for k, _ in RESULT_FIELDS], None, None, None, None)
+            out = {k: np.empty(n, dt) for k, dt in RESULT_FIELDS + EXTRA_FIELDS}
+        R = Result(*[_ptr(out[k]) for k, _ in RESULT_FIELDS], None, None,
+                   *[_ptr(out.get(k)) for k, _ in EXTRA_FIELDS])
         st = self.lib.cs_poll(self.h, request_id, int(timeout_us), ctypes.byref(R))
         if st == CS_PENDING:
             return None

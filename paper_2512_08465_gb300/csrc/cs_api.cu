@@ -62,7 +62,7 @@ size_t reserved_bytes(const cs_ctx* ctx) {
     return b;
 }
 
-size_t result_bytes(int64_t n) { return (size_t)n * (8 * 3 + 2 + 2 + 1 + 1); }
+size_t result_bytes(int64_t n) { return (size_t)n * (8 * 6 + 2 + 2 + 1 + 1 + 1); }
 
 cs_result result_at(const cs_result& r, int64_t c0, int nb) {
     cs_result o = r;
@@ -86,16 +86,16 @@ void result_layout(char* base, int64_t n, cs_result* r) {
     r->cost = (double*)base;                         // doubles first for alignment
     r->max_re = r->cost + n;
     r->min_zeta = r->max_re + n;
-    r->n_islands = (int16_t*)(r->min_zeta + n);
+    r->v_margin = r->min_zeta + n;
+    r->max_loading = r->v_margin + n;
+    r->shed_mw = r->max_loading + n;
+    r->n_islands = (int16_t*)(r->shed_mw + n);
     r->opf_iters = r->n_islands + n;
     r->klass = (uint8_t*)(r->opf_iters + n);
     r->severe = r->klass + n;
+    r->main_klass = r->severe + n;
     r->Vm = nullptr;
     r->Va = nullptr;
-    r->v_margin = nullptr;
-    r->max_loading = nullptr;
-    r->shed_mw = nullptr;
-    r->main_klass = nullptr;
 }
 
 }  // namespace csi

@@ -178,8 +178,8 @@ cs_status evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level, con
                         const int32_t* ej, int64_t n, const cs_result* out, cudaStream_t s, bool record,
                         int64_t chunk, const int32_t* ek = nullptr);
 
-// Result records of n scenarios as one SoA block (doubles first): byte size and
-// the pointers into a block at base.
+// Result records of n scenarios as one SoA block (doubles first; every per-scenario
+// field, Vm / Va excluded): byte size and the pointers into a block at base.
 size_t result_bytes(int64_t n);
 void result_layout(char* base, int64_t n, cs_result* r);
 

@@ -80,6 +80,10 @@ void finish_batch(cs_ctx* ctx, Slot& sl, cudaError_t q) {
         std::memcpy(d.opf_iters, b.opf_iters + o, 2 * n);
         std::memcpy(d.klass, b.klass + o, n);
         std::memcpy(d.severe, b.severe + o, n);
+        std::memcpy(d.v_margin, b.v_margin + o, 8 * n);
+        std::memcpy(d.max_loading, b.max_loading + o, 8 * n);
+        std::memcpy(d.shed_mw, b.shed_mw + o, 8 * n);
+        std::memcpy(d.main_klass, b.main_klass + o, n);
         r.state = 2;
         ctx->stats.completed += 1;
     }
@@ -315,6 +319,10 @@ cs_status cs_poll(cs_ctx* ctx, uint64_t request_id, int32_t timeout_us, const cs
         if (out->cost) std::memcpy(out->cost, h.cost, 8 * n);
         if (out->max_re) std::memcpy(out->max_re, h.max_re, 8 * n);
         if (out->min_zeta) std::memcpy(out->min_zeta, h.min_zeta, 8 * n);
+        if (out->v_margin) std::memcpy(out->v_margin, h.v_margin, 8 * n);
+        if (out->max_loading) std::memcpy(out->max_loading, h.max_loading, 8 * n);
+        if (out->shed_mw) std::memcpy(out->shed_mw, h.shed_mw, 8 * n);
+        if (out->main_klass) std::memcpy(out->main_klass, h.main_klass, n);
     }
     ctx->sreqs.erase(it);
     return CS_OK;

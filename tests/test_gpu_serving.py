@@ -14,7 +14,8 @@ from paper_2512_08465_gb300 import cs, synth  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
-FIELDS = ("klass", "severe", "n_islands", "opf_iters", "cost", "max_re", "min_zeta")
+FIELDS = ("klass", "severe", "n_islands", "opf_iters", "cost", "max_re", "min_zeta",
+          "v_margin", "max_loading", "shed_mw", "main_klass")
 
 
 @pytest.fixture(scope="module")
@@ -28,7 +29,7 @@ def nets():
 def _direct(ctx, nid, level, ei, ej):
     ti = torch.as_tensor(np.asarray(ei, np.int32), device=DEV)
     tj = torch.as_tensor(np.asarray(ej, np.int32), device=DEV)
-    out = ctx.alloc_results(ti.numel(), DEV)
+    out = ctx.alloc_results(ti.numel(), DEV, indices=True, main_island=True)
     ctx.evaluate_device(nid, level, ti, tj, out)
     ctx.sync()
     return {k: out[k].cpu().numpy() for k in FIELDS}
@@ -116,4 +117,29 @@ def test_hbm_budget_admission(nets):
     for k in FIELDS:
         np.testing.assert_array_equal(got[k], want[k], err_msg=k)
     ref.close()
+    ctx.close()
+
+
+def test_main_island_requests_equal_direct_evaluation(nets):
+    """With the main-island form on, requests of islanded and connected pairs return the
+    main-island fields (shed, class of the main island, its OPF cost and indices) equal,
+    bit for bit, to direct evaluation."""
+    from oracle import grid
+    small, big = nets
+    ii, jj = synth.all_pairs(big.n_elem)
+    rng = np.random.default_rng(31)
+    sel = rng.choice(ii.size, 1500, replace=False)
+    isl = np.array([grid.count_islands(big.n_bus, *(lambda sc: (big.f[sc.br], big.t[sc.br]))(
+        grid.make_scenario(big, 0, int(ii[q]), int(jj[q])))) > 1 for q in sel])
+    assert isl.sum() > 50
+    ctx = cs.Context(precision=cs.PREC_MIXED, main_island=1)
+    nid = ctx.load_network(big)
+    rids = [ctx.submit(nid, 1, ii[sel[q:q + 500]], jj[sel[q:q + 500]]) for q in range(0, 1500, 500)]
+    outs = [ctx.poll(r, 600_000_000) for r in rids]
+    got = {k: np.concatenate([o[k] for o in outs]) for k in FIELDS}
+    want = _direct(ctx, nid, 1, ii[sel], jj[sel])
+    for k in FIELDS:
+        np.testing.assert_array_equal(got[k], want[k], err_msg=k)
+    assert np.all(got["main_klass"][isl] != 255) and np.all(got["main_klass"][~isl] == 255)
+    assert np.all(got["shed_mw"][~isl] == 0.0) and np.all(got["shed_mw"][isl] >= 0.0)
     ctx.close()
