@@ -64,7 +64,7 @@ def cpu_baseline(net, n=256, seed=1234):
     t0 = time.perf_counter()
     pipeline.evaluate_many(net, sample, cores)
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "per_core": n / dt / cores, "kind": "oracle",
             "sample": f"{n} N-2 scenarios drawn uniformly (seed {seed}) from the 57,360 of the workload, "
                       f"half per load level; {dt:.1f} s wall on {cores} processes"}
 
@@ -93,7 +93,7 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD + f"; reference arm: each step a bounded sample of {per_step} "
                                               f"N-2 scenarios of it on the host cores"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "per_core": v / cores, "kind": "oracle",
                              "sample": last["sample"] if last else ""},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
