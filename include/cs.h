@@ -137,12 +137,15 @@ typedef struct {
      * the component of the lowest-numbered bus), with the reference bus moved to the
      * island's largest in-service unit (lowest index among equals) when the original one
      * lies outside.  opf_iters, cost, v_margin, max_loading, Vm and Va then describe that
-     * OPF (Vm = Va = 0 at buses outside the main island); no eigenvalue screen is run. */
+     * OPF (Vm = Va = 0 at buses outside the main island), and max_re / min_zeta the
+     * small-signal screen of the main island (its in-service units, angles referred to the
+     * first of them) when its OPF converged within every limit. */
     double* shed_mw;           /* active load outside the main island, MW (0 if not islanded,
                                   NaN if islanded and main_island = 0) */
-    uint8_t* main_klass;       /* CS_SECURE, CS_OPF_NONCONV (also: no component has generation)
-                                  or CS_LIMIT for the main island; 255 if not islanded or
-                                  main_island = 0 */
+    uint8_t* main_klass;       /* class of the main island with the precedence of Section II-B:
+                                  CS_OPF_NONCONV (also: no component has generation), CS_LIMIT,
+                                  CS_EIG_FAIL, CS_SS_UNSTABLE, CS_SS_POORLY_DAMPED or CS_SECURE;
+                                  255 if not islanded or main_island = 0 */
 } cs_result;
 
 /* Create / destroy a context on opt->device (NULL = defaults).  cs_create

@@ -21,10 +21,13 @@ Readings (the paper gives the idea, not the rules):
   * load shed: the active load (MW) of every bus outside the main island;
   * the main island's OPF is the unchanged OPF (``opf.solve``) of the network
     made of the main island alone: its buses renumbered in increasing order,
-    the in-service branches and generators inside it, the new reference.  Its
-    class: SECURE (0) if it converges within every limit, OPF_NONCONV (2), or
-    LIMIT (3).  Bus voltages outside the main island are reported as 0
-    (de-energised).
+    the in-service branches and generators inside it, the new reference; a
+    point that converges within every limit then gets the unchanged small-signal
+    screen (``dynamics``, ``eig``) of that network, whose machines are the main
+    island's in-service units (angles referred to the first of them).  Its class
+    follows the pipeline's precedence: OPF_NONCONV (2), LIMIT (3), EIG_FAIL (6),
+    SS_UNSTABLE (4), SS_POORLY_DAMPED (5) or SECURE (0).  Bus voltages outside
+    the main island are reported as 0 (de-energised).
 
 Pins (``tests/test_oracle_island.py``): two networks built apart and joined by
 one tie branch; with the tie out, the main island's OPF equals the standalone
@@ -38,10 +41,11 @@ import copy
 
 import numpy as np
 
-from . import grid, opf
+from . import grid, opf, dynamics, eig
 
-SECURE, OPF_NONCONV, LIMIT = 0, 2, 3
+SECURE, OPF_NONCONV, LIMIT, SS_UNSTABLE, SS_POORLY_DAMPED, EIG_FAIL = 0, 2, 3, 4, 5, 6
 NOT_ISLANDED = 255
+DAMPING_MIN = 0.05
 
 
 def island_labels(n_bus: int, f, t) -> np.ndarray:
@@ -129,13 +133,14 @@ def sub_network(net, sc: grid.Scenario, live: np.ndarray, ref: int):
     return sub, grid.make_scenario(sub, sc.level)
 
 
-def evaluate_main_island(net, level: int, i: int = -1, j: int = -1, k: int = -1):
+def evaluate_main_island(net, level: int, i: int = -1, j: int = -1, k: int = -1,
+                         damping_min: float = DAMPING_MIN):
     """Main-island result of scenario (level, i, j[, k]).  A scenario that does not
     split gets main_klass NOT_ISLANDED and no OPF (the ordinary path covers it)."""
     sc = grid.make_scenario(net, level, i, j, k)
     nan = float("nan")
     out = dict(main_klass=NOT_ISLANDED, shed_mw=0.0, opf_iters=0, converged=False, cost=nan,
-               v_margin=nan, max_loading=nan, ref=-1, live=None, Va=None, Vm=None)
+               v_margin=nan, max_loading=nan, max_re=nan, min_zeta=nan, ref=-1, live=None, Va=None, Vm=None)
     if grid.count_islands(net.n_bus, net.f[sc.br], net.t[sc.br]) <= 1:
         return out
     live, ref, shed = main_island(net, sc)
@@ -153,7 +158,22 @@ def evaluate_main_island(net, level: int, i: int = -1, j: int = -1, k: int = -1)
         return out
     out["cost"] = r["cost"]
     out["v_margin"], out["max_loading"] = opf.severity_indices(r)
-    out["main_klass"] = LIMIT if opf.limit_violation(r) else SECURE
+    if opf.limit_violation(r):
+        out["main_klass"] = LIMIT
+        return out
+    model = dynamics.Model(sub, subsc, r["Va"], r["Vm"], r["Pg"], r["Qg"])
+    lam, ok, _ = eig.eigvals(model.reduced_state_matrix())
+    if not ok:
+        out["main_klass"] = EIG_FAIL
+        return out
+    max_re, min_zeta = eig.stability_stats(lam)
+    out.update(max_re=max_re, min_zeta=min_zeta)
+    if max_re >= 0.0:
+        out["main_klass"] = SS_UNSTABLE
+    elif min_zeta < damping_min:
+        out["main_klass"] = SS_POORLY_DAMPED
+    else:
+        out["main_klass"] = SECURE
     return out
 
 

@@ -474,10 +474,14 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
         }
         const Outage out = decode_outage(nbr, ng, a.ei[s], a.ej[s], a.ek ? a.ek[s] : -1);
         const double* xs = o.x + (size_t)s * nx;
+        // main island of an islanded scenario: the OPF point has Vm = 0 at the buses
+        // outside it; those buses, their branches and their machines are out of the model
+        const bool isl = a.out.n_islands[s] > 1;
+        auto live = [&](int i) { return !isl || xs[nb + i] != 0.0; };
         if (tid == 0) {
             int m = 0;
             for (int k = 0; k < ng; ++k)
-                if (!gen_out(out, k)) gidx[m++] = k;
+                if (!gen_out(out, k) && live(net.gbus[k])) gidx[m++] = k;
             sh.m = m;
             sh.nn = 5 * m - 1;           // angles referred to the first in-service machine
             sh.fail = 0;
@@ -489,6 +493,10 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
         for (int tg = tid; tg < nb + net.nL; tg += kThreads) {
             if (tg < nb) {
                 const int j = tg, i = net.perm[j];
+                if (!live(i)) {                       // de-energised bus: identity row
+                    st(W + L.Yd + 2 * j, cm(1.0, 0.0));
+                    continue;
+                }
                 const double Vm = xs[nb + i];
                 cplx y = cm(net.gsh[i], net.bsh[i]);
                 y = y + (1.0 / (Vm * Vm)) * cm(Pd[i], -Qd[i]);
@@ -510,7 +518,7 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
                 cplx y = cm(0.0, 0.0);
                 for (int e = net.blk_br_ptr[q]; e < net.blk_br_ptr[q + 1]; ++e) {
                     const int b = net.blk_br[e];
-                    if (br_out(out, b)) continue;
+                    if (br_out(out, b) || !live(net.f[b])) continue;
                     y = y + ((net.f[b] == Rb) ? net.yft[b] : net.ytf[b]);
                 }
                 st(W + L.Yu + 2 * q, y);
@@ -675,8 +683,12 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
         const double nan = __longlong_as_double(0x7ff8000000000000ll);
         if (sh.fail) {                                // Y_bb singular: no model at this point
             if (tid == 0) {
-                a.out.klass[s] = CS_EIG_FAIL;
-                a.out.severe[s] = 1;
+                if (isl) {                            // the main island's class; the scenario's stays ISLANDED
+                    if (a.out.main_klass) a.out.main_klass[s] = CS_EIG_FAIL;
+                } else {
+                    a.out.klass[s] = CS_EIG_FAIL;
+                    a.out.severe[s] = 1;
+                }
                 a.out.max_re[s] = nan;
                 a.out.min_zeta[s] = nan;
                 if (kMode == DYN_FRONT) o.status[s] = 7;
@@ -727,8 +739,12 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
                 else if (maxre >= 0.0) k = CS_SS_UNSTABLE;
                 else if (minz < damping_min) k = CS_SS_POORLY_DAMPED;
                 else k = CS_SECURE;
-                a.out.klass[s] = k;
-                a.out.severe[s] = (k != CS_SECURE);
+                if (isl) {
+                    if (a.out.main_klass) a.out.main_klass[s] = k;
+                } else {
+                    a.out.klass[s] = k;
+                    a.out.severe[s] = (k != CS_SECURE);
+                }
                 a.out.max_re[s] = sh.fail ? nan : maxre;
                 a.out.min_zeta[s] = sh.fail ? nan : minz;
             }
@@ -1131,8 +1147,12 @@ hqr_smem_kernel(EvalArgs a, OpfOut o, const float* __restrict__ hbuf, size_t hst
                 if (maxre >= 0.0f) k = CS_SS_UNSTABLE;
                 else if (minz < damping_min) k = CS_SS_POORLY_DAMPED;
                 else k = CS_SECURE;
-                a.out.klass[s] = k;
-                a.out.severe[s] = (k != CS_SECURE);
+                if (a.out.n_islands[s] > 1) {              // main island: the scenario's class stays ISLANDED
+                    if (a.out.main_klass) a.out.main_klass[s] = k;
+                } else {
+                    a.out.klass[s] = k;
+                    a.out.severe[s] = (k != CS_SECURE);
+                }
                 a.out.max_re[s] = maxre;
                 a.out.min_zeta[s] = minz;
             }

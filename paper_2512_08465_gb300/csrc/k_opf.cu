@@ -1364,11 +1364,13 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
         }
         double* xs = o.x + (size_t)s * nx;
         for (int i = tid; i < nb; i += kThreads) {
-            const bool on = lv.bus(i);         // a bus outside the main island is de-energised
-            xs[i] = W[L.Va + i];
-            xs[nb + i] = W[L.Vm + i];
-            if (a.out.Va) a.out.Va[(size_t)s * nb + i] = on ? W[L.Va + i] : 0.0;
-            if (a.out.Vm) a.out.Vm[(size_t)s * nb + i] = on ? W[L.Vm + i] : 0.0;
+            // a bus outside the main island is de-energised: Vm = 0 also tells the
+            // small-signal kernels which buses are out
+            const bool on = lv.bus(i);
+            xs[i] = on ? W[L.Va + i] : 0.0;
+            xs[nb + i] = on ? W[L.Vm + i] : 0.0;
+            if (a.out.Va) a.out.Va[(size_t)s * nb + i] = xs[i];
+            if (a.out.Vm) a.out.Vm[(size_t)s * nb + i] = xs[nb + i];
         }
         for (int k = tid; k < ng; k += kThreads) {
             xs[2 * nb + k] = W[L.Pg + k];
@@ -1381,10 +1383,10 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
             if (a.out.max_loading) a.out.max_loading[s] = converged ? sc.red[1] : nan;
             if (a.out.v_margin) a.out.v_margin[s] = converged ? sc.red[2] : nan;
             if (isl) {                         // main island of an islanded scenario: class unchanged
-                o.status[s] = 3;
+                const bool ok = converged && sc.red[0] == 0.0;
+                o.status[s] = ok ? 1 : 3;      // within limits: on to the small-signal screen, which sets main_klass
                 if (a.out.shed_mw) a.out.shed_mw[s] = B * sc.shed;
-                if (a.out.main_klass)
-                    a.out.main_klass[s] = !converged ? CS_OPF_NONCONV : (sc.red[0] != 0.0 ? CS_LIMIT : CS_SECURE);
+                if (a.out.main_klass && !ok) a.out.main_klass[s] = converged ? CS_LIMIT : CS_OPF_NONCONV;
             } else if (!converged || sc.red[0] != 0.0) {
                 o.status[s] = 2;
                 a.out.klass[s] = converged ? CS_LIMIT : CS_OPF_NONCONV;
