@@ -12,13 +12,12 @@ in the guard band of the parity suite (an oracle OPF that needed >= 48 of its 50
 iterations, or a decisive eigen statistic within 1e-6 of its threshold).
 Scenarios that do not split are unchanged by the form.
 """
-import copy
-
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import twonets  # noqa: E402
 from paper_2512_08465_gb300 import cs, synth  # noqa: E402
 from oracle import grid, island  # noqa: E402
 
@@ -138,26 +137,6 @@ def test_main_island_118bus_matches_oracle(net118):
     ref_ctx.close()
 
 
-def _join(A, Bn, a_bus, b_bus, ref):
-    nA = A.n_bus
-    J = copy.copy(A)
-    for k in ("Vmin", "Vmax", "Gs", "Bs", "Pd_shape", "Qd_shape"):
-        setattr(J, k, np.concatenate([getattr(A, k), getattr(Bn, k)]))
-    J.Pd = np.concatenate([A.Pd, Bn.Pd], axis=1)
-    J.Qd = np.concatenate([A.Qd, Bn.Qd], axis=1)
-    J.f = np.concatenate([A.f, Bn.f + nA, [a_bus]]).astype(np.int32)
-    J.t = np.concatenate([A.t, Bn.t + nA, [nA + b_bus]]).astype(np.int32)
-    tie = dict(r=0.01, x=0.05, b=0.0, rate=300.0, tap=1.0, kind=synth.KIND_LINE)
-    for k, v in tie.items():
-        J.__dict__[k] = np.concatenate([getattr(A, k), getattr(Bn, k), [v]]).astype(getattr(A, k).dtype)
-    J.gbus = np.concatenate([A.gbus, Bn.gbus + nA]).astype(np.int32)
-    for k in ("Pmin", "Pmax", "Qmin", "Qmax", "c2", "c1", "c0", "H", "D",
-              "xd", "xq", "xdp", "Td0p", "Tq0p", "KA", "TA"):
-        setattr(J, k, np.concatenate([getattr(A, k), getattr(Bn, k)]))
-    J.ref_bus = int(ref)
-    return J
-
-
 def test_tie_line_split_moves_the_reference_and_no_generation_case():
     """Two networks joined by one tie with the reference on the smaller side: with the
     tie out the larger side is the main island and the reference moves to its largest
@@ -165,9 +144,8 @@ def test_tie_line_split_moves_the_reference_and_no_generation_case():
     island: main_klass OPF_NONCONV, the whole load shed, Vm = Va = 0."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    A = synth.make_network(14, 20, 5, 11, 1, seed=3, levels=(0.5,))
-    Bn = synth.make_network(9, 12, 3, 6, 0, seed=5, levels=(0.5,))
-    J = _join(A, Bn, 2, 4, ref=A.n_bus + Bn.ref_bus)
+    A, Bn = twonets.pair()
+    J = twonets.join(A, Bn, 2, 4, ref=A.n_bus + Bn.ref_bus)
     tie = J.n_branch - 1
     scen = [(tie, -1), (tie, 0), (tie, J.n_branch + 1)]       # tie alone, with a branch, with a unit
     ctx = cs.Context(main_island=1)

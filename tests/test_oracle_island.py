@@ -10,37 +10,10 @@ constant and nothing else changes.
 import copy
 
 import numpy as np
-import pytest
 
+import twonets
 from paper_2512_08465_gb300 import synth
 from oracle import grid, island, opf, pipeline
-
-
-def _join(A, Bn, a_bus, b_bus, ref):
-    """A and B side by side (B's buses after A's), plus one tie branch a_bus - (nA + b_bus)."""
-    nA = A.n_bus
-    J = copy.copy(A)
-    for k in ("Vmin", "Vmax", "Gs", "Bs", "Pd_shape", "Qd_shape"):
-        setattr(J, k, np.concatenate([getattr(A, k), getattr(Bn, k)]))
-    J.Pd = np.concatenate([A.Pd, Bn.Pd], axis=1)
-    J.Qd = np.concatenate([A.Qd, Bn.Qd], axis=1)
-    J.f = np.concatenate([A.f, Bn.f + nA, [a_bus]]).astype(np.int32)
-    J.t = np.concatenate([A.t, Bn.t + nA, [nA + b_bus]]).astype(np.int32)
-    tie = dict(r=0.01, x=0.05, b=0.0, rate=300.0, tap=1.0, kind=synth.KIND_LINE)
-    for k, v in tie.items():
-        J.__dict__[k] = np.concatenate([getattr(A, k), getattr(Bn, k), [v]]).astype(getattr(A, k).dtype)
-    J.gbus = np.concatenate([A.gbus, Bn.gbus + nA]).astype(np.int32)
-    for k in ("Pmin", "Pmax", "Qmin", "Qmax", "c2", "c1", "c0", "H", "D",
-              "xd", "xq", "xdp", "Td0p", "Tq0p", "KA", "TA"):
-        setattr(J, k, np.concatenate([getattr(A, k), getattr(Bn, k)]))
-    J.ref_bus = int(ref)
-    return J
-
-
-def _nets():
-    A = synth.make_network(14, 20, 5, 11, 1, seed=3, levels=(0.5,))
-    Bn = synth.make_network(9, 12, 3, 6, 0, seed=5, levels=(0.5,))
-    return A, Bn
 
 
 def _standalone(net):
@@ -79,9 +52,9 @@ def test_labels_are_components_in_lowest_bus_order():
 
 
 def test_tie_out_larger_generation_is_main_and_slack_moves():
-    A, Bn = _nets()
+    A, Bn = twonets.pair()
     assert A.Pmax.sum() > Bn.Pmax.sum()
-    J = _join(A, Bn, 2, 4, ref=A.n_bus + Bn.ref_bus)          # reference inside B
+    J = twonets.join(A, Bn, 2, 4, ref=A.n_bus + Bn.ref_bus)          # reference inside B
     tie = J.n_branch - 1
     r = island.evaluate_main_island(J, 0, tie)
     nA = A.n_bus
@@ -94,20 +67,20 @@ def test_tie_out_larger_generation_is_main_and_slack_moves():
 
 
 def test_reference_kept_when_inside_main_island():
-    A, Bn = _nets()
-    J = _join(A, Bn, 2, 4, ref=A.ref_bus)
+    A, Bn = twonets.pair()
+    J = twonets.join(A, Bn, 2, 4, ref=A.ref_bus)
     r = island.evaluate_main_island(J, 0, J.n_branch - 1)
     assert r["ref"] == A.ref_bus
     _check_equal_opf(r, A, slice(0, A.n_bus), same_ref=True)
 
 
 def test_swapping_generation_swaps_the_main_island():
-    A, Bn = _nets()
+    A, Bn = twonets.pair()
     Bn = copy.copy(Bn)
     for k in ("Pmax", "Qmax", "Qmin"):
         setattr(Bn, k, 10.0 * getattr(Bn, k))
     assert Bn.Pmax.sum() > A.Pmax.sum()
-    J = _join(A, Bn, 2, 4, ref=A.ref_bus)
+    J = twonets.join(A, Bn, 2, 4, ref=A.ref_bus)
     r = island.evaluate_main_island(J, 0, J.n_branch - 1)
     nA = A.n_bus
     assert r["live"][nA:].all() and not r["live"][:nA].any()
@@ -117,14 +90,14 @@ def test_swapping_generation_swaps_the_main_island():
 
 
 def test_equal_generation_picks_the_island_of_bus_zero():
-    A, _ = _nets()
-    J = _join(A, A, 1, 1, ref=A.n_bus + A.ref_bus)
+    A, _ = twonets.pair()
+    J = twonets.join(A, A, 1, 1, ref=A.n_bus + A.ref_bus)
     r = island.evaluate_main_island(J, 0, J.n_branch - 1)
     assert r["live"][:A.n_bus].all() and not r["live"][A.n_bus:].any()
 
 
 def test_connected_scenario_is_not_islanded():
-    A, _ = _nets()
+    A, _ = twonets.pair()
     r = island.evaluate_main_island(A, 0)
     assert r["main_klass"] == island.NOT_ISLANDED and r["shed_mw"] == 0.0 and r["opf_iters"] == 0
 
