@@ -9,7 +9,7 @@
 
 namespace {
 
-constexpr int kWarpsPerBlock = 8;
+constexpr int kWarpsPerBlock = 8;   // per CTA, fewer when n_bus ints per warp exceed the shared memory
 
 __device__ int uf_find(int* p, int u) {
     while (p[u] != u) {
@@ -21,10 +21,11 @@ __device__ int uf_find(int* p, int u) {
 
 __global__ void islands_kernel(DevNet net, EvalArgs a, int* islanded) {
     extern __shared__ int sh_parent[];
+    const int wpb = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int* parent = sh_parent + warp * net.nb;
-    const int nwarps_total = gridDim.x * kWarpsPerBlock;
-    for (int s = blockIdx.x * kWarpsPerBlock + warp; s < a.n; s += nwarps_total) {
+    const int nwarps_total = gridDim.x * wpb;
+    for (int s = blockIdx.x * wpb + warp; s < a.n; s += nwarps_total) {
         const int ei = a.ei[s], ej = a.ej[s], ek = a.ek ? a.ek[s] : -1;
         const bool bad = ei < -1 || ej < -1 || ek < -1 || ei >= net.nE || ej >= net.nE || ek >= net.nE ||
                          (ei < 0 && ej >= 0) || (ej < 0 && ek >= 0);
@@ -109,10 +110,24 @@ __global__ void enumerate_kernel(int E, long long first, long long count, int* e
 
 cudaError_t launch_islands(const DevNet& net, const EvalArgs& a, int* islanded, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    const size_t smem = sizeof(int) * (size_t)net.nb * kWarpsPerBlock;
-    int blocks = (a.n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    // one parent array of n_bus ints per warp; above the default 48 KB the kernel opts in
+    // to the device's per-CTA maximum, and fewer warps share a CTA if even that is short
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const size_t per_warp = sizeof(int) * (size_t)net.nb;
+    int wpb = kWarpsPerBlock;
+    while (wpb > 1 && per_warp * wpb > (size_t)optin) --wpb;
+    const size_t smem = per_warp * wpb;
+    if (smem > (size_t)optin) return cudaErrorInvalidValue;     // one bus array alone does not fit
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(islands_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int blocks = (a.n + wpb - 1) / wpb;
     if (blocks > 4096) blocks = 4096;
-    islands_kernel<<<blocks, 32 * kWarpsPerBlock, smem, s>>>(net, a, islanded);
+    islands_kernel<<<blocks, 32 * wpb, smem, s>>>(net, a, islanded);
     return cudaGetLastError();
 }
 
