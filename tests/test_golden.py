@@ -1,0 +1,35 @@
+"""The stored expected values (tests/golden/*.json, written by make_golden.py from the
+oracle alone) are still what the current oracle computes: a seeded sample of their
+scenarios is re-evaluated here.  Classes and integers exactly; cost, max Re and min
+damping ratio to 1e-9 relative (BLAS builds may round differently)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2512_08465_gb300 import synth
+from oracle import pipeline
+
+HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.mark.parametrize("name,count", [("case118_n1.json", 5), ("case118_pairs.json", 4)])
+def test_golden_sample_reproduces_from_the_oracle(name, count):
+    gold = json.load(open(os.path.join(HERE, name)))
+    assert gold["meta"]["network"] == "synth118" and gold["meta"]["damping_min"] == pipeline.DAMPING_MIN
+    net = synth.case118()
+    rows = gold["scenarios"]
+    pick = np.random.default_rng(7).choice(len(rows), count, replace=False)
+    for q in pick:
+        g = rows[int(q)]
+        r = pipeline.evaluate(net, g["level"], g["i"], g["j"])
+        for k in ("klass", "severe", "n_islands", "opf_iters"):
+            assert int(r[k]) == g[k], (name, q, k)
+        for k in ("cost", "max_re", "min_zeta"):
+            if g[k] is None:
+                assert not np.isfinite(r[k]), (name, q, k)
+            else:
+                assert abs(r[k] - g[k]) <= 1e-9 * max(1.0, abs(g[k])), (name, q, k, r[k], g[k])
+        if "Vm" in g:
+            assert np.abs(np.asarray(r["Vm"]) - g["Vm"]).max() <= 1e-9
