@@ -110,3 +110,43 @@ def test_no_generation_anywhere_means_no_main_island():
     r = island.evaluate_main_island(net, 0, bridges[0], net.n_branch)    # the only generator out too
     assert r["live"] is None and r["main_klass"] == island.OPF_NONCONV
     assert abs(r["shed_mw"] - net.Pd[0].sum()) <= 1e-9 * net.Pd[0].sum()
+
+
+def test_generator_outage_moves_the_main_island():
+    """Same split, different generation: with the tie and A's largest unit out, B (now the
+    larger total Pmax) is the main island although A has more buses."""
+    A, Bn = twonets.pair()
+    Bn = copy.copy(Bn)
+    kA = int(np.argmax(A.Pmax))
+    gap = A.Pmax.sum() - A.Pmax[kA]                       # A's capacity without its largest unit
+    scale = 1.0 + (gap - Bn.Pmax.sum()) / Bn.Pmax.sum() + 0.2
+    for k in ("Pmax", "Qmax", "Qmin"):
+        setattr(Bn, k, scale * getattr(Bn, k))
+    assert A.Pmax.sum() > Bn.Pmax.sum() > gap and A.n_bus > Bn.n_bus
+    J = twonets.join(A, Bn, 2, 4, ref=A.ref_bus)
+    tie = J.n_branch - 1
+    assert island.evaluate_main_island(J, 0, tie)["live"][:A.n_bus].all()
+    r = island.evaluate_main_island(J, 0, tie, J.n_branch + kA)
+    assert r["live"][A.n_bus:].all() and not r["live"][:A.n_bus].any()
+    assert r["ref"] == A.n_bus + int(Bn.gbus[np.argmax(Bn.Pmax)])
+    assert abs(r["shed_mw"] - A.Pd[0].sum()) <= 1e-9 * A.Pd[0].sum()
+
+
+def test_three_way_split_picks_the_largest_generation():
+    """A - B - C chained by two ties; both ties out gives three islands, and the main one
+    is the island with the largest total Pmax wherever it sits in the bus order."""
+    A, Bn = twonets.pair()
+    C = synth.make_network(9, 12, 3, 6, 0, seed=11, levels=(0.5,))
+    C = copy.copy(C)
+    for k in ("Pmax", "Qmax", "Qmin"):
+        setattr(C, k, 3.0 * getattr(C, k))
+    AB = twonets.join(A, Bn, 2, 4, ref=A.ref_bus)
+    J = twonets.join(AB, C, A.n_bus + 1, 3, ref=A.ref_bus)   # second tie: a bus of B to a bus of C
+    caps = [A.Pmax.sum(), Bn.Pmax.sum(), C.Pmax.sum()]
+    assert int(np.argmax(caps)) == 2
+    t1, t2 = AB.n_branch - 1, J.n_branch - 1
+    r = island.evaluate_main_island(J, 0, t1, t2)
+    assert grid.count_islands(J.n_bus, np.delete(J.f, [t1, t2]), np.delete(J.t, [t1, t2])) == 3
+    nAB = AB.n_bus
+    assert r["live"][nAB:].all() and not r["live"][:nAB].any()
+    assert abs(r["shed_mw"] - (A.Pd[0].sum() + Bn.Pd[0].sum())) <= 1e-9 * (A.Pd[0].sum() + Bn.Pd[0].sum())
