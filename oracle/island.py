@@ -30,10 +30,13 @@ Readings (the paper gives the idea, not the rules):
     the main island are reported as 0 (de-energised).
 
 Pins (``tests/test_oracle_island.py``): two networks built apart and joined by
-one tie branch; with the tie out, the main island's OPF equals the standalone
-OPF of the network with the larger generation (cost, magnitudes, angles up to
-the reference shift), the shed is the other network's load, and swapping the
-generation swaps the choice; equal generation picks the island of bus 0.
+one tie branch; with the tie out, the main island's OPF and small-signal screen
+equal the standalone ones of the network with the larger generation (cost,
+magnitudes, angles up to the reference shift, class, max Re, min damping ratio),
+the shed is the other network's load, and swapping the generation swaps the
+choice; a generator outage that reverses the capacities moves the main island to
+the side with fewer buses; of three islands the one with the largest capacity
+wins; equal generation picks the island of bus 0.
 """
 from __future__ import annotations
 
