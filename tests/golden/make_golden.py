@@ -27,12 +27,15 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 KEYS = ("level", "i", "j", "klass", "severe", "n_islands", "opf_iters", "converged", "cost", "max_re", "min_zeta")
 
 
+# the oracle modules the stored values come from, and the input generator
+SOURCES = ("oracle/grid.py", "oracle/opf.py", "oracle/dynamics.py", "oracle/eig.py", "oracle/eig.c",
+           "oracle/pipeline.py", "paper_2512_08465_gb300/synth.py")
+
+
 def oracle_hash():
     h = hashlib.sha256()
-    for fn in sorted(os.listdir(os.path.join(ROOT, "oracle"))):
-        if fn.endswith((".py", ".c")):
-            h.update(open(os.path.join(ROOT, "oracle", fn), "rb").read())
-    h.update(open(os.path.join(ROOT, "paper_2512_08465_gb300", "synth.py"), "rb").read())
+    for rel in SOURCES:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
     return h.hexdigest()[:16]
 
 

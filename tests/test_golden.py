@@ -2,6 +2,7 @@
 oracle alone) are still what the current oracle computes: a seeded sample of their
 scenarios is re-evaluated here.  Classes and integers exactly; cost, max Re and min
 damping ratio to 1e-9 relative (BLAS builds may round differently)."""
+import importlib.util
 import json
 import os
 
@@ -12,6 +13,21 @@ from paper_2512_08465_gb300 import synth
 from oracle import pipeline
 
 HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _make_golden():
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(HERE, "make_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_golden_files_come_from_the_current_oracle_sources():
+    """The stored hash is that of the oracle modules (and input generator) the values
+    come from: a change to any of them must be followed by make_golden.py."""
+    h = _make_golden().oracle_hash()
+    for name in ("case118_n1.json", "case118_pairs.json"):
+        assert json.load(open(os.path.join(HERE, name)))["meta"]["oracle"] == h, name
 
 
 @pytest.mark.parametrize("name,count", [("case118_n1.json", 5), ("case118_pairs.json", 4)])
