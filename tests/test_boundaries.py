@@ -44,3 +44,14 @@ def _oracle_import_scopes(path):
 def test_oracle_imported_only_where_allowed():
     assert set(_oracle_import_scopes(os.path.join(ROOT, "bench.py"))) <= {"cpu_baseline", "run_reference"}
     assert set(_oracle_import_scopes(os.path.join(ROOT, "__graft_entry__.py"))) <= {"build", "smoke"}
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libcs the binding raises; there is no CPU fallback to return results."""
+    import pytest
+    from paper_2512_08465_gb300 import build as libbuild
+    from paper_2512_08465_gb300 import cs
+    monkeypatch.setattr(cs, "_LIB", None)
+    monkeypatch.setattr(libbuild, "LIB", str(tmp_path / "libcs.so"))
+    with pytest.raises(RuntimeError, match="libcs not found"):
+        cs.load_library(build_if_missing=False)
