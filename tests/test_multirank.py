@@ -82,3 +82,39 @@ def test_two_ranks_merge_equals_single_rank():
     lam = synth.failure_rates(E, 3)
     for mode in (risk.EQ3, risk.ORDERED):
         np.testing.assert_array_equal(risk.risk_index(lam, S1, S2, mode), risk.risk_index(lam, S1, S2s, mode))
+
+
+def _dead_peer_worker(rank, world, port, outq):
+    import datetime
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), OPENBLAS_NUM_THREADS="1")
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        os._exit(0)                                     # leaves between steps, never joins the merge
+    try:
+        shard.merge_severity(np.zeros(16, np.uint8))
+        outq.put("merged")
+    except Exception as e:                              # the collective ends with an error, not a hang
+        outq.put("error " + type(e).__name__)
+    outq.close()
+    outq.join_thread()
+    os._exit(0)
+
+
+def test_a_rank_that_leaves_ends_the_merge_with_an_error():
+    """Failure detection of the sharded form on the host: when a rank exits before the
+    severity merge, the surviving rank's collective fails within the process-group
+    timeout instead of waiting forever."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dead_peer_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        msg = q.get(timeout=120)
+    finally:
+        for p in procs:
+            p.join(timeout=30)
+            if p.is_alive():
+                p.kill()
+    assert msg.startswith("error"), msg
