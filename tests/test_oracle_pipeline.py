@@ -61,3 +61,42 @@ def test_n3_scenarios_reduce_to_n2_and_are_order_free():
         assert r["klass"] == r0["klass"] and r["opf_iters"] == r0["opf_iters"]
         if r0["converged"]:
             assert r["cost"] == r0["cost"]
+
+
+def test_classification_truth_table(monkeypatch):
+    """Section II-B: a scenario is severe when at least one criterion fails, and the
+    class is the first failing criterion in the order islanding, OPF convergence,
+    operational limits, eigenvalue iteration, Re >= 0, damping below the threshold.
+    Every combination of outcomes is forced by stubbing the criteria themselves."""
+    import itertools
+    from oracle import dynamics, eig, opf
+    net = synth.make_network(9, 12, 3, 6, 0, seed=5, levels=(0.5,))
+    order = ("island", "nonconv", "limit", "eigfail", "unstable", "damped")
+    klass = {"island": pipeline.ISLANDED, "nonconv": pipeline.OPF_NONCONV, "limit": pipeline.LIMIT,
+             "eigfail": pipeline.EIG_FAIL, "unstable": pipeline.SS_UNSTABLE, "damped": pipeline.SS_POORLY_DAMPED}
+    nb = net.n_bus
+    for bits in itertools.product((False, True), repeat=len(order)):
+        fail = dict(zip(order, bits))
+        monkeypatch.setattr(grid, "count_islands", lambda n, f, t, v=fail["island"]: 2 if v else 1)
+        monkeypatch.setattr(opf, "solve", lambda net_, sc, v=fail["nonconv"]: dict(
+            converged=not v, iterations=7, cost=1.0, Va=np.zeros(nb), Vm=np.ones(nb),
+            Pg=np.zeros(3), Qg=np.zeros(3), conds=(0, 0, 0, 0)))
+        monkeypatch.setattr(opf, "severity_indices", lambda r: (0.01, 0.5))
+        monkeypatch.setattr(opf, "limit_violation", lambda r, v=fail["limit"]: v)
+
+        class _M:
+            def __init__(self, *a):
+                pass
+
+            def reduced_state_matrix(self):
+                return np.zeros((2, 2))
+        monkeypatch.setattr(dynamics, "Model", _M)
+        re = 0.1 if fail["unstable"] else -0.5
+        zeta = 0.01 if fail["damped"] else 0.3
+        lam = np.array([complex(re, 1.0), complex(-zeta, np.sqrt(1 - zeta * zeta))])
+        monkeypatch.setattr(eig, "eigvals", lambda A, v=fail["eigfail"], lam=lam: (lam, not v, 3))
+        r = pipeline.evaluate(net, 0, 1, 2)
+        first = next((k for k in order if fail[k]), None)
+        want = pipeline.SECURE if first is None else klass[first]
+        assert r["klass"] == want, (fail, r["klass"])
+        assert r["severe"] == int(any(bits)), fail
