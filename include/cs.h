@@ -171,6 +171,30 @@ cs_status cs_unload_network(cs_ctx* ctx, int32_t net_id);
  * entries are written (HOST array). */
 cs_status cs_network_stats(cs_ctx* ctx, int32_t net_id, int64_t* stats, int32_t n_stats);
 
+/* The symbolic analysis a loaded network gets (cs_load_network), on its own:
+ * HOST only, no context and no device.  Every scenario's Newton system (4x4
+ * blocks per bus, Section II-B-1) and the small-signal model's network matrix
+ * (Section II-B-2) have the bus graph with every branch in service as block
+ * pattern, an outage only zeroing values, so one ordering and one fill pattern
+ * serve all contingencies.  The paper has no counterpart (it calls external
+ * solvers); this entry point exposes the analysis for inspection and testing.
+ *   n_bus, n_branch, f[k], t[k]: the bus graph (HOST arrays; parallel branches
+ *     allowed, self loops rejected); ref_bus: eliminated last (-1: none);
+ *   perm[n_bus]: elimination order, perm[new] = old bus (exact minimum degree on
+ *     the elimination graph, ties to the smaller bus index);
+ *   col_ptr[n_bus + 1], row[cap]: rows (new indices, ascending, all below the
+ *     diagonal) of each column's off-diagonal blocks of L, CSC;
+ *   level[n_bus]: elimination-tree height of each column (new index); the
+ *     columns of one height are independent and form one parallel step;
+ *   stats[0..3]: off-diagonal blocks of L, levels, block updates of one numeric
+ *     factorisation, the capacity row needs.
+ * Every output pointer may be NULL (skipped).  CS_E_ARG: sizes or ends out of
+ * range, a self loop, a NULL edge array, or cap below stats[3] (the other
+ * outputs are then written). */
+cs_status cs_symbolic_pattern(int32_t n_bus, int32_t n_branch, const int32_t* f, const int32_t* t,
+                              int32_t ref_bus, int32_t* perm, int32_t* col_ptr, int32_t* row, int64_t cap,
+                              int32_t* level, int64_t* stats);
+
 /* Base-case result of a level (host out, one record). */
 cs_status cs_base_result(cs_ctx* ctx, int32_t net_id, int32_t level, const cs_result* out);
 

@@ -32,7 +32,8 @@ EXPORTS = ("cs_default_options", "cs_create", "cs_destroy", "cs_load_network", "
            "cs_risk_index", "cs_risk_reduce_device", "cs_enumerate_pairs_device", "cs_last_error",
            "cs_last_launch_count", "cs_set_timing", "cs_kernel_times", "cs_alu_peak", "cs_eigen_reruns",
            "cs_risk_index_static", "cs_network_stats", "cs_serving_stats", "cs_risk_index_batch",
-           "cs_evaluate_device_n3", "cs_enumerate_triples_device", "cs_risk_index_pair_freq")
+           "cs_evaluate_device_n3", "cs_enumerate_triples_device", "cs_risk_index_pair_freq",
+           "cs_symbolic_pattern")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -106,6 +107,7 @@ def load_library(build_if_missing: bool = True):
         "cs_risk_index": (i32, [P, i32, i32, P, i32, P, ctypes.POINTER(i64)]),
         "cs_risk_index_static": (i32, [P, i32, i32, P, i32, P, ctypes.POINTER(i64)]),
         "cs_network_stats": (i32, [P, i32, P, i32]),
+        "cs_symbolic_pattern": (i32, [i32, i32, P, P, i32, P, P, P, i64, P, P]),
         "cs_serving_stats": (i32, [P, P, i32]),
         "cs_risk_index_batch": (i32, [P, i32, i32, P, i64, i32, P, P]),
         "cs_evaluate_device_n3": (i32, [P, i32, i32, P, P, P, i64, ctypes.POINTER(Result), P]),
@@ -408,3 +410,28 @@ def enumerate_pairs_device(n_elem: int, first: int, count: int, ei, ej, stream=N
                                                   _stream_handle(stream))
     if st != CS_OK:
         raise CSError(st, "cs_enumerate_pairs_device")
+
+
+def symbolic_pattern(n_bus: int, f, t, ref_bus: int = -1) -> dict:
+    """cs_symbolic_pattern on host arrays (no device): the elimination order
+    (perm[new] = old bus), the CSC pattern of L's off-diagonal blocks (col_ptr, row),
+    the elimination-tree height of each column (level) and the counts (blocks,
+    levels, block updates)."""
+    lib = load_library()
+    f = np.ascontiguousarray(f, dtype=np.int32)
+    t = np.ascontiguousarray(t, dtype=np.int32)
+    stats = np.zeros(4, np.int64)
+    st = lib.cs_symbolic_pattern(int(n_bus), int(f.size), _ptr(f), _ptr(t), int(ref_bus),
+                                 None, None, None, 0, None, _ptr(stats))
+    if st != CS_OK:
+        raise CSError(st, "cs_symbolic_pattern")
+    perm = np.zeros(n_bus, np.int32)
+    col_ptr = np.zeros(n_bus + 1, np.int32)
+    row = np.zeros(max(1, int(stats[3])), np.int32)
+    level = np.zeros(n_bus, np.int32)
+    st = lib.cs_symbolic_pattern(int(n_bus), int(f.size), _ptr(f), _ptr(t), int(ref_bus),
+                                 _ptr(perm), _ptr(col_ptr), _ptr(row), int(row.size), _ptr(level), _ptr(stats))
+    if st != CS_OK:
+        raise CSError(st, "cs_symbolic_pattern")
+    return dict(perm=perm, col_ptr=col_ptr, row=row[:int(stats[3])], level=level,
+                blocks=int(stats[0]), levels=int(stats[1]), updates=int(stats[2]))

@@ -527,6 +527,34 @@ cs_status cs_network_stats(cs_ctx* ctx, int32_t net_id, int64_t* stats, int32_t 
     return CS_OK;
 }
 
+cs_status cs_symbolic_pattern(int32_t n_bus, int32_t n_branch, const int32_t* f, const int32_t* t,
+                              int32_t ref_bus, int32_t* perm, int32_t* col_ptr, int32_t* row, int64_t cap,
+                              int32_t* level, int64_t* stats) {
+    if (n_bus <= 0 || n_branch < 0 || (n_branch > 0 && (!f || !t)) || ref_bus < -1 || ref_bus >= n_bus)
+        return CS_E_ARG;
+    std::vector<int> F(f, f + n_branch), T(t, t + n_branch);
+    Symbolic S;
+    if (!symbolic_analysis(n_bus, F, T, ref_bus, S).empty()) return CS_E_ARG;
+    const int64_t nL = S.Lcolptr[n_bus];
+    std::vector<int> height(n_bus, 0);
+    for (int h = 0; h < S.nlevels; ++h)
+        for (int w = S.lev_ptr[h]; w < S.lev_ptr[h + 1]; ++w) height[S.lev_col[w]] = h;
+    if (stats) {
+        stats[0] = nL;
+        stats[1] = S.nlevels;
+        stats[2] = S.block_updates;
+        stats[3] = nL;
+    }
+    if (perm) std::copy(S.perm.begin(), S.perm.end(), perm);
+    if (col_ptr) std::copy(S.Lcolptr.begin(), S.Lcolptr.end(), col_ptr);
+    if (level) std::copy(height.begin(), height.end(), level);
+    if (row) {
+        if (cap < nL) return CS_E_ARG;
+        std::copy(S.Lrow.begin(), S.Lrow.end(), row);
+    }
+    return CS_OK;
+}
+
 cs_status cs_base_result(cs_ctx* ctx, int32_t net_id, int32_t level, const cs_result* out) {
     if (!ctx) return CS_E_ARG;
     std::lock_guard<std::mutex> lock(ctx->mu);
