@@ -35,6 +35,10 @@ constant complex matrix W; ``quad_hessian`` gives its exact Hessian with respect
 to (Va, Vm).  Pinned in ``tests/test_oracle_opf.py`` against central finite
 differences, the two-bus power-flow closed form, the two-generator lossless
 economic dispatch closed form and the KKT residuals at every converged point.
+``conditions`` is pinned against values worked by hand from the MIPS
+definitions, and the stopping rule against the iteration trace;
+``limit_violation`` against limits moved across a converged two-bus point whose
+flow is computed from its voltages alone (violated beyond 1e-6 p.u., not within).
 """
 from __future__ import annotations
 

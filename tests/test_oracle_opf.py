@@ -158,3 +158,92 @@ def test_severity_indices_at_binding_limits():
     assert r["converged"]
     margin, loading = opf.severity_indices(r)
     assert abs(r["Vm"][0] - net.Vmax[0]) <= 1e-6 and abs(margin) <= 1e-6 and loading < 1.0
+
+
+def test_conditions_hand_computed():
+    """The four MIPS stopping quantities (Wang et al. 2007, Section III; the reading
+    of the OPF of Section II-B-1) on numbers worked by hand:
+      feasibility  max(|g|_inf, max h) / (1 + max(|x|_inf, |z|_inf)) = max(0.3, 0.2) / 5 = 0.06
+      gradient     |Lx|_inf / (1 + max(|lam|_inf, |mu|_inf))          = 1.4 / 7           = 0.2
+      complement.  z.mu / (1 + |x|_inf)                               = (1 + 1) / 5       = 0.4
+      cost change  |f - f_prev| / (1 + |f_prev|)                      = 2 / 9
+    The second case has every h < 0 (feasibility from g alone) and a cost drop."""
+    x = np.array([3.0, -4.0])
+    z = np.array([0.5, 2.0])
+    g = np.array([0.1, -0.3])
+    h = np.array([-0.5, 0.2])
+    lam = np.array([1.0, -6.0])
+    mu = np.array([2.0, 0.5])
+    Lx = np.array([0.7, -1.4])
+    feas, grad, comp, cost = opf.conditions(None, x, z, lam, mu, 10.0, 8.0, g, h, Lx)
+    assert feas == pytest.approx(0.06, abs=1e-15)
+    assert grad == pytest.approx(0.2, abs=1e-15)
+    assert comp == pytest.approx(0.4, abs=1e-15)
+    assert cost == pytest.approx(2.0 / 9.0, abs=1e-15)
+    # all h negative: the largest |g| decides; |z| larger than |x|; cost falls from -4 to -7
+    x = np.array([0.5])
+    z = np.array([9.0, 1.0])
+    g = np.array([-0.02])
+    h = np.array([-3.0, -1.0])
+    lam = np.array([0.0])
+    mu = np.array([0.25, 0.75])
+    Lx = np.array([-2.0])
+    feas, grad, comp, cost = opf.conditions(None, x, z, lam, mu, -7.0, -4.0, g, h, Lx)
+    assert feas == pytest.approx(0.02 / 10.0, abs=1e-15)     # 1 + max(0.5, 9)
+    assert grad == pytest.approx(2.0 / 1.75, abs=1e-15)      # 1 + max(0, 0.75)
+    assert comp == pytest.approx(3.0 / 1.5, abs=1e-15)       # 9*0.25 + 1*0.75 = 3
+    assert cost == pytest.approx(3.0 / 5.0, abs=1e-15)
+
+
+def test_iteration_stops_at_first_point_meeting_all_four_conditions():
+    """The iteration count is the first iterate at which every condition is below
+    the tolerance: the trace's previous iterate still fails one of them."""
+    net = synth.case118()
+    r = opf.solve(net, grid.make_scenario(net, 0, 5), trace=True)
+    assert r["converged"] and r["iterations"] == len(r["hist"])
+    last = r["hist"][-1][4:]
+    prev = r["hist"][-2][4:]
+    assert all(c < opf.TOL for c in last)
+    assert any(c >= opf.TOL for c in prev)
+
+
+def _forced(res, **changes):
+    """A converged result with some limits of its problem moved (the point is
+    unchanged); h is re-evaluated for the moved limits."""
+    import copy
+    prob = copy.copy(res["prob"])
+    for k, v in changes.items():
+        setattr(prob, k, v)
+    x = np.concatenate([res["Va"], res["Vm"], res["Pg"], res["Qg"]])
+    out = dict(res)
+    out["prob"] = prob
+    out["h"] = prob.evaluate(x)[3]
+    return out
+
+
+def test_limit_violation_forced_by_cutting_limits_below_the_point():
+    """Section II-B-1: a converged point beyond an operational limit by more than
+    1e-6 p.u. is a violation.  The two-bus point's sending-end flow is computed
+    here from the voltages alone, |S_f| = |V_0 conj((V_0 - V_1)/(r + jx))|; a rating
+    cut 3e-6 p.u. below it is violated, 0.5e-6 below it is within tolerance, and the
+    same holds for Vmax, Pmax and Qmin moved across the point."""
+    r_, x_ = 0.02, 0.08
+    net = _two_bus(r_, x_, 400.0, 150.0, [(0, 2000.0, 0.01, 20.0)])
+    res = opf.solve(net, grid.make_scenario(net, 0))
+    assert res["converged"] and not opf.limit_violation(res)
+    V = res["Vm"] * np.exp(1j * res["Va"])
+    Sf = abs(V[0] * np.conj((V[0] - V[1]) / complex(r_, x_)))
+    St = abs(V[1] * np.conj((V[1] - V[0]) / complex(r_, x_)))
+    assert Sf > St                                    # the sending end carries the losses
+    assert not opf.limit_violation(_forced(res, Smax2=np.array([(Sf - 0.5e-6) ** 2])))
+    assert opf.limit_violation(_forced(res, Smax2=np.array([(Sf - 3e-6) ** 2])))
+    assert not opf.limit_violation(_forced(res, Smax2=np.array([(Sf * 10.0) ** 2])))
+    vmax = res["prob"].Vmax.copy()
+    vmax[1] = res["Vm"][1] - 3e-6
+    assert opf.limit_violation(_forced(res, Vmax=vmax))
+    vmax[1] = res["Vm"][1] - 0.5e-6
+    assert not opf.limit_violation(_forced(res, Vmax=vmax))
+    assert opf.limit_violation(_forced(res, Pmax=res["Pg"] - 3e-6))
+    assert not opf.limit_violation(_forced(res, Pmax=res["Pg"] - 0.5e-6))
+    assert opf.limit_violation(_forced(res, Qmin=res["Qg"] + 3e-6))
+    assert opf.limit_violation(_forced(res, Vmin=res["Vm"] + 3e-6))
