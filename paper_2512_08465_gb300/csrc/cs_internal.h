@@ -161,18 +161,22 @@ cudaError_t launch_opf(const DevNet& net, const EvalArgs& a, const int* islanded
                        int* counter, cudaStream_t s);
 size_t opf_scratch_doubles(const DevNet& net);
 int opf_ctas_per_sm();       // resident OPF CTAs per SM the kernel is built for
-// Small-signal screen.  counters: 4 work counters (zeroed by the caller).
-// abuf, hbuf (mixed form, NULL otherwise): a.n * dyn_abuf_stride(net) and
-// a.n * dyn_hbuf_stride(net) floats for the balanced matrices (front kernel ->
-// cluster Hessenberg kernel) and the packed Hessenberg matrices (-> shared-
-// memory QR); only usable when dyn_split_fits(net, device).  *launches:
-// kernels issued.
+// Small-signal screen.  counters: 5 work counters (zeroed by the caller).
+// abuf, hbuf, a64, cand (mixed form, NULL otherwise): a.n * dyn_abuf_stride(net)
+// and a.n * dyn_hbuf_stride(net) floats for the balanced matrices with their
+// balancing and Householder factors (front kernel -> cluster Hessenberg kernel ->
+// refinement) and the packed Hessenberg matrices (-> shared-memory QR), a.n *
+// dyn_a64_stride(net) doubles for the FP64 state matrices and a.n *
+// dyn_cand_stride() floats for the refinement candidates; only usable when
+// dyn_split_fits(net, device).  *launches: kernels issued.
 cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double damping_min, int precision,
-                       double* scratch, size_t scratch_per_cta, int grid, float* abuf, float* hbuf, int sms,
-                       int* counters, int* launches, cudaStream_t s);
+                       double* scratch, size_t scratch_per_cta, int grid, float* abuf, float* hbuf, double* a64,
+                       float* cand, int sms, int* counters, int* launches, cudaStream_t s);
 size_t dyn_scratch_doubles(const DevNet& net);
 size_t dyn_hbuf_stride(const DevNet& net);
 size_t dyn_abuf_stride(const DevNet& net);
+size_t dyn_a64_stride(const DevNet& net);     // doubles per scenario: the FP64 state matrix (mixed form)
+size_t dyn_cand_stride();                     // floats per scenario: refinement candidates (mixed form)
 bool dyn_split_fits(const DevNet& net, int device);
 cudaError_t launch_risk(int nE, const uint8_t* S1, const uint8_t* S2, const double* lam, int mode,
                         double* R, int64_t* missing, cudaStream_t s, const double* F = nullptr);

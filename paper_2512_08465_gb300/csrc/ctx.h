@@ -41,6 +41,7 @@ struct DevBuf {
 
 struct Network {
     int id = 0;
+    int busy = 0;                     // calls reading its tables outside the context lock
     DevNet dev{};
     DevBuf blob;                      // all static device arrays
     Symbolic sym;
@@ -63,15 +64,16 @@ struct Network {
 // workspace are chained through `free` (each waits for the previous one,
 // whatever its stream).
 struct Workspace {
-    DevBuf scratch, isl, opfx, opfst, counters, hbuf, abuf;
+    DevBuf scratch, isl, opfx, opfst, counters, hbuf, abuf, a64, cand;
     cudaEvent_t free = nullptr;
     bool used = false;
     size_t bytes() const {
-        return scratch.bytes + isl.bytes + opfx.bytes + opfst.bytes + counters.bytes + hbuf.bytes + abuf.bytes;
+        return scratch.bytes + isl.bytes + opfx.bytes + opfst.bytes + counters.bytes + hbuf.bytes + abuf.bytes +
+               a64.bytes + cand.bytes;
     }
     void release() {
         scratch.release(); isl.release(); opfx.release(); opfst.release(); counters.release();
-        hbuf.release(); abuf.release();
+        hbuf.release(); abuf.release(); a64.release(); cand.release();
     }
     ~Workspace() {
         if (free) cudaEventDestroy(free);

@@ -147,10 +147,19 @@ __device__ void eig2(double p, double q, double r, double s, double* re, double*
 // scaled (a scaling by a power of two changes the other norms by a known
 // amount), so the sequential scan over the indices needs no reduction.  One
 // thread takes each index's decision; only indices that are scaled cost a
-// pass over the matrix.
+// pass over the matrix.  The scale search stops at 2^+-kBalExp (T = float) or
+// 2^+-(4 kBalExp) (T = double), so a row or column norm that is tiny next to
+// the other cannot drive the factor to overflow or zero; an index whose best
+// factor lies beyond that is scaled by the bound.  When dsc is given, dsc[i]
+// receives the product of the factors of index i: the balanced matrix is
+// diag(dsc)^-1 A diag(dsc), exactly (every factor is a power of two).
+constexpr int kBalExp = 30;
 template <typename T>
-__device__ void balance(T* A, const int n, T* cs, T* rs, DShared& sh) {
+__device__ void balance(T* A, const int n, T* cs, T* rs, DShared& sh, T* dsc = nullptr) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const T fmaxb = (T)ldexp(1.0, sizeof(T) == 8 ? 4 * kBalExp : kBalExp), fminb = (T)1 / fmaxb;
+    if (dsc)
+        for (int j = tid; j < n; j += kThreads) dsc[j] = (T)1;
     for (int sweep = 0; sweep < 100; ++sweep) {
         for (int j = tid; j < n; j += kThreads) {
             T c = 0;
@@ -178,9 +187,9 @@ __device__ void balance(T* A, const int n, T* cs, T* rs, DShared& sh) {
                     if (c == 0 || r == 0 || !isfinite(c) || !isfinite(r)) continue;
                     T g = r / 2, f = 1;
                     const T ssum = c + r;
-                    while (c < g) { f *= 2; c *= 4; }
+                    while (c < g && f < fmaxb) { f *= 2; c *= 4; }
                     g = r * 2;
-                    while (c > g) { f /= 2; c /= 4; }
+                    while (c > g && f > fminb) { f /= 2; c /= 4; }
                     if ((c + r) / f < (T)0.95 * ssum) { pick = i; fpick = (double)f; }
                 }
                 sh.bal_i = pick;
@@ -194,6 +203,7 @@ __device__ void balance(T* A, const int n, T* cs, T* rs, DShared& sh) {
                 if (j == i) {
                     cs[i] *= f;
                     rs[i] *= finv;
+                    if (dsc) dsc[i] *= f;
                     continue;
                 }
                 const T a = A[(size_t)i * n + j], b = A[(size_t)j * n + i];
@@ -423,6 +433,30 @@ __host__ __device__ inline int hq_off(int n, int i) {
 }
 constexpr int kHqHead = 4;          // floats before the packed matrix: the order n (int bits), padding
 
+// Slot of one scenario in the balanced-matrix buffer (front kernel -> cluster
+// Hessenberg kernel -> refinement kernel), floats: the head, the balanced
+// matrix (row-major n x n), then the balancing factors D (the balanced matrix is
+// D^-1 A D) and the Householder factors beta_k.  The cluster kernel overwrites
+// the matrix area with the Householder vectors once it has loaded the matrix:
+// vector k (entries for rows k+1..n-1, the first one the reflector's head) at
+// refl_off(n, k).
+__host__ __device__ inline size_t ab_mat_floats(int nmax) { return ((size_t)nmax * nmax + 3) & ~(size_t)3; }
+__host__ __device__ inline size_t ab_d_off(int nmax) { return kHqHead + ab_mat_floats(nmax); }
+__host__ __device__ inline size_t ab_beta_off(int nmax) { return ab_d_off(nmax) + (((size_t)nmax + 3) & ~(size_t)3); }
+__host__ __device__ inline size_t ab_stride(int nmax) { return ab_beta_off(nmax) + (((size_t)nmax + 3) & ~(size_t)3); }
+__host__ __device__ inline int refl_off(int n, int k) { return k * (n - 1) - (k * (k - 1)) / 2; }
+
+// Candidates of the FP64 refinement per scenario (shared-memory QR -> refinement
+// kernel), floats: [0] count (int bits), [1] flags (int bits; bit 2c: candidate c
+// may carry the largest real part, bit 2c+1: the smallest damping ratio), then
+// the FP32 eigenvalue (re, im >= 0) of each candidate.
+constexpr int kRefK = 4;                     // candidates per scenario at most (more: FP64 re-run)
+constexpr int kCandStride = 4 + 2 * kRefK;
+// Bound on the distance of an FP32 eigenvalue of the 118-bus state matrix from the
+// exact one (measured differences are below 3e-5): an eigenvalue can decide max Re
+// or min zeta only if its FP32 value is within this bound of deciding it.
+constexpr float kEigDelta = 1e-3f;
+
 // max Re and min damping ratio over the n eigenvalues (block-wide, result on all threads)
 __device__ void eig_stats(DShared& sh, int n, const double* wr, const double* wi, double& maxre, double& minz) {
     const int tid = threadIdx.x;
@@ -449,7 +483,7 @@ enum { DYN_FULL64 = 0, DYN_MIXED_INLINE = 1, DYN_FRONT = 2, DYN_RERUN = 3 };
 template <int kMode>
 __global__ void __launch_bounds__(kThreads)
 dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch, size_t per_cta, DLay L,
-           float* hbuf, size_t hstride, int* counter) {
+           float* hbuf, size_t hstride, double* a64, size_t a64stride, int* counter) {
     __shared__ DShared sh;
     extern __shared__ double dsm[];   // [ng] ints (compact -> generator id), then cs, rs, v [5 ng] each
     int* gidx = reinterpret_cast<int*>(dsm);
@@ -627,7 +661,8 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
         }
         __syncthreads();
         // ---- state matrix: one thread per 5x5 block (k, l) ----
-        double* A = W + L.A;
+        // (the front kernel keeps it per scenario for the FP64 refinement)
+        double* A = (kMode == DYN_FRONT && a64) ? a64 + (size_t)s * a64stride : W + L.A;
         for (int w = tid; w < m * m; w += kThreads) {
             const int kk = w / m, ll = w % m;
             const int k = gidx[kk];
@@ -706,7 +741,8 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
             for (int w = tid; w < n * n; w += kThreads) A32[w] = (float)A[w];
             if (tid == 0) dst[0] = __int_as_float(n);
             __syncthreads();
-            balance<float>(A32, n, reinterpret_cast<float*>(cs_d), reinterpret_cast<float*>(rs_d), sh);
+            balance<float>(A32, n, reinterpret_cast<float*>(cs_d), reinterpret_cast<float*>(rs_d), sh,
+                           dst + ab_d_off(5 * ng - 1));
             __syncthreads();
             continue;
         }
@@ -786,7 +822,7 @@ constexpr int kHsWarps = kHsThreads / 32;
 constexpr int kHsCols = 12;         // columns per lane in the row pass: orders up to 32 * 12 + 1
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kHsThreads, 1)
-hess_cluster_kernel(EvalArgs a, OpfOut o, const float* __restrict__ abuf, size_t astride, float* __restrict__ hbuf,
+hess_cluster_kernel(EvalArgs a, OpfOut o, float* __restrict__ abuf, size_t astride, float* __restrict__ hbuf,
                     size_t hstride, int nmax, int* counter) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -816,9 +852,14 @@ hess_cluster_kernel(EvalArgs a, OpfOut o, const float* __restrict__ abuf, size_t
         cl.sync();                                    // both have read scen
         if (s >= a.n) break;
         if (o.status[s] != 1) continue;
-        const float* src = abuf + (size_t)s * astride;
+        float* src = abuf + (size_t)s * astride;
         const int n = __float_as_int(src[0]);
         const float* Ag = src + kHqHead;
+        // Householder vectors and factors for the refinement kernel: rank 0 writes them
+        // over the slot's matrix, after both CTAs have loaded their rows (the first
+        // cluster barrier of column 0)
+        float* refl = src + kHqHead;
+        float* betas = src + ab_beta_off(nmax);
         const int h = (n + 1) / 2, r0 = rank * h, r1 = min(n, r0 + h), nr = max(0, r1 - r0);
         for (int w = tid; w < nr * n; w += kHsThreads) As[w] = Ag[(size_t)r0 * n + w];
         __syncthreads();
@@ -845,7 +886,10 @@ hess_cluster_kernel(EvalArgs a, OpfOut o, const float* __restrict__ abuf, size_t
             }
             cl.sync();                                // reflector and norm partials in place
             const float tail = np[par * 2] + np[par * 2 + 1];
-            if (tail == 0.0f) continue;               // column already reduced (same in both CTAs)
+            if (tail == 0.0f) {                       // column already reduced (same in both CTAs)
+                if (rank == 0 && tid == 0) betas[k] = 0.0f;
+                continue;
+            }
             const float x0 = v[0];
             const float nrm = sqrtf(x0 * x0 + tail);
             const float alpha = (x0 >= 0.0f) ? -nrm : nrm;
@@ -856,6 +900,11 @@ hess_cluster_kernel(EvalArgs a, OpfOut o, const float* __restrict__ abuf, size_t
             __syncthreads();
             if (tid == 0) v[0] = v0;
             __syncthreads();
+            if (rank == 0) {
+                float* rk = refl + refl_off(n, k);
+                for (int i = tid; i < n - k - 1; i += kHsThreads) rk[i] = v[i];
+                if (tid == 0) betas[k] = beta;
+            }
             float* w_own = wb + (par * 2 + rank) * nmax;
             float* w_peer = peer_wb + (par * 2 + rank) * nmax;
             for (int j = k + 1 + tid; j < n; j += kHsThreads) {   // partial v^T A over own rows
@@ -948,7 +997,7 @@ __device__ __forceinline__ void eig2f(float p, float q, float r, float s, float*
 
 __global__ void __launch_bounds__(kQrThreads, 1)
 hqr_smem_kernel(EvalArgs a, OpfOut o, const float* __restrict__ hbuf, size_t hstride, int nmax,
-                double damping_min, int* counter) {
+                double damping_min, float* __restrict__ cand, int* counter) {
     extern __shared__ float qsm[];
     __shared__ float red[2][kQrThreads / 32];
     __shared__ float xs[2][3];
@@ -1143,11 +1192,362 @@ hqr_smem_kernel(EvalArgs a, OpfOut o, const float* __restrict__ hbuf, size_t hst
                 o.status[s] = 6;
                 atomicAdd(a.reruns, 1);
             } else {
+                // Candidates of the FP64 refinement, in index order: every eigenvalue
+                // (im >= 0 of a pair) whose exact value may carry the largest real part
+                // or the smallest damping ratio, given |FP32 - exact| <= kEigDelta.
+                // Damping ratio of lambda with |delta lambda| <= d moves by at most 2 d / |lambda|.
+                float zu = INFINITY;
+                for (int i = 0; i < n; ++i) {
+                    if (wi[i] < 0.0f) continue;
+                    const float mg = sqrtf(wr[i] * wr[i] + wi[i] * wi[i]);
+                    const float z = mg > 0.0f ? -wr[i] / mg : 1.0f;
+                    zu = fminf(zu, mg > 0.0f ? z + 2.0f * kEigDelta / mg : INFINITY);
+                }
+                float* cs = cand + (size_t)s * kCandStride;
+                int cnt = 0, flags = 0;
+                for (int i = 0; i < n; ++i) {
+                    if (wi[i] < 0.0f) continue;
+                    const float mg = sqrtf(wr[i] * wr[i] + wi[i] * wi[i]);
+                    const float z = mg > 0.0f ? -wr[i] / mg : 1.0f;
+                    const bool cre = wr[i] >= maxre - 2.0f * kEigDelta;
+                    const bool cz = !(mg > 0.0f) || z - 2.0f * kEigDelta / mg <= zu;
+                    if (!cre && !cz) continue;
+                    if (cnt < kRefK) {
+                        cs[4 + 2 * cnt] = wr[i];
+                        cs[5 + 2 * cnt] = wi[i];
+                        flags |= (cre ? 1 : 0) << (2 * cnt);
+                        flags |= (cz ? 2 : 0) << (2 * cnt);
+                    }
+                    ++cnt;
+                }
+                if (cnt > kRefK) {                         // too many to refine: FP64 screen
+                    o.status[s] = 6;
+                    atomicAdd(a.reruns, 1);
+                } else {
+                    cs[0] = __int_as_float(cnt);
+                    cs[1] = __int_as_float(flags);
+                    o.status[s] = 8;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 refinement of the FP32 screen's decisive eigenvalues.  For each candidate
+// (an FP32 eigenvalue sigma that may carry max Re or min zeta), one warp computes
+// the right and another the left eigenvector of the packed FP32 Hessenberg matrix
+// H by two passes of inverse iteration with shift sigma, and takes each back to
+// the balanced matrix through the Householder vectors of the cluster kernel.  The
+// eigenvalue is then the two-sided Rayleigh quotient w^H A v / w^H v with the
+// scenario's FP64 state matrix A (v, w scaled by the balancing factors), whose
+// error is second order in the vectors' FP32 error.  The statistics over the
+// refined candidates decide the class.  A candidate whose quotient is
+// ill-conditioned or lands away from sigma sends the scenario to the FP64 screen.
+//
+// Inverse iteration on an upper Hessenberg G - sigma I, one warp: Gaussian
+// elimination with partial pivoting between each carried row and the next row of
+// G (the only one with an entry below the diagonal), U^{-X} b (X = H or T) formed
+// row by row as U's rows appear, so U is never stored; the row operations E_k
+// (swap flag and multiplier) are kept and applied as E_0^X ... E_{n-2}^X at the
+// end.  The left vector solves (H - sigma I)^H z = b with G = H; the right one
+// solves (H - sigma I) x = b as (G - sigma I)^T (J x) = J b with G = J H^T J
+// (J reverses the order), which is upper Hessenberg again.
+constexpr int kRfThreads = 256;
+constexpr int kRfWarps = kRfThreads / 32;
+static_assert(2 * kRefK <= kRfWarps, "one warp per eigenvector");
+
+__device__ __forceinline__ float2 cmul2(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 cconj2(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cdiv2(float2 a, float2 b) {
+    const float sc = fmaxf(fabsf(b.x), fabsf(b.y));
+    const float bx = b.x / sc, by = b.y / sc;
+    const float d = (bx * bx + by * by) * sc;
+    return make_float2((a.x * bx + a.y * by) / d, (a.y * bx - a.x * by) / d);
+}
+
+template <bool kRight>
+__device__ __forceinline__ float hess_g(const float* Hs, const int* rb, int n, int i, int j) {
+    return kRight ? Hs[rb[n - 1 - j] + n - 1 - i] : Hs[rb[i] + j];
+}
+
+// y <- (G - sig I)^{-X} y (X = H for the left vector, T for the right one), one warp.
+template <bool kRight>
+__device__ void hess_inverse_pass(const float* Hs, const int* rb, int n, float2 sig, float tiny, float2* y, float2* c,
+                                  float2* mul, unsigned* swp, int lane) {
+    const bool cj = !kRight;
+    for (int j = lane; j < n; j += 32)
+        c[j] = make_float2(hess_g<kRight>(Hs, rb, n, 0, j) - (j == 0 ? sig.x : 0.0f), j == 0 ? -sig.y : 0.0f);
+    for (int w = lane; w < (n + 31) / 32; w += 32) swp[w] = 0u;
+    __syncwarp();
+    for (int k = 0; k < n; ++k) {
+        const bool last = (k == n - 1);
+        const float2 ck = c[k];
+        const float2 bk = y[k];
+        const float rk = last ? 0.0f : hess_g<kRight>(Hs, rb, n, k + 1, k);
+        const bool sw = !last && fabsf(rk) > fabsf(ck.x) + fabsf(ck.y);
+        float2 pk = sw ? make_float2(rk, 0.0f) : ck;
+        if (pk.x == 0.0f && pk.y == 0.0f) pk.x = tiny;             // exactly singular: perturb the pivot
+        const float2 ok = sw ? ck : make_float2(rk, 0.0f);
+        const float2 mk = last ? make_float2(0.0f, 0.0f) : cdiv2(ok, pk);
+        const float2 yk = cdiv2(bk, cj ? cconj2(pk) : pk);
+        __syncwarp();                                               // every lane has read c[k], y[k]
+        for (int j = k + 1 + lane; j < n; j += 32) {
+            float2 rj = make_float2(hess_g<kRight>(Hs, rb, n, k + 1, j), 0.0f);
+            if (j == k + 1) {
+                rj.x -= sig.x;
+                rj.y -= sig.y;
+            }
+            const float2 cv = c[j];
+            const float2 pj = sw ? rj : cv, oj = sw ? cv : rj;
+            const float2 t = cmul2(cj ? cconj2(pj) : pj, yk);
+            y[j] = make_float2(y[j].x - t.x, y[j].y - t.y);
+            const float2 u = cmul2(mk, pj);
+            c[j] = make_float2(oj.x - u.x, oj.y - u.y);
+        }
+        if (lane == 0) {
+            y[k] = yk;
+            mul[k] = mk;
+            if (sw) swp[k >> 5] |= 1u << (k & 31);
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        for (int k = n - 2; k >= 0; --k) {
+            const float2 t = cmul2(cj ? cconj2(mul[k]) : mul[k], y[k + 1]);
+            y[k] = make_float2(y[k].x - t.x, y[k].y - t.y);
+            if ((swp[k >> 5] >> (k & 31)) & 1u) {
+                const float2 q = y[k];
+                y[k] = y[k + 1];
+                y[k + 1] = q;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// scale y to a largest component of modulus 1; false if it has none (zero or not finite)
+__device__ bool warp_normalise(float2* y, int n, int lane) {
+    float mx = 0.0f;
+    for (int j = lane; j < n; j += 32) mx = fmaxf(mx, fmaxf(fabsf(y[j].x), fabsf(y[j].y)));
+    for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (!(mx > 0.0f) || !isfinite(mx)) return false;
+    const float inv = 1.0f / mx;
+    for (int j = lane; j < n; j += 32) y[j] = make_float2(y[j].x * inv, y[j].y * inv);
+    __syncwarp();
+    return true;
+}
+
+struct RfShared {
+    int scen, cnt, flags;
+    float tiny;
+    int bad[2 * kRefK];
+    float hred[kRfWarps];
+    double acc[kRfWarps][kRefK][6];   // per warp: num (re, im), den (re, im), |v|^2, |w|^2
+};
+
+__global__ void __launch_bounds__(kRfThreads, 1)
+eig_refine_kernel(EvalArgs a, OpfOut o, const float* __restrict__ hbuf, size_t hstride, const float* __restrict__ abuf,
+                  size_t astride, const double* __restrict__ a64, size_t a64stride, const float* __restrict__ cand,
+                  int nmax, double damping_min, int* counter) {
+    extern __shared__ float4 rsm4[];
+    float* rsm = reinterpret_cast<float*>(rsm4);
+    __shared__ RfShared sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const size_t hsz = ((size_t)hq_off(nmax, nmax) + 3) & ~(size_t)3;
+    const size_t vsz = (size_t)4 * kRefK * nmax * 2;                 // FP64 vectors (doubles as float pairs)
+    float* Hs = rsm;                                                  // packed H, later the FP64 vectors
+    double2* vA = reinterpret_cast<double2*>(rsm);                    // [kRefK][nmax]
+    double2* wA = vA + (size_t)kRefK * nmax;                          // [kRefK][nmax]
+    int* rb = reinterpret_cast<int*>(rsm + (hsz > vsz ? hsz : vsz));
+    float2* wk = reinterpret_cast<float2*>(rb + ((nmax + 3) & ~3));   // per warp: c, mul [nmax] each
+    float2* vec = wk + (size_t)kRfWarps * 2 * nmax;                   // [2 kRefK][nmax] vectors
+    unsigned* swp = reinterpret_cast<unsigned*>(vec + (size_t)2 * kRefK * nmax);   // per warp: bits
+    const int swords = (nmax + 31) / 32;
+
+    for (;;) {
+        if (tid == 0) sh.scen = atomicAdd(counter, 1);
+        __syncthreads();
+        const int s = sh.scen;
+        if (s >= a.n) break;
+        if (o.status[s] != 8) {
+            __syncthreads();
+            continue;
+        }
+        const float* src = hbuf + (size_t)s * hstride;
+        const int n = __float_as_int(src[0]);
+        const int hs = hq_off(n, n);
+        const float* slot = abuf + (size_t)s * astride;
+        const float* cs = cand + (size_t)s * kCandStride;
+        {
+            const float4* s4 = reinterpret_cast<const float4*>(src + kHqHead);
+            float4* d4 = reinterpret_cast<float4*>(Hs);
+            for (int w = tid; w < (hs >> 2); w += kRfThreads) d4[w] = s4[w];
+            for (int w = (hs & ~3) + tid; w < hs; w += kRfThreads) Hs[w] = src[kHqHead + w];
+        }
+        for (int i = tid; i < n; i += kRfThreads) rb[i] = hq_off(n, i) - hq_start(i);
+        if (tid == 0) {
+            sh.cnt = __float_as_int(cs[0]);
+            sh.flags = __float_as_int(cs[1]);
+        }
+        if (tid < 2 * kRefK) sh.bad[tid] = 0;
+        __syncthreads();
+        {
+            float hm = 0.0f;
+            for (int w = tid; w < hs; w += kRfThreads) hm = fmaxf(hm, fabsf(Hs[w]));
+            for (int off = 16; off; off >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, off));
+            if (lane == 0) sh.hred[warp] = hm;
+            __syncthreads();
+            if (tid == 0) {
+                float m = sh.hred[0];
+                for (int w = 1; w < kRfWarps; ++w) m = fmaxf(m, sh.hred[w]);
+                sh.tiny = 1.1920928955078125e-07f * (m > 0.0f ? m : 1.0f);
+            }
+            __syncthreads();
+        }
+        const int cnt = sh.cnt;
+        // ---- eigenvectors of H, one warp each: task 2c = right vector of candidate c, 2c+1 = left ----
+        if (warp < 2 * cnt) {
+            const int c = warp >> 1;
+            const bool right = (warp & 1) == 0;
+            const float2 sig = make_float2(cs[4 + 2 * c], cs[5 + 2 * c]);
+            float2* y = vec + (size_t)warp * nmax;
+            float2* cw = wk + (size_t)warp * 2 * nmax;
+            float2* mw = cw + nmax;
+            unsigned* sb = swp + warp * swords;
+            for (int j = lane; j < n; j += 32) y[j] = make_float2(1.0f, 0.0f);
+            __syncwarp();
+            bool ok = true;
+            for (int pass = 0; pass < 2 && ok; ++pass) {
+                if (right) hess_inverse_pass<true>(Hs, rb, n, sig, sh.tiny, y, cw, mw, sb, lane);
+                else hess_inverse_pass<false>(Hs, rb, n, sig, sh.tiny, y, cw, mw, sb, lane);
+                ok = warp_normalise(y, n, lane);
+            }
+            if (ok && right) {                                   // J x -> x
+                for (int j = lane; j < n / 2; j += 32) {
+                    const float2 q = y[j];
+                    y[j] = y[n - 1 - j];
+                    y[n - 1 - j] = q;
+                }
+                __syncwarp();
+            }
+            if (ok) {                                            // Q x: reflectors n-3 .. 0
+                const float* betas = slot + ab_beta_off(nmax);
+                for (int k = n - 3; k >= 0; --k) {
+                    const float bt = betas[k];
+                    if (bt == 0.0f) continue;
+                    const float* u = slot + kHqHead + refl_off(n, k);
+                    const int mm = n - k - 1;
+                    float sr = 0.0f, si = 0.0f;
+                    for (int i = lane; i < mm; i += 32) {
+                        const float2 q = y[k + 1 + i];
+                        sr += u[i] * q.x;
+                        si += u[i] * q.y;
+                    }
+                    for (int off = 16; off; off >>= 1) {
+                        sr += __shfl_xor_sync(0xffffffffu, sr, off);
+                        si += __shfl_xor_sync(0xffffffffu, si, off);
+                    }
+                    sr *= bt;
+                    si *= bt;
+                    for (int i = lane; i < mm; i += 32) {
+                        const float2 q = y[k + 1 + i];
+                        y[k + 1 + i] = make_float2(q.x - sr * u[i], q.y - si * u[i]);
+                    }
+                    __syncwarp();
+                }
+                ok = warp_normalise(y, n, lane);
+            }
+            if (lane == 0 && !ok) sh.bad[warp] = 1;
+        }
+        __syncthreads();
+        // ---- FP64: v_A = D v_B, w_A = D^-1 w_B; two-sided Rayleigh quotient with A ----
+        const float* D = slot + ab_d_off(nmax);
+        for (int w = tid; w < cnt * n; w += kRfThreads) {
+            const int c = w / n, j = w % n;
+            const double d = (double)D[j];
+            const float2 v = vec[(size_t)(2 * c) * nmax + j], u = vec[(size_t)(2 * c + 1) * nmax + j];
+            vA[(size_t)c * nmax + j] = make_double2(d * v.x, d * v.y);
+            wA[(size_t)c * nmax + j] = make_double2(u.x / d, u.y / d);
+        }
+        __syncthreads();
+        {
+            double acc[kRefK][6];
+#pragma unroll
+            for (int c = 0; c < kRefK; ++c)
+#pragma unroll
+                for (int q = 0; q < 6; ++q) acc[c][q] = 0.0;
+            const double* A = a64 + (size_t)s * a64stride;
+            for (int i = warp; i < n; i += kRfWarps) {
+                const double* Ar = A + (size_t)i * n;
+                double pr[kRefK], pi[kRefK];
+#pragma unroll
+                for (int c = 0; c < kRefK; ++c) pr[c] = pi[c] = 0.0;
+                for (int j = lane; j < n; j += 32) {
+                    const double aij = Ar[j];
+#pragma unroll
+                    for (int c = 0; c < kRefK; ++c) {
+                        if (c < cnt) {
+                            const double2 v = vA[(size_t)c * nmax + j];
+                            pr[c] = fma(aij, v.x, pr[c]);
+                            pi[c] = fma(aij, v.y, pi[c]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < kRefK; ++c) {
+                    if (c >= cnt) continue;
+                    for (int off = 16; off; off >>= 1) {
+                        pr[c] += __shfl_xor_sync(0xffffffffu, pr[c], off);
+                        pi[c] += __shfl_xor_sync(0xffffffffu, pi[c], off);
+                    }
+                    const double2 w = wA[(size_t)c * nmax + i], v = vA[(size_t)c * nmax + i];
+                    // conj(w_i) (A v)_i and conj(w_i) v_i
+                    acc[c][0] += w.x * pr[c] + w.y * pi[c];
+                    acc[c][1] += w.x * pi[c] - w.y * pr[c];
+                    acc[c][2] += w.x * v.x + w.y * v.y;
+                    acc[c][3] += w.x * v.y - w.y * v.x;
+                    acc[c][4] += v.x * v.x + v.y * v.y;
+                    acc[c][5] += w.x * w.x + w.y * w.y;
+                }
+            }
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < kRefK; ++c)
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) sh.acc[warp][c][q] = acc[c][q];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            bool good = true;
+            double maxre = -INFINITY, minz = INFINITY;
+            for (int c = 0; c < cnt; ++c) {
+                double t[6] = {0, 0, 0, 0, 0, 0};
+                for (int w = 0; w < kRfWarps; ++w)
+                    for (int q = 0; q < 6; ++q) t[q] += sh.acc[w][c][q];
+                const cplx lam = cdiv(cm(t[0], t[1]), cm(t[2], t[3]));
+                const double sx = cs[4 + 2 * c], sy = cs[5 + 2 * c];
+                const bool ok = !sh.bad[2 * c] && !sh.bad[2 * c + 1] && isfinite(lam.re) && isfinite(lam.im) &&
+                                t[2] * t[2] + t[3] * t[3] >= 1e-10 * t[4] * t[5] &&
+                                fabs(lam.re - sx) <= 2.0 * kEigDelta && fabs(fabs(lam.im) - sy) <= 2.0 * kEigDelta;
+                if (!ok) {
+                    good = false;
+                    break;
+                }
+                const double mg = sqrt(lam.re * lam.re + lam.im * lam.im);
+                if ((sh.flags >> (2 * c)) & 1) maxre = fmax(maxre, lam.re);
+                if ((sh.flags >> (2 * c)) & 2) minz = fmin(minz, mg > 0.0 ? -lam.re / mg : 1.0);
+            }
+            if (!good || !(maxre > -INFINITY) || !(minz < INFINITY)) {
+                o.status[s] = 6;                                // FP64 screen instead
+                atomicAdd(a.reruns, 1);
+            } else {
                 uint8_t k;
-                if (maxre >= 0.0f) k = CS_SS_UNSTABLE;
+                if (maxre >= 0.0) k = CS_SS_UNSTABLE;
                 else if (minz < damping_min) k = CS_SS_POORLY_DAMPED;
                 else k = CS_SECURE;
-                if (a.out.n_islands[s] > 1) {              // main island: the scenario's class stays ISLANDED
+                if (a.out.n_islands[s] > 1) {                   // main island: the scenario's class stays ISLANDED
                     if (a.out.main_klass) a.out.main_klass[s] = k;
                 } else {
                     a.out.klass[s] = k;
@@ -1155,6 +1555,7 @@ hqr_smem_kernel(EvalArgs a, OpfOut o, const float* __restrict__ hbuf, size_t hst
                 }
                 a.out.max_re[s] = maxre;
                 a.out.min_zeta[s] = minz;
+                o.status[s] = 1;
             }
         }
         __syncthreads();
@@ -1170,13 +1571,24 @@ size_t dyn_hbuf_stride(const DevNet& net) {
     return (size_t)kHqHead + (size_t)((hq_off(nmax, nmax) + 3) & ~3);
 }
 
-size_t dyn_abuf_stride(const DevNet& net) {
+size_t dyn_abuf_stride(const DevNet& net) { return ab_stride(5 * net.ng - 1); }
+
+size_t dyn_a64_stride(const DevNet& net) {
     const size_t nmax = 5 * (size_t)net.ng - 1;
-    return (size_t)kHqHead + ((nmax * nmax + 3) & ~(size_t)3);
+    return nmax * nmax;
 }
+
+size_t dyn_cand_stride() { return kCandStride; }
 
 static size_t qr_smem_bytes(int nmax) {
     return sizeof(float) * ((size_t)((hq_off(nmax, nmax) + 3) & ~3) + 3 * (size_t)nmax);
+}
+
+static size_t refine_smem_bytes(int nmax) {
+    const size_t hsz = ((size_t)hq_off(nmax, nmax) + 3) & ~(size_t)3;
+    const size_t vsz = (size_t)8 * kRefK * nmax;
+    return sizeof(float) * (std::max(hsz, vsz) + (((size_t)nmax + 3) & ~(size_t)3) + (size_t)kRfWarps * 4 * nmax +
+                            (size_t)4 * kRefK * nmax + (size_t)kRfWarps * ((nmax + 31) / 32));
 }
 
 static size_t hess_smem_bytes(int nmax) {
@@ -1188,36 +1600,39 @@ bool dyn_split_fits(const DevNet& net, int device) {
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return false;
     const int nmax = 5 * net.ng - 1;
     if (nmax - 1 > 32 * kHsCols) return false;
-    return qr_smem_bytes(nmax) + 1024 <= (size_t)optin && hess_smem_bytes(nmax) + 1024 <= (size_t)optin;
+    return qr_smem_bytes(nmax) + 1024 <= (size_t)optin && hess_smem_bytes(nmax) + 1024 <= (size_t)optin &&
+           refine_smem_bytes(nmax) + sizeof(RfShared) + 1024 <= (size_t)optin;
 }
 
 template <int kMode>
 static cudaError_t launch_mode(const DevNet& net, const EvalArgs& a, OpfOut o, double damping_min, double* scratch,
-                               size_t per_cta, const DLay& L, float* hbuf, size_t hstride, int grid, int* counter,
-                               cudaStream_t s) {
+                               size_t per_cta, const DLay& L, float* hbuf, size_t hstride, double* a64, int grid,
+                               int* counter, cudaStream_t s) {
     const size_t smem = sizeof(double) * ((size_t)((net.ng + 1) >> 1) + 15 * (size_t)net.ng);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(dyn_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    dyn_kernel<kMode><<<grid, kThreads, smem, s>>>(net, a, o, damping_min, scratch, per_cta, L, hbuf, hstride, counter);
+    dyn_kernel<kMode><<<grid, kThreads, smem, s>>>(net, a, o, damping_min, scratch, per_cta, L, hbuf, hstride, a64,
+                                                   dyn_a64_stride(net), counter);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double damping_min, int precision,
-                       double* scratch, size_t scratch_per_cta, int grid, float* abuf, float* hbuf, int sms,
-                       int* counters, int* launches, cudaStream_t s) {
+                       double* scratch, size_t scratch_per_cta, int grid, float* abuf, float* hbuf, double* a64,
+                       float* cand, int sms, int* counters, int* launches, cudaStream_t s) {
     *launches = 0;
     if (a.n <= 0) return cudaSuccess;
     const DLay L = make_dlayout(net);
     if ((size_t)L.total > scratch_per_cta) return cudaErrorInvalidValue;
     cudaError_t e;
-    if (precision == CS_PREC_MIXED && hbuf && abuf) {
-        // FP32 screen in four kernels: front (model, balancing) at several CTAs per SM,
+    if (precision == CS_PREC_MIXED && hbuf && abuf && a64 && cand) {
+        // FP32 screen in five kernels: front (model, balancing) at several CTAs per SM,
         // Hessenberg reduction on a two-CTA cluster, QR from shared memory at one CTA per
-        // SM, and the FP64 re-run of the scenarios the FP32 screen cannot decide.
+        // SM, FP64 refinement of the decisive eigenvalues, and the FP64 re-run of the
+        // scenarios the FP32 screen cannot decide.
         const size_t hstride = dyn_hbuf_stride(net), astride = dyn_abuf_stride(net);
-        e = launch_mode<DYN_FRONT>(net, a, o, damping_min, scratch, scratch_per_cta, L, abuf, astride, grid,
+        e = launch_mode<DYN_FRONT>(net, a, o, damping_min, scratch, scratch_per_cta, L, abuf, astride, a64, grid,
                                    counters, s);
         if (e != cudaSuccess) return e;
         const int nmax = 5 * net.ng - 1;
@@ -1232,20 +1647,27 @@ cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double da
         e = cudaFuncSetAttribute(hqr_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
         if (e != cudaSuccess) return e;
         const int gq = (int)std::min<int64_t>((int64_t)sms, a.n);
-        hqr_smem_kernel<<<gq, kQrThreads, qsm, s>>>(a, o, hbuf, hstride, nmax, damping_min, counters + 1);
+        hqr_smem_kernel<<<gq, kQrThreads, qsm, s>>>(a, o, hbuf, hstride, nmax, damping_min, cand, counters + 1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        e = launch_mode<DYN_RERUN>(net, a, o, damping_min, scratch, scratch_per_cta, L, nullptr, 0, grid,
+        const size_t rsm = refine_smem_bytes(nmax);
+        e = cudaFuncSetAttribute(eig_refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+        if (e != cudaSuccess) return e;
+        eig_refine_kernel<<<gq, kRfThreads, rsm, s>>>(a, o, hbuf, hstride, abuf, astride, a64, dyn_a64_stride(net),
+                                                       cand, nmax, damping_min, counters + 4);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = launch_mode<DYN_RERUN>(net, a, o, damping_min, scratch, scratch_per_cta, L, nullptr, 0, nullptr, grid,
                                    counters + 2, s);
         if (e != cudaSuccess) return e;
-        *launches = 4;
+        *launches = 5;
     } else if (precision == CS_PREC_MIXED) {
-        e = launch_mode<DYN_MIXED_INLINE>(net, a, o, damping_min, scratch, scratch_per_cta, L, nullptr, 0, grid,
-                                          counters, s);
+        e = launch_mode<DYN_MIXED_INLINE>(net, a, o, damping_min, scratch, scratch_per_cta, L, nullptr, 0, nullptr,
+                                          grid, counters, s);
         if (e != cudaSuccess) return e;
         *launches = 1;
     } else {
-        e = launch_mode<DYN_FULL64>(net, a, o, damping_min, scratch, scratch_per_cta, L, nullptr, 0, grid,
+        e = launch_mode<DYN_FULL64>(net, a, o, damping_min, scratch, scratch_per_cta, L, nullptr, 0, nullptr, grid,
                                     counters, s);
         if (e != cudaSuccess) return e;
         *launches = 1;

@@ -7,10 +7,12 @@ Bar: main_klass and the choice of island bit-exact (buses outside it carry
 Vm = Va = 0 exactly); the shed bit-exact (both sides add the same per-unit loads
 in bus order); cost within 1e-6 relative; Vm, Va, voltage margin and loading
 within 1e-8 where the main island's OPF converged; max Re and min damping ratio
-of its small-signal screen within 1e-6 (FP64 form).  A main_klass may differ only
-in the guard band of the parity suite (an oracle OPF that needed >= 48 of its 50
-iterations, or a decisive eigen statistic within 1e-6 of its threshold).
-Scenarios that do not split are unchanged by the form.
+of its small-signal screen within 1e-6 (FP64 form); iteration counts of converged
+OPFs exactly.  No
+main_klass may differ; cases in the guard band of the parity suite (an oracle OPF
+that needed >= 48 of its 50 iterations, or a decisive eigen statistic within 1e-6
+of its threshold) are counted and reported.  Scenarios that do not split are
+unchanged by the form.
 """
 import numpy as np
 import pytest
@@ -42,12 +44,12 @@ def _compare(got, refs, nb):
         assert int(got["klass"][q]) == 1 and int(got["severe"][q]) == 1, q
         assert got["shed_mw"][q] == r["shed_mw"], (q, got["shed_mw"][q], r["shed_mw"])
         mk = int(got["main_klass"][q])
-        if mk != r["main_klass"]:
-            near = r["opf_iters"] >= 48 or (np.isfinite(r["max_re"]) and (
-                abs(r["max_re"]) < TOL_EIG or abs(r["min_zeta"] - island.DAMPING_MIN) < TOL_EIG))
-            assert near, (q, mk, r["main_klass"])
-            guard += 1
-            continue
+        near = r["opf_iters"] >= 48 or (np.isfinite(r["max_re"]) and (
+            abs(r["max_re"]) < TOL_EIG or abs(r["min_zeta"] - island.DAMPING_MIN) < TOL_EIG))
+        guard += bool(near)
+        assert mk == r["main_klass"], (q, mk, r["main_klass"], "guard band" if near else "")
+        if r["converged"]:
+            assert int(got["opf_iters"][q]) == r["opf_iters"], (q, int(got["opf_iters"][q]), r["opf_iters"])
         if r["live"] is None:
             continue
         vm = got["Vm"][q * nb:(q + 1) * nb]
@@ -132,7 +134,7 @@ def test_main_island_118bus_matches_oracle(net118):
         assert np.all(base["main_klass"] == 255)
         assert np.all(np.isnan(base["shed_mw"][:len(scen)]))
         assert np.all(base["opf_iters"][:len(scen)] == 0)
-    assert guard <= 1
+    print(f"[parity] main island, 118-bus: 0 main-class mismatches, {guard} in the guard band")
     ctx.close()
     ref_ctx.close()
 
@@ -153,7 +155,7 @@ def test_tie_line_split_moves_the_reference_and_no_generation_case():
     got = _run(ctx, nid, 0, [a for a, _ in scen], [b for _, b in scen], J.n_bus)
     refs = [island.evaluate_main_island(J, 0, a, b) for a, b in scen]
     assert refs[0]["ref"] != J.ref_bus
-    assert _compare(got, refs, J.n_bus) == 0
+    _compare(got, refs, J.n_bus)
     ctx.close()
     one = synth.make_network(9, 9, 1, 6, 0, seed=5, levels=(0.5,))
     bridges = [b for b in range(one.n_branch)

@@ -1,12 +1,14 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
 
 Tolerances (from the method's accuracy targets): severity classes, island
-counts and the Risk Index are compared exactly; bus voltage magnitudes and
-angles within 1e-8 (p.u., rad); OPF cost within 1e-6 relative; max Re(lambda)
-and the minimum damping ratio within 1e-6.  A class may differ only inside the
-guard band where floating-point rounding legitimately decides it: an oracle
-OPF that needed >= 48 of its 50 iterations, or a decisive eigen statistic
-within 1e-6 of its threshold; such cases are counted and must stay rare.
+counts, the interior-point iteration count of every converged OPF and the Risk
+Index are compared exactly (an OPF that fails may stop on a numerical failure
+one side detects an iteration earlier than the other); bus voltage magnitudes and angles within 1e-8 (p.u., rad); OPF cost
+within 1e-6 relative; max Re(lambda) and the minimum damping ratio within 1e-6.
+No class may differ.  Scenarios inside the guard band (an oracle OPF that needed
+>= 48 of its 50 iterations, or a decisive eigen statistic within 1e-6 of its
+threshold), where rounding could legitimately decide the class, are counted and
+reported.
 """
 import json
 import os
@@ -65,28 +67,30 @@ def _guard(ref, dmin=pipeline.DAMPING_MIN):
     return False
 
 
-def _compare(got, refs, nb=None, max_guard=0):
+def _compare(got, refs, nb=None, tol_eig=TOL_EIG, label=""):
+    """Every record against the oracle's; returns the number of guard-band cases."""
     guard = 0
     for q, r in enumerate(refs):
+        guard += bool(_guard(r))
         k = int(got["klass"][q])
-        if k != r["klass"]:
-            assert _guard(r), f"class mismatch at {q}: gpu {k} oracle {r['klass']} ({r['level']},{r['i']},{r['j']})"
-            guard += 1
-            continue
-        assert int(got["n_islands"][q]) == r["n_islands"]
-        assert int(got["severe"][q]) == int(r["severe"])
+        where = f"{label} {q}: ({r['level']},{r['i']},{r['j']})"
+        assert k == r["klass"], f"class mismatch at {where}: gpu {k} oracle {r['klass']} (guard {_guard(r)})"
+        assert int(got["n_islands"][q]) == r["n_islands"], where
+        assert int(got["severe"][q]) == int(r["severe"]), where
+        if r["klass"] not in (1, 2):           # a converged OPF: the same number of iterations
+            assert int(got["opf_iters"][q]) == r["opf_iters"], (where, int(got["opf_iters"][q]), r["opf_iters"])
         if r["klass"] in (0, 3, 4, 5):
             c = r["cost"]
-            assert abs(got["cost"][q] - c) <= TOL_COST * abs(c), (q, got["cost"][q], c)
+            assert abs(got["cost"][q] - c) <= TOL_COST * abs(c), (where, got["cost"][q], c)
         if r["klass"] in (0, 4, 5):
-            assert abs(got["max_re"][q] - r["max_re"]) <= TOL_EIG, (q, got["max_re"][q], r["max_re"])
-            assert abs(got["min_zeta"][q] - r["min_zeta"]) <= TOL_EIG, (q, got["min_zeta"][q], r["min_zeta"])
+            assert abs(got["max_re"][q] - r["max_re"]) <= tol_eig, (where, got["max_re"][q], r["max_re"])
+            assert abs(got["min_zeta"][q] - r["min_zeta"]) <= tol_eig, (where, got["min_zeta"][q], r["min_zeta"])
         if nb and r.get("Vm") is not None and r["klass"] in (0, 3, 4, 5):
             vm = got["Vm"][q * nb:(q + 1) * nb]
             va = got["Va"][q * nb:(q + 1) * nb]
-            assert np.abs(vm - np.asarray(r["Vm"])).max() <= TOL_V
-            assert np.abs(va - np.asarray(r["Va"])).max() <= TOL_V
-    assert guard <= max_guard, f"{guard} guard-band class differences"
+            assert np.abs(vm - np.asarray(r["Vm"])).max() <= TOL_V, where
+            assert np.abs(va - np.asarray(r["Va"])).max() <= TOL_V, where
+    print(f"[parity] {label}: {len(refs)} scenarios, 0 class mismatches, {guard} in the guard band")
     return guard
 
 
@@ -176,7 +180,7 @@ def test_small_network_every_scenario_vs_oracle(ctx):
     ej = np.concatenate([[-1], -np.ones(E, np.int32), jj]).astype(np.int32)
     got = _run(ctx, nid, 0, ei, ej, n_bus=net.n_bus)
     refs = pipeline.evaluate_many(net, [(0, int(a), int(b)) for a, b in zip(ei, ej)])
-    _compare(got, refs, nb=net.n_bus, max_guard=2)
+    _compare(got, refs, nb=net.n_bus, label="14-bus all N-1 and N-2")
     ctx.unload_network(nid)
 
 
@@ -186,7 +190,7 @@ def test_case118_n1_vs_golden(ctx, net118):
     g = _gold("case118_n1.json")
     refs = g["scenarios"]
     got = _run(ctx, nid, 0, [r["i"] for r in refs], [r["j"] for r in refs], n_bus=net.n_bus)
-    _compare(got, refs, nb=net.n_bus, max_guard=1)
+    _compare(got, refs, nb=net.n_bus, label="118-bus N-1")
 
 
 def test_case118_pairs_vs_golden(ctx, net118):
@@ -195,7 +199,7 @@ def test_case118_pairs_vs_golden(ctx, net118):
     for lv in (0, 1):
         sub = [r for r in refs if r["level"] == lv]
         got = _run(ctx, nid, lv, [r["i"] for r in sub], [r["j"] for r in sub])
-        _compare(got, sub, max_guard=2)
+        _compare(got, sub, label=f"118-bus pair sample, level {lv}")
 
 
 def test_full_size_batch_sampled(ctx, net118):
@@ -216,7 +220,7 @@ def test_full_size_batch_sampled(ctx, net118):
     index = {(int(a), int(b)): q for q, (a, b) in enumerate(zip(ii, jj))}
     pos = [index[(r["i"], r["j"])] for r in refs]
     sub = {k: v[pos] for k, v in got.items()}
-    _compare(sub, refs, max_guard=2)
+    _compare(sub, refs, label="118-bus full level 1, sampled")
     k = got["klass"]
     assert np.all(k <= 6)
     assert np.all(got["severe"] == (k != 0))
@@ -298,7 +302,12 @@ def test_base_case_secure_and_edges(ctx, net118):
 
 
 # ------------------------------------------------------------ mixed precision form --
-TOL_EIG_MIXED = 2e-3     # FP32 eigenvalue error bound outside the guard band (5e-3)
+# The mixed form refines the decisive eigenvalues in FP64 (two-sided Rayleigh quotient
+# with the FP64 state matrix), so it is held to the FP64 tolerance.  Networks whose
+# Hessenberg matrix exceeds one CTA's shared memory (300 buses) take the FP32 screen in
+# global memory without that refinement: FP32 error bound outside the guard band.
+TOL_EIG_MIXED = TOL_EIG
+TOL_EIG_INLINE = 2e-3
 
 
 @pytest.fixture(scope="module")
@@ -312,28 +321,16 @@ def mixed118():
     c.close()
 
 
-def test_mixed_form_classes_exact_vs_golden(mixed118):
-    """FP32 eigen screen with FP64 re-runs in the guard band: classes equal the
-    oracle's, the OPF outputs are FP64 (same tolerances), the eigen statistics
-    carry the stated FP32 error."""
+def test_mixed_form_vs_golden(mixed118):
+    """FP32 eigen screen with FP64 refinement of the decisive eigenvalues and FP64
+    re-runs in the guard band: every record as in the FP64 form's comparison."""
     c, net, nid = mixed118
     for name in ("case118_n1.json", "case118_pairs.json"):
         refs = _gold(name)["scenarios"]
         for lv in sorted({r["level"] for r in refs}):
             sub = [r for r in refs if r["level"] == lv]
             got = _run(c, nid, lv, [r["i"] for r in sub], [r["j"] for r in sub])
-            guard = 0
-            for q, r in enumerate(sub):
-                if int(got["klass"][q]) != r["klass"]:
-                    assert _guard(r), (name, q, r["i"], r["j"], int(got["klass"][q]), r["klass"])
-                    guard += 1
-                    continue
-                if r["klass"] in (0, 3, 4, 5):
-                    assert abs(got["cost"][q] - r["cost"]) <= TOL_COST * abs(r["cost"])
-                if r["klass"] in (0, 4, 5):
-                    assert abs(got["max_re"][q] - r["max_re"]) <= TOL_EIG_MIXED
-                    assert abs(got["min_zeta"][q] - r["min_zeta"]) <= TOL_EIG_MIXED
-            assert guard <= 2
+            _compare(got, sub, tol_eig=TOL_EIG_MIXED, label=f"mixed {name} level {lv}")
 
 
 def test_mixed_equals_fp64_classes_full_level(ctx, net118, mixed118):
@@ -352,9 +349,12 @@ def test_mixed_equals_fp64_classes_full_level(ctx, net118, mixed118):
     ctx.sync()
     c.sync()
     np.testing.assert_array_equal(a["klass"].cpu().numpy(), b["klass"].cpu().numpy())
-    ok = (a["klass"] == 0).cpu().numpy()
-    d = np.abs(a["max_re"].cpu().numpy()[ok] - b["max_re"].cpu().numpy()[ok])
-    assert d.max() <= TOL_EIG_MIXED
+    np.testing.assert_array_equal(a["opf_iters"].cpu().numpy(), b["opf_iters"].cpu().numpy())
+    np.testing.assert_array_equal(a["cost"].cpu().numpy(), b["cost"].cpu().numpy())
+    ok = np.isin(a["klass"].cpu().numpy(), (0, 4, 5))
+    for k in ("max_re", "min_zeta"):
+        d = np.abs(a[k].cpu().numpy()[ok] - b[k].cpu().numpy()[ok])
+        assert d.max() <= TOL_EIG_MIXED, (k, d.max())
     assert c.eigen_reruns() >= 0
 
 
@@ -378,8 +378,8 @@ def test_mixed_form_inline_path_on_a_300_bus_network():
     np.testing.assert_array_equal(a["cost"], b["cost"])
     ok = np.isfinite(a["max_re"])
     assert ok.any()
-    assert np.max(np.abs(a["max_re"][ok] - b["max_re"][ok])) <= TOL_EIG_MIXED
-    assert np.max(np.abs(a["min_zeta"][ok] - b["min_zeta"][ok])) <= TOL_EIG_MIXED
+    assert np.max(np.abs(a["max_re"][ok] - b["max_re"][ok])) <= TOL_EIG_INLINE
+    assert np.max(np.abs(a["min_zeta"][ok] - b["min_zeta"][ok])) <= TOL_EIG_INLINE
 
 
 def test_risk_index_batch_equals_single_and_oracle():
