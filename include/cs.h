@@ -161,6 +161,15 @@ cs_status cs_destroy(cs_ctx* ctx);
  * inconsistent sizes or indices, CS_E_BASE_INSECURE when a base case is not
  * secure and opt.require_secure_base is set. */
 cs_status cs_load_network(cs_ctx* ctx, const cs_network_desc* net, int32_t* net_id);
+
+/* The descriptor checks cs_load_network applies, on their own: HOST only, no
+ * context and no device.  CS_OK, or CS_E_ARG with a message naming the first
+ * offending entry (NULL array, sizes, an index out of range or a self loop, a
+ * non-finite load, shunt, impedance, tap, limit, cost or machine constant, a zero
+ * series impedance, a non-positive rating, tap, Pmax or time constant, Vmin <= 0
+ * or Vmin > Vmax, Pmin > Pmax, Qmin > Qmax, c2 < 0, D < 0) written to msg (at most
+ * msg_len bytes with its terminating zero; msg may be NULL). */
+cs_status cs_check_network(const cs_network_desc* net, char* msg, int32_t msg_len);
 cs_status cs_unload_network(cs_ctx* ctx, int32_t net_id);
 
 /* Sizes of a loaded network and of its symbolic analysis (Section II-A step 1),
@@ -321,7 +330,11 @@ cs_status cs_risk_index_batch(cs_ctx* ctx, int32_t net_id, int32_t level, const 
  * The array's address is looked up on the first call for a device, which
  * should come before any stream capture on that device.  All calls in the
  * process share the array, so they are serialised by a process-wide lock;
- * each returns after its stream has drained.  Blocking; HOST lambda, R_out. */
+ * each returns after its stream has drained.  It is ordered after the
+ * evaluations issued before it by device-side waits on their workspaces'
+ * completion events (no device-wide synchronisation) and holds the context lock
+ * only to enqueue, so the serving scheduler keeps running while it waits; the
+ * network cannot be unloaded during the call.  Blocking; HOST lambda, R_out. */
 cs_status cs_risk_index_static(cs_ctx* ctx, int32_t net_id, int32_t level, const double* lambda,
                                int32_t mode, double* R_out, int64_t* n_missing);
 

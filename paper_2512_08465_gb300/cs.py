@@ -33,7 +33,7 @@ EXPORTS = ("cs_default_options", "cs_create", "cs_destroy", "cs_load_network", "
            "cs_last_launch_count", "cs_set_timing", "cs_kernel_times", "cs_alu_peak", "cs_eigen_reruns",
            "cs_risk_index_static", "cs_network_stats", "cs_serving_stats", "cs_risk_index_batch",
            "cs_evaluate_device_n3", "cs_enumerate_triples_device", "cs_risk_index_pair_freq",
-           "cs_symbolic_pattern")
+           "cs_symbolic_pattern", "cs_check_network")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -78,6 +78,51 @@ class CSError(RuntimeError):
         self.status = status
 
 
+def _network_desc(net):
+    """cs_network_desc of a ``synth.Network``; the arrays it points to are returned
+    with it and must stay alive while it is used."""
+    arrs = {}
+
+    def d(name, v):
+        a = np.ascontiguousarray(v, dtype=np.float64)
+        arrs[name] = a
+        return a.ctypes.data_as(_dp)
+
+    def i(name, v):
+        a = np.ascontiguousarray(v, dtype=np.int32)
+        arrs[name] = a
+        return a.ctypes.data_as(_ip)
+
+    D = NetworkDesc()
+    D.n_bus, D.n_branch, D.n_gen = net.n_bus, net.n_branch, net.n_gen
+    D.n_levels, D.ref_bus = len(net.levels), int(net.ref_bus)
+    D.base_mva, D.f_hz = float(net.base_mva), float(net.f_hz)
+    for k in ("Vmin", "Vmax", "Gs", "Bs"):
+        setattr(D, k, d(k, getattr(net, k)))
+    D.Pd = d("Pd", np.asarray(net.Pd).reshape(-1))
+    D.Qd = d("Qd", np.asarray(net.Qd).reshape(-1))
+    D.f = i("f", net.f)
+    D.t = i("t", net.t)
+    for k in ("r", "x", "b", "rate", "tap"):
+        setattr(D, k, d(k, getattr(net, k)))
+    D.gbus = i("gbus", net.gbus)
+    for k in ("Pmin", "Pmax", "Qmin", "Qmax", "c2", "c1", "c0", "H", "D", "xd", "xq", "xdp", "Td0p",
+              "Tq0p", "KA", "TA"):
+        setattr(D, k, d(k, getattr(net, k)))
+    return D, arrs
+
+
+def check_network(net) -> None:
+    """cs_check_network: the descriptor checks of cs_load_network, on the host only.
+    Raises CSError (CS_E_ARG) with the library's message for an invalid network."""
+    lib = load_library()
+    D, arrs = _network_desc(net)
+    msg = ctypes.create_string_buffer(256)
+    st = lib.cs_check_network(ctypes.byref(D), msg, len(msg))
+    if st != 0:
+        raise CSError(st, "cs_check_network: " + msg.value.decode())
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -108,6 +153,7 @@ def load_library(build_if_missing: bool = True):
         "cs_risk_index_static": (i32, [P, i32, i32, P, i32, P, ctypes.POINTER(i64)]),
         "cs_network_stats": (i32, [P, i32, P, i32]),
         "cs_symbolic_pattern": (i32, [i32, i32, P, P, i32, P, P, P, i64, P, P]),
+        "cs_check_network": (i32, [ctypes.POINTER(NetworkDesc), ctypes.c_char_p, i32]),
         "cs_serving_stats": (i32, [P, P, i32]),
         "cs_risk_index_batch": (i32, [P, i32, i32, P, i64, i32, P, P]),
         "cs_evaluate_device_n3": (i32, [P, i32, i32, P, P, P, i64, ctypes.POINTER(Result), P]),
@@ -191,34 +237,7 @@ class Context:
     # -------------------------------------------------------------- networks --
     def load_network(self, net) -> int:
         """Copy a ``synth.Network`` (or any object with the same fields) to the device."""
-        arrs = {}
-
-        def d(name, v):
-            a = np.ascontiguousarray(v, dtype=np.float64)
-            arrs[name] = a
-            return a.ctypes.data_as(_dp)
-
-        def i(name, v):
-            a = np.ascontiguousarray(v, dtype=np.int32)
-            arrs[name] = a
-            return a.ctypes.data_as(_ip)
-
-        D = NetworkDesc()
-        D.n_bus, D.n_branch, D.n_gen = net.n_bus, net.n_branch, net.n_gen
-        D.n_levels, D.ref_bus = len(net.levels), int(net.ref_bus)
-        D.base_mva, D.f_hz = float(net.base_mva), float(net.f_hz)
-        for k in ("Vmin", "Vmax", "Gs", "Bs"):
-            setattr(D, k, d(k, getattr(net, k)))
-        D.Pd = d("Pd", np.asarray(net.Pd).reshape(-1))
-        D.Qd = d("Qd", np.asarray(net.Qd).reshape(-1))
-        D.f = i("f", net.f)
-        D.t = i("t", net.t)
-        for k in ("r", "x", "b", "rate", "tap"):
-            setattr(D, k, d(k, getattr(net, k)))
-        D.gbus = i("gbus", net.gbus)
-        for k in ("Pmin", "Pmax", "Qmin", "Qmax", "c2", "c1", "c0", "H", "D", "xd", "xq", "xdp", "Td0p",
-                  "Tq0p", "KA", "TA"):
-            setattr(D, k, d(k, getattr(net, k)))
+        D, arrs = _network_desc(net)
         nid = ctypes.c_int32()
         self._check(self.lib.cs_load_network(self.h, ctypes.byref(D), ctypes.byref(nid)), "cs_load_network")
         return nid.value

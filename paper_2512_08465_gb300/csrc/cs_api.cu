@@ -25,6 +25,7 @@ cs_status cuda_fail(cs_ctx* c, cudaError_t e, const char* where) {
 int64_t default_chunk(const cs_ctx* ctx) { return ctx->opt.chunk > 0 ? ctx->opt.chunk : 16384; }
 
 namespace {
+constexpr int kCounters = 6;      // work counters of one chunk: OPF, then five small-signal kernels
 struct Grids {
     int g_opf, g_dyn;
     size_t per_opf, per_dyn;
@@ -50,8 +51,10 @@ size_t workspace_bytes(const cs_ctx* ctx, const Network& net, int64_t chunk) {
     const int64_t cn = std::max<int64_t>(1, chunk);
     const Grids g = grids(ctx, dn, cn);
     size_t b = std::max(g.per_opf * g.g_opf, g.per_dyn * g.g_dyn) * sizeof(double);
-    b += sizeof(int) * cn + sizeof(double) * (2 * dn.nb + 2 * dn.ng) * cn + sizeof(int) * cn + sizeof(int) * 5;
-    if (split_path(ctx, dn)) b += sizeof(float) * (dyn_hbuf_stride(dn) + dyn_abuf_stride(dn)) * cn;
+    b += sizeof(int) * cn + sizeof(double) * (2 * dn.nb + 2 * dn.ng) * cn + sizeof(int) * cn + sizeof(int) * kCounters;
+    if (split_path(ctx, dn))
+        b += (sizeof(float) * (dyn_hbuf_stride(dn) + dyn_abuf_stride(dn) + dyn_cand_stride()) +
+              sizeof(double) * dyn_a64_stride(dn)) * cn;
     return b;
 }
 
@@ -133,12 +136,14 @@ cs_status csi::evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level
     CS_CUDA(ws.isl.ensure(sizeof(int) * cn));
     CS_CUDA(ws.opfx.ensure(sizeof(double) * nx * cn));
     CS_CUDA(ws.opfst.ensure(sizeof(int) * cn));
-    CS_CUDA(ws.counters.ensure(sizeof(int) * 5));
+    CS_CUDA(ws.counters.ensure(sizeof(int) * kCounters));
     // balanced and packed Hessenberg matrices between the kernels of the FP32 screen
     const bool split = split_path(ctx, dn);
     if (split) {
         CS_CUDA(ws.hbuf.ensure(sizeof(float) * dyn_hbuf_stride(dn) * cn));
         CS_CUDA(ws.abuf.ensure(sizeof(float) * dyn_abuf_stride(dn) * cn));
+        CS_CUDA(ws.a64.ensure(sizeof(double) * dyn_a64_stride(dn) * cn));
+        CS_CUDA(ws.cand.ensure(sizeof(float) * dyn_cand_stride() * cn));
     }
     if (!ctx->err_word.p) {
         CS_CUDA(ctx->err_word.ensure(sizeof(int) * 2));
@@ -162,7 +167,7 @@ cs_status csi::evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level
         a.err = (int*)ctx->err_word.p;
         a.reruns = (int*)ctx->err_word.p + 1;
         OpfOut o{(double*)ws.opfx.p, (int*)ws.opfst.p};
-        CS_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * 5, s));
+        CS_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * kCounters, s));
         auto mark = [&](int kind) -> cudaError_t {     // start event of a timed launch
             if (!ctx->timing) return cudaSuccess;
             while (ctx->ev.size() < 2 * (ctx->ev_used + 1)) {
@@ -192,8 +197,8 @@ cs_status csi::evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level
         int nl = 0;
         CS_CUDA(launch_dyn(dn, a, o, ctx->opt.damping_min, ctx->opt.precision, (double*)ws.scratch.p, per_dyn,
                            std::min<int64_t>(g_dyn, m), split ? (float*)ws.abuf.p : nullptr,
-                           split ? (float*)ws.hbuf.p : nullptr, ctx->sms,
-                           counters + 1, &nl, s));
+                           split ? (float*)ws.hbuf.p : nullptr, split ? (double*)ws.a64.p : nullptr,
+                           split ? (float*)ws.cand.p : nullptr, ctx->sms, counters + 1, &nl, s));
         CS_CUDA(done());
         ctx->launches += 2 + nl;
     }
@@ -303,32 +308,78 @@ cs_status cs_kernel_times(cs_ctx* ctx, double* ms, int64_t* launches) {
     return CS_OK;
 }
 
-cs_status cs_load_network(cs_ctx* ctx, const cs_network_desc* d, int32_t* net_id) {
-    if (!ctx) return CS_E_ARG;
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    if (!d || !net_id) return fail(ctx, CS_E_ARG, "NULL argument");
+}  // extern "C"
+
+namespace {
+// Host-side checks of a network descriptor (no device): sizes, indices, and every
+// value the method needs finite and in range.  Returns an empty string when valid.
+std::string check_desc(const cs_network_desc* d) {
+    if (!d) return "NULL network descriptor";
     const int nb = d->n_bus, nbr = d->n_branch, ng = d->n_gen, nlev = d->n_levels;
-    if (nb <= 0 || nbr < 0 || ng <= 0 || nlev <= 0 || d->ref_bus < 0 || d->ref_bus >= nb || !(d->base_mva > 0) ||
-        !(d->f_hz > 0))
-        return fail(ctx, CS_E_ARG, "invalid sizes");
+    if (nb <= 0 || nbr < 0 || ng <= 0 || nlev <= 0 || d->ref_bus < 0 || d->ref_bus >= nb ||
+        !(d->base_mva > 0) || !std::isfinite(d->base_mva) || !(d->f_hz > 0) || !std::isfinite(d->f_hz))
+        return "invalid sizes, reference bus, base or frequency";
     const void* req[] = {d->Vmin, d->Vmax, d->Gs, d->Bs, d->Pd, d->Qd, d->f, d->t, d->r, d->x, d->b, d->rate,
                          d->tap, d->gbus, d->Pmin, d->Pmax, d->Qmin, d->Qmax, d->c2, d->c1, d->c0, d->H, d->D,
                          d->xd, d->xq, d->xdp, d->Td0p, d->Tq0p, d->KA, d->TA};
     for (const void* p : req)
-        if (!p) return fail(ctx, CS_E_ARG, "NULL array in network descriptor");
-    if ((long long)nbr + ng > 32767) return fail(ctx, CS_E_ARG, "too many outage elements");
+        if (!p) return "NULL array in network descriptor";
+    if ((long long)nbr + ng > 32767) return "too many outage elements";
+    auto fin = [](double v) { return std::isfinite(v); };
+    for (int i = 0; i < nb; ++i) {
+        if (!fin(d->Vmin[i]) || !fin(d->Vmax[i]) || !(d->Vmin[i] > 0) || !(d->Vmin[i] <= d->Vmax[i]))
+            return "bus " + std::to_string(i) + ": voltage bounds not finite or not 0 < Vmin <= Vmax";
+        if (!fin(d->Gs[i]) || !fin(d->Bs[i])) return "bus " + std::to_string(i) + ": shunt not finite";
+    }
+    for (long long q = 0; q < (long long)nlev * nb; ++q)
+        if (!fin(d->Pd[q]) || !fin(d->Qd[q]))
+            return "load level " + std::to_string(q / nb) + ", bus " + std::to_string(q % nb) + ": load not finite";
     for (int k = 0; k < nbr; ++k) {
         if (d->f[k] < 0 || d->f[k] >= nb || d->t[k] < 0 || d->t[k] >= nb || d->f[k] == d->t[k])
-            return fail(ctx, CS_E_ARG, "branch end out of range or self loop");
-        if (!(d->rate[k] > 0) || !(d->tap[k] > 0) || !(std::fabs(d->r[k]) + std::fabs(d->x[k]) > 0))
-            return fail(ctx, CS_E_ARG, "branch rating, tap or impedance invalid");
+            return "branch " + std::to_string(k) + ": end out of range or self loop";
+        if (!fin(d->r[k]) || !fin(d->x[k]) || !fin(d->b[k]) || !(std::fabs(d->r[k]) + std::fabs(d->x[k]) > 0))
+            return "branch " + std::to_string(k) + ": impedance zero or not finite";
+        if (!(d->rate[k] > 0) || !fin(d->rate[k]) || !(d->tap[k] > 0) || !fin(d->tap[k]))
+            return "branch " + std::to_string(k) + ": rating or tap not positive and finite";
     }
     for (int k = 0; k < ng; ++k) {
-        if (d->gbus[k] < 0 || d->gbus[k] >= nb) return fail(ctx, CS_E_ARG, "generator bus out of range");
-        if (!(d->Pmax[k] > 0) || !(d->xdp[k] > 0) || !(d->H[k] > 0) || !(d->Td0p[k] > 0) || !(d->Tq0p[k] > 0) ||
-            !(d->TA[k] > 0) || !(d->KA[k] > 0))
-            return fail(ctx, CS_E_ARG, "generator data invalid");
+        if (d->gbus[k] < 0 || d->gbus[k] >= nb) return "generator " + std::to_string(k) + ": bus out of range";
+        const double v[] = {d->Pmin[k], d->Pmax[k], d->Qmin[k], d->Qmax[k], d->c2[k], d->c1[k], d->c0[k],
+                            d->H[k], d->D[k], d->xd[k], d->xq[k], d->xdp[k], d->Td0p[k], d->Tq0p[k], d->KA[k],
+                            d->TA[k]};
+        for (double x : v)
+            if (!fin(x)) return "generator " + std::to_string(k) + ": a value is not finite";
+        if (!(d->Pmax[k] > 0) || !(d->Pmin[k] <= d->Pmax[k]) || !(d->Qmin[k] <= d->Qmax[k]) || d->c2[k] < 0)
+            return "generator " + std::to_string(k) + ": limits or cost invalid";
+        if (!(d->xdp[k] > 0) || !(d->xd[k] > 0) || !(d->xq[k] > 0) || !(d->H[k] > 0) || d->D[k] < 0 ||
+            !(d->Td0p[k] > 0) || !(d->Tq0p[k] > 0) || !(d->TA[k] > 0) || !(d->KA[k] > 0))
+            return "generator " + std::to_string(k) + ": machine data invalid";
     }
+    return std::string();
+}
+}  // namespace
+
+extern "C" {
+
+cs_status cs_check_network(const cs_network_desc* d, char* msg, int32_t msg_len) {
+    const std::string m = check_desc(d);
+    if (msg && msg_len > 0) {
+        const size_t n = std::min<size_t>(m.size(), (size_t)msg_len - 1);
+        std::memcpy(msg, m.data(), n);
+        msg[n] = '\0';
+    }
+    return m.empty() ? CS_OK : CS_E_ARG;
+}
+
+cs_status cs_load_network(cs_ctx* ctx, const cs_network_desc* d, int32_t* net_id) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (!d || !net_id) return fail(ctx, CS_E_ARG, "NULL argument");
+    {
+        const std::string m = check_desc(d);
+        if (!m.empty()) return fail(ctx, CS_E_ARG, m);
+    }
+    const int nb = d->n_bus, nbr = d->n_branch, ng = d->n_gen, nlev = d->n_levels;
     CS_CUDA(cudaSetDevice(ctx->device));
     std::unique_ptr<Network> net(new Network());
     std::vector<int> f(d->f, d->f + nbr), t(d->t, d->t + nbr);
@@ -507,6 +558,7 @@ cs_status cs_unload_network(cs_ctx* ctx, int32_t net_id) {
     auto it = ctx->nets.find(net_id);
     if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
     if (serve_uses_network(ctx, net_id)) return fail(ctx, CS_E_ARG, "network has queued or running requests");
+    if (it->second->busy > 0) return fail(ctx, CS_E_ARG, "network is in use by a Risk Index call");
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     ctx->nets.erase(it);
@@ -796,8 +848,16 @@ cs_status cs_enumerate_pairs_device(int32_t n_elem, int64_t first, int64_t count
 // looked up once per device, with that device current, on the first call for
 // it; that first call should happen before any stream capture on the device.
 // All calls in the process share the one array per device, so overlapping
-// calls would race on it: the whole call runs under a process-wide lock and
-// returns only after its stream has drained.
+// calls would race on it: a process-wide lock serialises them, and each returns
+// only after its stream has drained.
+//
+// Ordering without a device-wide synchronisation: the library stream waits
+// (on the device) for the completion events of every workspace of the context,
+// i.e. for the evaluations issued before the call, whatever their streams.  The
+// context lock is held only while that is enqueued; the copies and the wait
+// for them run without it, so the serving scheduler keeps retiring and
+// admitting batches meanwhile (the network is marked busy, so it cannot be
+// unloaded under the call).
 constexpr int kStaticRiskMaxElem = 4096;
 constexpr int kStaticRiskDoubles = 2 * kStaticRiskMaxElem + 32;   // + counter, padded
 static __device__ __align__(256) double g_static_risk[kStaticRiskDoubles];
@@ -820,39 +880,68 @@ cudaError_t static_risk_scratch(int device, double** p) {
 }
 }  // namespace
 
+namespace {
+// the library stream waits for every evaluation issued so far on the context's workspaces
+cudaError_t wait_for_evaluations(cs_ctx* ctx, cudaStream_t s) {
+    auto wait = [&](const Workspace& ws) -> cudaError_t {
+        return (ws.used && ws.free) ? cudaStreamWaitEvent(s, ws.free, 0) : cudaSuccess;
+    };
+    cudaError_t e = wait(ctx->direct);
+    if (e == cudaSuccess) e = wait(ctx->direct2);
+    for (auto& sl : ctx->slots)
+        if (e == cudaSuccess) e = wait(sl->ws);
+    return e;
+}
+}  // namespace
+
 cs_status cs_risk_index_static(cs_ctx* ctx, int32_t net_id, int32_t level, const double* lambda, int32_t mode,
                                double* R_out, int64_t* n_missing) {
     if (!ctx) return CS_E_ARG;
     std::lock_guard<std::mutex> glock(g_static_mu);
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    auto it = ctx->nets.find(net_id);
-    if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
-    Network* net = it->second.get();
-    if (level < 0 || level >= net->nlev || !lambda || !R_out || (mode != CS_RISK_EQ3 && mode != CS_RISK_ORDERED))
-        return fail(ctx, CS_E_ARG, "bad level, mode or NULL");
-    const int nE = net->dev.nE;
-    if (nE > kStaticRiskMaxElem)
-        return fail(ctx, CS_E_ARG, "cs_risk_index_static: " + std::to_string(nE) + " outage elements exceed its " +
-                                       std::to_string(kStaticRiskMaxElem) + "-element static scratch; use cs_risk_index");
-    for (int i = 0; i < nE; ++i)
-        if (!(lambda[i] >= std::ldexp(1.0, -30) && lambda[i] <= std::ldexp(1.0, 10)))
-            return fail(ctx, CS_E_ARG, "lambda outside [2^-30, 2^10]");
-    CS_CUDA(cudaSetDevice(ctx->device));
+    Network* net = nullptr;
+    const uint8_t *S1 = nullptr, *S2 = nullptr;
     double* base = nullptr;
-    CS_CUDA(static_risk_scratch(ctx->device, &base));
+    int nE = 0;
+    cudaStream_t s = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        auto it = ctx->nets.find(net_id);
+        if (it == ctx->nets.end()) return fail(ctx, CS_E_UNKNOWN_ID, "unknown network");
+        net = it->second.get();
+        if (level < 0 || level >= net->nlev || !lambda || !R_out || (mode != CS_RISK_EQ3 && mode != CS_RISK_ORDERED))
+            return fail(ctx, CS_E_ARG, "bad level, mode or NULL");
+        nE = net->dev.nE;
+        if (nE > kStaticRiskMaxElem)
+            return fail(ctx, CS_E_ARG, "cs_risk_index_static: " + std::to_string(nE) +
+                                           " outage elements exceed its " + std::to_string(kStaticRiskMaxElem) +
+                                           "-element static scratch; use cs_risk_index");
+        for (int i = 0; i < nE; ++i)
+            if (!(lambda[i] >= std::ldexp(1.0, -30) && lambda[i] <= std::ldexp(1.0, 10)))
+                return fail(ctx, CS_E_ARG, "lambda outside [2^-30, 2^10]");
+        CS_CUDA(cudaSetDevice(ctx->device));
+        CS_CUDA(static_risk_scratch(ctx->device, &base));
+        s = ctx->req_stream;
+        CS_CUDA(wait_for_evaluations(ctx, s));     // tables written by earlier evaluations on any stream
+        S1 = (const uint8_t*)net->sev_n1[level]->p;
+        S2 = (const uint8_t*)net->sev_pairs[level]->p;
+        net->busy++;
+    }
+    // copies, launch and wait without the context lock
     double* dl = base;
     double* dr = base + kStaticRiskMaxElem;
     int64_t* dm = (int64_t*)(base + 2 * kStaticRiskMaxElem);
-    cudaStream_t s = ctx->req_stream;
-    CS_CUDA(cudaDeviceSynchronize());      // tables written by earlier evaluations on any stream
-    CS_CUDA(cudaMemcpyAsync(dl, lambda, sizeof(double) * nE, cudaMemcpyHostToDevice, s));
-    CS_CUDA(cudaMemsetAsync(dm, 0, sizeof(int64_t), s));
-    CS_CUDA(launch_risk(nE, (const uint8_t*)net->sev_n1[level]->p, (const uint8_t*)net->sev_pairs[level]->p, dl,
-                        mode, dr, dm, s));
-    CS_CUDA(cudaMemcpyAsync(R_out, dr, sizeof(double) * nE, cudaMemcpyDeviceToHost, s));
     int64_t miss = 0;
-    CS_CUDA(cudaMemcpyAsync(&miss, dm, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CS_CUDA(cudaStreamSynchronize(s));
+    cudaError_t e = cudaSetDevice(ctx->device);
+    const char* where = "cudaSetDevice";
+    if (e == cudaSuccess) { e = cudaMemcpyAsync(dl, lambda, sizeof(double) * nE, cudaMemcpyHostToDevice, s); where = "copy of lambda"; }
+    if (e == cudaSuccess) { e = cudaMemsetAsync(dm, 0, sizeof(int64_t), s); where = "clear of the missing-pair counter"; }
+    if (e == cudaSuccess) { e = launch_risk(nE, S1, S2, dl, mode, dr, dm, s); where = "risk_kernel launch"; }
+    if (e == cudaSuccess) { e = cudaMemcpyAsync(R_out, dr, sizeof(double) * nE, cudaMemcpyDeviceToHost, s); where = "copy of R"; }
+    if (e == cudaSuccess) { e = cudaMemcpyAsync(&miss, dm, sizeof(int64_t), cudaMemcpyDeviceToHost, s); where = "copy of the count"; }
+    if (e == cudaSuccess) { e = cudaStreamSynchronize(s); where = "cudaStreamSynchronize"; }
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    net->busy--;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, where);
     if (n_missing) *n_missing = miss;
     return CS_OK;
 }
