@@ -68,3 +68,30 @@ def test_static_risk_index_validates_like_the_allocating_one(ctx):
     with pytest.raises(cs.CSError):
         ctx.risk_index_static(nid + 1000, 0, lam)             # unknown network
     ctx.unload_network(nid)
+
+
+def _replicated(net, k):
+    """The same electrical network with every branch split into k identical parallel
+    branches (impedance x k, charging and rating / k), so that it has k times the
+    branch outage elements."""
+    import dataclasses
+    rep = lambda a: np.repeat(a, k)
+    return dataclasses.replace(net, f=rep(net.f), t=rep(net.t), r=rep(net.r) * k, x=rep(net.x) * k,
+                               b=rep(net.b) / k, rate=rep(net.rate) / k, tap=rep(net.tap), kind=rep(net.kind))
+
+
+def test_static_risk_index_rejects_networks_beyond_its_scratch(ctx):
+    """More than 4096 outage elements do not fit the static scratch: CS_E_ARG with a
+    message naming the limit, while the allocating entry point still answers."""
+    base = synth.make_network(14, 20, 5, 11, 1, seed=3, levels=(0.5,))
+    net = _replicated(base, 205)                          # 4100 branches + 5 generators
+    assert net.n_elem == 4105
+    nid = ctx.load_network(net)
+    lam = synth.failure_rates(net.n_elem, 3)
+    with pytest.raises(cs.CSError) as err:
+        ctx.risk_index_static(nid, 0, lam)
+    assert "4096" in str(err.value)
+    R, missing = ctx.risk_index(nid, 0, lam)
+    assert R.shape == (net.n_elem,) and missing == net.n_elem * (net.n_elem + 1) // 2
+    assert np.all(R == 0.0)                                # nothing evaluated yet
+    ctx.unload_network(nid)
