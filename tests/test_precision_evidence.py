@@ -1,0 +1,107 @@
+"""Evidence for the precision form: FP32 factors of the interior-point Newton
+systems do not reach the accuracy the OPF needs (CPU only).
+
+The Newton systems are the oracle's own (Section II-B-1, the MIPS reading:
+[M, Jg^T; Jg, 0] at every iterate of two 118-bus scenarios).  Each is solved
+two ways, both with FP64 iterative refinement against the FP64 matrix and a
+power-of-two equilibration (rows and columns scaled by 2^-round(log2 sqrt(max
+|row|))):
+
+* factors in FP64 (LU with partial pivoting) -- the precision the GPU path uses;
+* factors in FP32, refined in FP64 -- the pattern a mixed-precision KKT
+  factorisation would use.
+
+The target is the GPU path's: a componentwise backward error
+max |b - K x| / (|K| |x| + |b|) of at most 1e-13.  FP64 factors reach it on
+nearly every system within three refinement steps; FP32 factors stall
+between 1e-11 and 1 and reach it on none, even with ten steps, because these
+systems have condition numbers far above 1/eps_32 from the first iterations on.
+That is why the OPF keeps FP64 factors and the mixed form lowers the precision
+of the eigen screen instead."""
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+from paper_2512_08465_gb300 import synth
+from oracle import grid, opf
+
+TARGET = 1e-13
+
+
+def _backward_error(K, x, b):
+    r = b - K @ x
+    den = np.abs(K) @ np.abs(x) + np.abs(b)
+    return float(np.max(np.where(den > 0, np.abs(r) / np.where(den > 0, den, 1.0), 0.0)))
+
+
+def _refined(K, b, dtype, steps):
+    """Equilibrated LU in `dtype`, then FP64 refinement; backward error after each step."""
+    s = 2.0 ** (-np.round(np.log2(np.sqrt(np.maximum(np.abs(K).max(1), 1e-300)))))
+    lu = sl.lu_factor((s[:, None] * K * s[None, :]).astype(dtype))
+    x = np.zeros_like(b)
+    r = b.copy()
+    errs = []
+    for _ in range(steps):
+        x = x + s * sl.lu_solve(lu, (s * r).astype(dtype)).astype(np.float64)
+        r = b - K @ x
+        errs.append(_backward_error(K, x, b))
+        if errs[-1] <= TARGET:
+            break
+    return errs
+
+
+def _newton_systems(net, level, i, j):
+    """The Newton matrix and right-hand side of every iteration of the oracle's IPM."""
+    sc = grid.make_scenario(net, level, i, j)
+    prob = opf.Problem(net, sc)
+    x = prob.x0()
+    f, df, g, h, Jg, Jh, cache = prob.evaluate(x)
+    gamma, lam = 1.0, np.zeros(prob.neq)
+    z = np.maximum(-h, 1.0)
+    mu = gamma / z
+    Lx = df + Jg.T @ lam + Jh.T @ mu
+    for _ in range(opf.MAX_IT):
+        zinv = 1.0 / z
+        M = prob.hessian(cache, lam, mu) + Jh.T @ ((mu * zinv)[:, None] * Jh)
+        N = Lx + Jh.T @ (zinv * (mu * h + gamma))
+        K = np.block([[M, Jg.T], [Jg, np.zeros((prob.neq, prob.neq))]])
+        b = -np.concatenate([N, g])
+        yield K, b
+        sol = np.linalg.solve(K, b)
+        dx, dlam = sol[:prob.nx], sol[prob.nx:]
+        dz = -h - z - Jh @ dx
+        dmu = -mu + zinv * (gamma - mu * dz)
+        k = dz < 0
+        ap = min(opf.XI * np.min(-z[k] / dz[k]), 1.0) if k.any() else 1.0
+        k = dmu < 0
+        ad = min(opf.XI * np.min(-mu[k] / dmu[k]), 1.0) if k.any() else 1.0
+        x, z, lam, mu = x + ap * dx, z + ap * dz, lam + ad * dlam, mu + ad * dmu
+        gamma = opf.SIGMA * float(z @ mu) / prob.niq
+        f_prev = f
+        f, df, g, h, Jg, Jh, cache = prob.evaluate(x)
+        Lx = df + Jg.T @ lam + Jh.T @ mu
+        if all(c < opf.TOL for c in opf.conditions(prob, x, z, lam, mu, f, f_prev, g, h, Lx)):
+            return
+
+
+@pytest.mark.slow
+def test_fp32_factors_miss_the_backward_error_target():
+    net = synth.case118()
+    n = ok64 = ok32 = 0
+    steps64 = []
+    best32 = []
+    for (lv, i, j) in ((0, -1, -1), (1, 100, 200)):
+        for K, b in _newton_systems(net, lv, i, j):
+            e64 = _refined(K, b, np.float64, 3)
+            e32 = _refined(K, b, np.float32, 10)
+            n += 1
+            ok64 += e64[-1] <= TARGET
+            ok32 += e32[-1] <= TARGET
+            steps64.append(len(e64))
+            best32.append(min(e32))
+    print(f"[precision] {n} Newton systems: FP64 factors reach {TARGET:g} on {ok64} "
+          f"(mean {np.mean(steps64):.2f} refinement steps), FP32 factors on {ok32}; "
+          f"FP32 best backward error median {np.median(best32):.1e}")
+    assert n >= 60
+    assert ok64 >= 0.9 * n
+    assert ok32 <= 0.05 * n
