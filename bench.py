@@ -56,17 +56,61 @@ def _oracle_sample(net, n, seed):
     return [(int(q % 2), int(ii[k]), int(jj[k])) for q, k in enumerate(ks)]
 
 
-def cpu_baseline(net, n=256, seed=1234):
-    """The oracle as it stands on a bounded sample of the workload, all host cores."""
+def cpu_baseline(net, n=256, seed=1234, keep=False):
+    """The oracle as it stands on a bounded sample of the workload, all host cores.
+    keep: also return the oracle's records of that sample and of the N-1 branch set at
+    the 70 % level (evaluated after the timing), for the per-output error table."""
     from oracle import pipeline
     cores = os.cpu_count() or 1
     sample = _oracle_sample(net, n, seed)
     t0 = time.perf_counter()
-    pipeline.evaluate_many(net, sample, cores)
+    recs = pipeline.evaluate_many(net, sample, cores)
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": cores, "per_core": n / dt / cores, "kind": "oracle",
-            "sample": f"{n} N-2 scenarios drawn uniformly (seed {seed}) from the 57,360 of the workload, "
-                      f"half per load level; {dt:.1f} s wall on {cores} processes"}
+    out = {"value": n / dt, "unit": UNIT, "cores": cores, "per_core": n / dt / cores, "kind": "oracle",
+           "sample": f"{n} N-2 scenarios drawn uniformly (seed {seed}) from the 57,360 of the workload, "
+                     f"half per load level; {dt:.1f} s wall on {cores} processes"}
+    if not keep:
+        return out
+    n1 = [(0, e, -1) for e in range(net.n_branch)]
+    return out, {"pairs": (sample, recs), "n1": (n1, pipeline.evaluate_many(net, n1, cores))}
+
+
+def _error_table(refs, got, nb):
+    """Error of GPU records against the oracle's records of the same scenarios, per output:
+    max and 99th percentile of the absolute and of the relative error of Vm and Va (every
+    bus of every scenario whose OPF converged), OPF cost, max Re and min damping ratio
+    (scenarios whose eigen screen ran), and the count of differing classes."""
+    import numpy as np
+    cols = {k: [] for k in ("Vm", "Va", "cost", "max_re", "min_zeta")}
+    refv = {k: [] for k in cols}
+    mism = 0
+    for q, r in enumerate(refs):
+        if int(got["klass"][q]) != int(r["klass"]):
+            mism += 1
+            continue
+        if r.get("converged") and r.get("Vm") is not None:
+            for k in ("Vm", "Va"):
+                ref = np.asarray(r[k], dtype=np.float64)
+                cols[k].append(got[k][q * nb:(q + 1) * nb] - ref)
+                refv[k].append(ref)
+            cols["cost"].append(np.array([got["cost"][q] - r["cost"]]))
+            refv["cost"].append(np.array([r["cost"]]))
+        if r["klass"] in (0, 4, 5):
+            for k in ("max_re", "min_zeta"):
+                cols[k].append(np.array([got[k][q] - r[k]]))
+                refv[k].append(np.array([r[k]]))
+    table = {"class_mismatches": mism, "scenarios": len(refs)}
+    for k in cols:
+        if not cols[k]:
+            table[k] = None
+            continue
+        d = np.abs(np.concatenate(cols[k]))
+        ref = np.abs(np.concatenate(refv[k]))
+        rel = d[ref > 0] / ref[ref > 0]
+        table[k] = {"n": int(d.size), "max_abs": float(d.max()), "p99_abs": float(np.percentile(d, 99)),
+                    "max_rel": float(rel.max()) if rel.size else None,
+                    "p99_rel": float(np.percentile(rel, 99)) if rel.size else None}
+    return table
 
 
 def run_reference(args):
@@ -146,25 +190,6 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def fp64_peak_measured(torch, dev):
-    """Measured FP64 peak: best of 3 float64 GEMMs 4096^3 (cuBLAS), TFLOP/s."""
-    n = 4096
-    a = torch.randn(n, n, dtype=torch.float64, device=dev)
-    b = torch.randn(n, n, dtype=torch.float64, device=dev)
-    torch.mm(a, b)
-    torch.cuda.synchronize()
-    best = 1e9
-    for _ in range(3):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        torch.mm(a, b)
-        e1.record()
-        torch.cuda.synchronize()
-        best = min(best, e0.elapsed_time(e1) / 1e3)
-    del a, b
-    return 2.0 * n ** 3 / best / 1e12
-
-
 def _algorithmic_flops(net, res_lv, E, mixed_reruns=0):
     """Algorithmic FP64/FP32 work of the small-signal kernel for one step:
     10 n^3 flops per converged scenario (Golub & Van Loan's count for
@@ -196,40 +221,80 @@ def _opf_flops_per_iter(st):
     return factor + solve + residual + nbr * 1200
 
 
+# DRAM traffic of a kernel group per processed unit, from the committed ncu summary of
+# its dominant kernel: a line "traffic: <group> <sha16 of the kernel source> <bytes per
+# unit>" in profiles/.  Reported only while the kernel source still has that hash (a
+# capture of an older kernel is not the traffic of this build).
+_TRAFFIC_SRC = {"opf": "paper_2512_08465_gb300/csrc/k_opf.cu", "dyn": "paper_2512_08465_gb300/csrc/k_dyn.cu"}
+
+
+def _captured_traffic(group, units_per_launch):
+    import glob
+    import hashlib
+    import re
+    src = os.path.join(ROOT, _TRAFFIC_SRC[group])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    found = None
+    for fn in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for m in re.finditer(r"^traffic: (\w+) ([0-9a-f]{16}) ([0-9.eE+]+)\s*$", open(fn).read(), re.M):
+            if m.group(1) == group:
+                found = (m.group(2), float(m.group(3)), os.path.basename(fn))
+    if found is None:
+        return {"traffic": None, "traffic_source": "no ncu capture of this kernel group in profiles/"}
+    if found[0] != sha:
+        return {"traffic": None, "traffic_source": f"profiles/{found[2]}: captured on an earlier version of "
+                                                   f"{_TRAFFIC_SRC[group]} (source hash {found[0]}, now {sha})"}
+    return {"traffic": found[1] * units_per_launch,
+            "traffic_source": f"profiles/{found[2]}: ncu dram__bytes_read.sum + dram__bytes_write.sum per "
+                              f"unit ({found[1]:.4g} B) x the units of an average launch of this step"}
+
+
 def run_ours(args):
     import numpy as np
     rank, world, local = _env_rank()
-    cpu = None
+    cpu = recs = None
     if rank == 0 and not args.no_cpu_baseline:
         from paper_2512_08465_gb300 import synth as _s
-        cpu = cpu_baseline(_s.case118(), n=args.cpu_sample)       # spawned workers, before any GPU call
+        cpu, recs = cpu_baseline(_s.case118(), n=args.cpu_sample, keep=True)   # spawned workers, before any GPU call
     import torch
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_2512_08465_gb300 import cs, synth
-    net = synth.case118(seed=118 + rank)
+    from paper_2512_08465_gb300 import cs, shard, synth
+    net = synth.case118()                                 # one network, its scenarios sharded over the ranks
     E = net.n_elem
     npair = E * (E - 1) // 2
     lam = synth.failure_rates(E, 2512)
+    lam_d = torch.as_tensor(lam, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    # this rank's contiguous block of the pairs and of the single outages of each level
+    p0, pc = shard.pair_block(rank, world, npair)
+    s0, sc_ = shard.pair_block(rank, world, E)
 
     def make(prec, **opt):
         ctx = cs.Context(device=local, precision=prec, **opt)
         nid = ctx.load_network(net)
         return ctx, nid
 
-    ei = torch.empty(npair, dtype=torch.int32, device=dev)
-    ej = torch.empty(npair, dtype=torch.int32, device=dev)
-    cs.enumerate_pairs_device(E, 0, npair, ei, ej)
-    n1i = torch.arange(E, dtype=torch.int32, device=dev)
-    n1j = torch.full((E,), -1, dtype=torch.int32, device=dev)
+    ei_all = torch.empty(npair, dtype=torch.int32, device=dev)
+    ej_all = torch.empty(npair, dtype=torch.int32, device=dev)
+    cs.enumerate_pairs_device(E, 0, npair, ei_all, ej_all)
+    ei, ej = ei_all[p0:p0 + pc], ej_all[p0:p0 + pc]
+    n1i = torch.arange(s0, s0 + sc_, dtype=torch.int32, device=dev)
+    n1j = torch.full((sc_,), -1, dtype=torch.int32, device=dev)
+    # severity tables of both levels in one buffer: [S1 (E) | S2 (npair)] per level; after
+    # each rank fills its block, one element-wise MIN over the ranks merges them (255 = not
+    # evaluated), and the exact Risk Index of the merged tables is the single-rank one
+    flat = torch.empty(2 * (E + npair), dtype=torch.uint8, device=dev)
+    tabs = {lv: (flat[lv * (E + npair):lv * (E + npair) + E], flat[lv * (E + npair) + E:(lv + 1) * (E + npair)])
+            for lv in (0, 1)}
+    R = {lv: torch.empty(E, dtype=torch.float64, device=dev) for lv in (0, 1)}
 
     def measure(ctx, nid, warmup, steps, clocks=False, main=False):
-        outs = {lv: (ctx.alloc_results(npair, dev, main_island=main), ctx.alloc_results(E, dev, main_island=main))
+        outs = {lv: (ctx.alloc_results(pc, dev, main_island=main), ctx.alloc_results(sc_, dev, main_island=main))
                 for lv in (0, 1)}
         launches = [0]
 
@@ -239,8 +304,13 @@ def run_ours(args):
                 launches[0] += ctx.last_launch_count()
                 ctx.evaluate_device(nid, lv, n1i, n1j, outs[lv][1], stream)
                 launches[0] += ctx.last_launch_count()
+            flat.fill_(shard.MISSING)
             for lv in (0, 1):
-                ctx.risk_index(nid, lv, lam, cs.RISK_ORDERED)
+                tabs[lv][1][p0:p0 + pc].copy_(outs[lv][0]["severe"])
+                tabs[lv][0][s0:s0 + sc_].copy_(outs[lv][1]["severe"])
+            shard.merge_severity_device(flat)
+            for lv in (0, 1):
+                cs.risk_reduce_device(E, tabs[lv][0], tabs[lv][1], lam_d, R[lv], cs.RISK_ORDERED, stream)
                 launches[0] += 1
 
         for _ in range(warmup):
@@ -272,8 +342,7 @@ def run_ours(args):
         kms, kcnt = ctx.kernel_times()
         ctx.set_timing(False)
         ms = sum(step_ms) / len(step_ms)
-        from paper_2512_08465_gb300 import shard
-        ms_max = shard.max_over_ranks(ms, device=dev)            # replicas: the slowest rank sets the step
+        ms_max = shard.max_over_ranks(ms, device=dev)            # the slowest rank sets the step
         if world > 1:
             torch.distributed.barrier()
         klass = [outs[lv][0]["klass"].cpu().numpy() for lv in (0, 1)]
@@ -281,12 +350,43 @@ def run_ours(args):
         iters = sum(int(outs[lv][q]["opf_iters"].to(torch.int64).sum().item()) for lv in (0, 1) for q in (0, 1))
         mk = [outs[lv][0]["main_klass"].cpu().numpy() for lv in (0, 1)] if main else None
         shed = [outs[lv][0]["shed_mw"].cpu().numpy() for lv in (0, 1)] if main else None
+        # the merged tables' Risk Index against the context's own (one rank: the same tables)
+        r_same = None
+        if world == 1:
+            r_same = all(np.array_equal(R[lv].cpu().numpy(), ctx.risk_index(nid, lv, lam, cs.RISK_ORDERED)[0])
+                         for lv in (0, 1))
+        rsha = __import__("hashlib").sha256(b"".join(R[lv].cpu().numpy().tobytes() for lv in (0, 1))).hexdigest()[:16]
         return dict(ms=ms_max, wall=wall, kms=kms, kcnt=kcnt, clocks=clk, launches=launches[0],
-                    klass=klass, iters=iters, stats=stats, main_klass=mk, shed=shed)
+                    klass=klass, iters=iters, stats=stats, main_klass=mk, shed=shed, r_same=r_same, r_sha=rsha)
+
+    def accuracy(ctx, nid):
+        """Error table of this form against the oracle's records (rank 0, after the timing)."""
+        out = {}
+        for name, (sc, refs) in recs.items():
+            by_lv = {}
+            for q, (lv, i, j) in enumerate(sc):
+                by_lv.setdefault(lv, []).append(q)
+            got = {}
+            for lv, qs in by_lv.items():
+                ti = torch.as_tensor(np.array([sc[q][1] for q in qs], np.int32), device=dev)
+                tj = torch.as_tensor(np.array([sc[q][2] for q in qs], np.int32), device=dev)
+                o = ctx.alloc_results(len(qs), dev, net.n_bus)
+                ctx.evaluate_device(nid, lv, ti, tj, o, stream)
+                ctx.sync(stream)
+                g = {k: v.cpu().numpy() for k, v in o.items()}
+                for k, v in g.items():
+                    got.setdefault(k, np.zeros(len(sc) * (net.n_bus if k in ("Vm", "Va") else 1), v.dtype))
+                    for m, q in enumerate(qs):
+                        if k in ("Vm", "Va"):
+                            got[k][q * net.n_bus:(q + 1) * net.n_bus] = v[m * net.n_bus:(m + 1) * net.n_bus]
+                        else:
+                            got[k][q] = v[m]
+            out[name] = _error_table(refs, got, net.n_bus)
+        return out
 
     ctx_m, nid_m = make(cs.PREC_MIXED)
     mixed = measure(ctx_m, nid_m, args.warmup, args.steps, clocks=True)
-    reruns = ctx_m.eigen_reruns()
+    reruns_m = ctx_m.eigen_reruns()
     # Monte-Carlo Risk Index (uncertain failure rates): 10,000 seeded rate vectors against the
     # level-0 tables of this step, exact per sample; outside the timed step
     gen = torch.Generator(device=dev).manual_seed(2512)
@@ -311,11 +411,16 @@ def run_ours(args):
     fp64 = measure(ctx_d, nid_d, 1, args.steps)
     same = all(np.array_equal(a, b) for a, b in zip(mixed["klass"], fp64["klass"]))
     # largest deviation of the mixed form's eigen statistics from the FP64 form's (FP32 screen
-    # outside the guard band; scenarios re-run in FP64 agree to rounding)
+    # refined in FP64 outside the guard band; scenarios re-run in FP64 agree to rounding)
     mdev = {}
     for f in ("max_re", "min_zeta"):
         d = [np.abs(a - b)[np.isfinite(a) & np.isfinite(b)] for a, b in zip(mixed["stats"][f], fp64["stats"][f])]
         mdev[f] = float(max((x.max() if x.size else 0.0) for x in d))
+    acc = None
+    if rank == 0 and recs is not None:
+        acc = {"mixed": accuracy(ctx_m, nid_m), "fp64": accuracy(ctx_d, nid_d),
+               "sets": {"n1": f"the {net.n_branch} branch N-1 scenarios at the 70 % level",
+                        "pairs": f"the {args.cpu_sample} sampled N-2 scenarios of the CPU baseline"}}
     ctx_d.close()
     # main-island form: every islanded pair also gets its main island's OPF (classes unchanged)
     ctx_i, nid_i = make(cs.PREC_MIXED, main_island=1)
@@ -324,7 +429,7 @@ def run_ours(args):
     mk = np.concatenate(isl["main_klass"])
     shed = np.concatenate(isl["shed"])
     n_isl = int((mk != 255).sum())
-    main_form = {"value": 2 * npair * world / (isl["ms"] / 1e3), "ms_per_step": isl["ms"], "steps": min(2, args.steps),
+    main_form = {"value": 2 * npair / (isl["ms"] / 1e3), "ms_per_step": isl["ms"], "steps": min(2, args.steps),
                  "kernel_ms_per_step": {k: v / min(2, args.steps) for k, v in isl["kms"].items()},
                  "classes_identical_to_mixed": bool(all(np.array_equal(a, b) for a, b in
                                                         zip(mixed["klass"], isl["klass"]))),
@@ -334,7 +439,7 @@ def run_ours(args):
                                         (5, "ss_poorly_damped"), (6, "eig_fail"))},
                  "shed_mw_mean_over_islanded": float(shed[mk != 255].mean()) if n_isl else None}
 
-    n2 = 2 * npair * world
+    n2 = 2 * npair
     value = n2 / (mixed["ms"] / 1e3)
     kms, kcnt = mixed["kms"], mixed["kcnt"]
     share = {k: v / max(1e-9, sum(kms.values())) for k, v in kms.items()}
@@ -353,88 +458,88 @@ def run_ours(args):
                 "achieved": mixed["iters"] * fl / (kms["opf"] / args.steps / 1e3) / 1e12,
                 "iterations_per_step": mixed["iters"], "flops_per_iteration": fl},
         "dyn": {"kernel": "small-signal kernels (model + balancing; cluster Hessenberg; shared-memory Francis QR; "
-                          "FP64 re-run)", "bound": "alu", "unit": "TFLOP/s", "peak": peak32,
+                          "FP64 refinement; FP64 re-run)", "bound": "alu", "unit": "TFLOP/s", "peak": peak32,
                 "peak_source": "measured in this run: FP32 FMA-chain probe (cs_alu_peak), all SMs",
                 "work": "10 n^3 flops per converged scenario, n = 5 x in-service generators - 1",
                 "achieved": _algorithmic_flops(net, mixed["klass"], E) / (kms["dyn"] / args.steps / 1e3) / 1e12},
     }
-    # DRAM traffic per launch: bytes per scenario from the ncu captures of the same kernels on
-    # the first 2,048 pairs (profiles/*_118bus_2048pairs.md: OPF 44.3 GB for 1,877 OPFs; front
-    # 4.35 GB + cluster Hessenberg 0.73 GB + QR 0.26 GB for 1,742 converged scenarios), scaled
-    # by the scenarios an average launch of this step processes
     n_opf = sum(int(np.sum(k != 1)) for k in mixed["klass"])
     n_conv = sum(int(np.sum((k == 0) | (k == 4) | (k == 5) | (k == 6))) for k in mixed["klass"])
-    per_scen = {"opf": (44.30e9 / 1877, n_opf), "dyn": ((4.354e9 + 0.726e9 + 0.263e9) / 1742, n_conv)}
-    # Both kernel groups changed after those captures (the main-island bus mask), so the
-    # bench line's traffic is null and the captured figure is given beside it, labelled.
+    units = {"opf": n_opf, "dyn": n_conv}
     for k, r in roofs.items():
         launches = max(1.0, kcnt[k] / args.steps)
-        b_per, units = per_scen[k]
-        r.update({"launches_per_step": kcnt[k] / args.steps, "avg_launch_ms": kms[k] / max(1, kcnt[k]),
-                  "traffic": None,
-                  "traffic_at_last_capture": b_per * units / launches,
-                  "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum on 2,048 pairs, scaled "
-                                    "per scenario to an average launch of the step (profiles/); taken before "
-                                    "the kernel's main-island bus mask, hence not the traffic of this build"})
+        r.update({"launches_per_step": kcnt[k] / args.steps, "avg_launch_ms": kms[k] / max(1, kcnt[k])})
+        r.update(_captured_traffic(k, units[k] / launches))
     dominant = max(("opf", "dyn"), key=lambda k: kms[k])
     roof = roofs[dominant]
     roof_other = roofs["dyn" if dominant == "opf" else "opf"]
 
-    # ---- end to end through the host-buffer ABI (mixed form) ----
+    # ---- end to end through the host-buffer ABI (mixed form), this rank's block ----
     ei_h = ei.cpu().numpy()
     ej_h = ej.cpu().numpy()
-    n1i_h = np.arange(E, dtype=np.int32)
-    n1j_h = np.full(E, -1, np.int32)
+    n1i_h = n1i.cpu().numpy()
+    n1j_h = n1j.cpu().numpy()
     chunk = args.request
     lat = []
-    e2e_ms = []
-    for rep in range(1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pend = []
-        for lv in (0, 1):
-            for c0 in range(0, npair, chunk):
-                rid = ctx_m.submit(nid_m, lv, ei_h[c0:c0 + chunk], ej_h[c0:c0 + chunk])
-                pend.append((rid, time.perf_counter()))
-            pend.append((ctx_m.submit(nid_m, lv, n1i_h, n1j_h), time.perf_counter()))
-        for rid, ts in pend:
-            ctx_m.poll(rid, 600_000_000)
-            lat.append(1e3 * (time.perf_counter() - ts))
-        for lv in (0, 1):
-            ctx_m.risk_index(nid_m, lv, lam, cs.RISK_ORDERED)
-        e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_step = sum(e2e_ms) / len(e2e_ms)
-    h2d = 2 * (2 * npair + 2 * E) * 4 + 2 * E * 8
-    d2h = 2 * (npair + E) * (1 + 1 + 1 + 2 + 2 + 8 * 6) + 2 * E * 8   # every per-scenario record field + R
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pend = []
+    for lv in (0, 1):
+        for c0 in range(0, pc, chunk):
+            rid = ctx_m.submit(nid_m, lv, ei_h[c0:c0 + chunk], ej_h[c0:c0 + chunk])
+            pend.append((rid, time.perf_counter()))
+        pend.append((ctx_m.submit(nid_m, lv, n1i_h, n1j_h), time.perf_counter()))
+    for rid, ts in pend:
+        ctx_m.poll(rid, 600_000_000)
+        lat.append(1e3 * (time.perf_counter() - ts))
+    for lv in (0, 1):
+        ctx_m.risk_index(nid_m, lv, lam, cs.RISK_ORDERED)
+    e2e_step = shard.max_over_ranks(1e3 * (time.perf_counter() - t0), device=dev)
+    h2d = 2 * (2 * pc + 2 * sc_) * 4 + 2 * E * 8
+    d2h = 2 * (pc + sc_) * (1 + 1 + 1 + 2 + 2 + 8 * 6) + 2 * E * 8   # every per-scenario record field + R
     lat.sort()
     ctx_m.close()
+    # ---- serving phase: Poisson arrivals over two resident networks, both forms ----
+    serving = None
+    if rank == 0 and not args.no_serve:
+        serving = {name: serve_phase(prec, args.serve_requests, args.serve_burst, args.serve_seed)
+                   for name, prec in (("mixed", cs.PREC_MIXED), ("fp64", cs.PREC_FP64))}
 
     if rank == 0:
         for r in (roof, roof_other):
             r["frac"] = r["achieved"] / r["peak"] if r.get("achieved") is not None else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": mixed["ms"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("FP64 form", "mixed form (FP64 OPF, FP32 eigen screen with "
+            "warmup": args.warmup, "ms_per_step": mixed["ms"], "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("FP64 form", "mixed form (FP64 OPF; FP32 eigen screen with "
+                                                               "FP64 refinement of the decisive eigenvalues and "
                                                                "FP64 re-run in the guard band)"),
                        "form": "mixed", "network_seed": 118, "n2_scenarios_per_step": n2,
-                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}",
-                       "wall_s_timed_region": mixed["wall"], "eigen_fp64_reruns": reruns},
+                       "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"pair range sharded over {world} rank(s), severity tables merged by one "
+                                      f"element-wise MIN all-reduce" if world > 1 else "one GPU",
+                       "wall_s_timed_region": mixed["wall"], "eigen_fp64_reruns_per_step":
+                           (reruns_m / (args.warmup + args.steps)) if args.warmup + args.steps else None},
             "fp64_form": {"value": n2 / (fp64["ms"] / 1e3), "ms_per_step": fp64["ms"],
                           "kernel_ms_per_step": {k: v / args.steps for k, v in fp64["kms"].items()},
                           "classes_identical_to_mixed": bool(same),
                           "mixed_max_abs_dev": mdev},
+            "risk_index": {"merged_tables_equal_context_tables": mixed["r_same"], "sha16": mixed["r_sha"],
+                           "sha16_fp64_form": fp64["r_sha"]},
+            "accuracy_vs_oracle": acc,
             "main_island_form": main_form,
             "roofline": roof,
             "roofline_other": roof_other,
             "risk_index_monte_carlo": mc,
             "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
             "kernel_share": share,
-            "e2e": {"value": 2 * npair * world / (e2e_step / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": n2 / (e2e_step / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step,
                     "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                                   "request_scenarios": chunk}},
+                                   "request_scenarios": chunk, "requests": len(lat),
+                                   "note": "requests submitted together; the serving entry has Poisson arrivals"}},
+            "serving": serving,
             "gpu_launches": mixed["launches"],
             "clocks": mixed["clocks"],
             "cpu_baseline": cpu,
@@ -470,7 +575,7 @@ def run_profile(args):
     ctx.close()
 
 
-def run_serve(args):
+def serve_phase(prec, n_requests, n_burst, seed):
     """Serving form: Poisson arrivals of requests over several resident networks
     (the 118-bus study network, both levels, and a 300-bus network of the same
     construction), each request a log-uniform number in [16, 4096] of random
@@ -478,17 +583,17 @@ def run_serve(args):
     throughput is measured first with a burst of requests submitted at once;
     then, for offered loads of 0.25, 0.5 and 0.9 of it, requests arrive at
     exponential intervals and each one's latency (submit to completed poll,
-    host clock) is recorded.  Mixed form, host-buffer ABI."""
+    host clock) is recorded.  Host-buffer ABI, precision form `prec`."""
     import math
     import numpy as np
     import torch  # noqa: F401  (CUDA context in this process before the library's threads)
     from paper_2512_08465_gb300 import cs, synth
     specs = [("118-bus", synth.case118()), ("300-bus", synth.case_scaled(300, seed=300, vband=(0.85, 1.15)))]
-    ctx = cs.Context(precision=cs.PREC_MIXED)
+    ctx = cs.Context(precision=prec)
     t0 = time.perf_counter()
     ids = [ctx.load_network(net) for _, net in specs]
     load_s = time.perf_counter() - t0
-    rng = np.random.default_rng(args.serve_seed)
+    rng = np.random.default_rng(seed)
     pairs = [synth.all_pairs(net.n_branch) for _, net in specs]
 
     def draw():
@@ -519,18 +624,18 @@ def run_serve(args):
 
     # warm-up, then saturation: every request of a burst submitted at once
     run([draw() for _ in range(4)], [0.0] * 4)
-    burst = [draw() for _ in range(args.serve_burst)]
+    burst = [draw() for _ in range(n_burst)]
     _, sc, wall = run(burst, [0.0] * len(burst))
     sat = sc / wall
     mean_size = float(np.mean([r[2].size for r in burst]))
-    out = {"mode": "serve", "metric": "N-2 scenarios/s and request latency under Poisson load", "unit": "scenarios/s",
+    out = {"form": "mixed" if prec == cs.PREC_MIXED else "fp64",
            "networks": [{"name": n, "n_bus": net.n_bus, "n_branch": net.n_branch, "n_gen": net.n_gen,
                          "levels": len(net.levels), "state_order": 5 * net.n_gen - 1} for n, net in specs],
            "load_networks_s": load_s, "request_sizes": "log-uniform integers in [16, 4096], random branch pairs",
            "saturation": {"requests": len(burst), "scenarios": sc, "wall_s": wall, "scenarios_per_s": sat},
            "rates": []}
     for frac in (0.25, 0.5, 0.9):
-        reqs = [draw() for _ in range(args.serve_requests)]
+        reqs = [draw() for _ in range(n_requests)]
         rate = frac * sat / mean_size                       # requests per second
         arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
         lat, sc, wall = run(reqs, arrivals)
@@ -543,6 +648,16 @@ def run_serve(args):
                                             "max": float(lat_ms[-1])}})
     out["serving_stats"] = ctx.serving_stats()
     ctx.close()
+    return out
+
+
+def run_serve(args):
+    """--serve: the serving phase alone, both forms, with the larger request counts."""
+    from paper_2512_08465_gb300 import cs
+    out = {"mode": "serve", "metric": "N-2 scenarios/s and request latency under Poisson load",
+           "unit": "scenarios/s",
+           "forms": [serve_phase(p, args.serve_requests, args.serve_burst, args.serve_seed)
+                     for p in (cs.PREC_MIXED, cs.PREC_FP64)]}
     print(json.dumps(out))
 
 
@@ -559,8 +674,9 @@ def main():
     ap.add_argument("--fp64", action="store_true", help="--profile: run the FP64 form instead of the mixed one")
     ap.add_argument("--serve", action="store_true",
                     help="serving form: Poisson request arrivals over several networks, p50/p99 latency")
-    ap.add_argument("--serve-requests", type=int, default=40, help="--serve: requests per offered load")
-    ap.add_argument("--serve-burst", type=int, default=30, help="--serve: requests of the saturation burst")
+    ap.add_argument("--serve-requests", type=int, default=24, help="serving phase: requests per offered load")
+    ap.add_argument("--serve-burst", type=int, default=16, help="serving phase: requests of the saturation burst")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving phase of the default run")
     ap.add_argument("--serve-seed", type=int, default=2024)
     ap.add_argument("--profile", type=int, default=0, metavar="N",
                     help="profiling case for ncu: N pairs of the 70 %% level, one warm-up and one launch set, "

@@ -31,9 +31,12 @@ def _worker(rank, world, port, outq):
     for k in range(first, first + count):
         tab[k] = pipeline.evaluate(net, 0, int(ii[k]), int(jj[k]))["severe"]
     merged = shard.merge_severity(tab)
+    # the in-place tensor form the benchmark uses on device tables (here a CPU tensor)
+    flat = torch.from_numpy(tab.copy())
+    shard.merge_severity_device(flat)
     step = shard.max_over_ranks(1.5 + rank)
     if rank == 0:
-        outq.put((merged, step))
+        outq.put((merged, step, flat.numpy().copy()))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -62,7 +65,7 @@ def test_two_ranks_merge_equals_single_rank():
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    merged, step = q.get(timeout=300)
+    merged, step, merged_t = q.get(timeout=300)
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
@@ -72,6 +75,7 @@ def test_two_ranks_merge_equals_single_rank():
     ii, jj = synth.all_pairs(E)
     single = np.array([pipeline.evaluate(net, 0, int(a), int(b))["severe"] for a, b in zip(ii, jj)], np.uint8)
     np.testing.assert_array_equal(merged, single)        # every pair evaluated by exactly one rank
+    np.testing.assert_array_equal(merged_t, single)      # the in-place tensor merge agrees
     S1 = np.array([pipeline.evaluate(net, 0, i, -1)["severe"] for i in range(E)], np.uint8)
     S2 = np.zeros((E, E), np.uint8)
     S2[ii, jj] = merged
