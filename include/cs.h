@@ -61,10 +61,17 @@ enum {
 enum { CS_RISK_EQ3 = 0, CS_RISK_ORDERED = 1 };
 
 /* Precision forms.  FP64: every step in FP64.  MIXED: the eigenvalue screen
- * runs in FP32 and is re-run in FP64 when its decision lies within 5e-3 of a
- * threshold (|max Re| or |min zeta - damping_min|) or the FP32 iteration fails;
- * classes are therefore those of the FP64 form, max_re / min_zeta carry the
- * FP32 error outside the guard band.  The OPF stays in FP64 in both forms. */
+ * (balancing, Hessenberg reduction, QR) runs in FP32; the eigenvalues that can
+ * carry max Re or min zeta are then refined in FP64 (two-sided Rayleigh quotient
+ * with the FP64 state matrix) and decide the class.  The whole screen is re-run
+ * in FP64 when the FP32 iteration fails, a refinement is ill-conditioned, or a
+ * refined statistic lies within 1e-7 of its threshold (|max Re| or |min zeta -
+ * damping_min|).  Classes are those of the FP64 form and max_re / min_zeta
+ * agree with it to about 1e-9.  (Networks whose Hessenberg matrix exceeds one
+ * block's shared memory, state order above ~300, run the FP32 screen in global
+ * memory without the refinement, re-run in FP64 within 5e-3 of a threshold:
+ * FP32 error outside that band.)  The OPF stays in FP64 in both forms: FP32
+ * factors of its Newton systems do not reach the backward-error target. */
 enum { CS_PREC_FP64 = 0, CS_PREC_MIXED = 1 };
 
 typedef struct cs_ctx cs_ctx;
@@ -80,15 +87,22 @@ typedef struct {
     int32_t precision;         /* CS_PREC_FP64 (default) or CS_PREC_MIXED */
     int64_t hbm_budget;        /* device bytes the context may hold (networks, workspaces,
                                   request buffers); 0 = no limit */
-    int32_t serve_slots;       /* batches in flight on the serving path (1..8, default 2) */
-    int32_t batch_cap;         /* scenarios per serving batch (default 16384) */
+    int32_t serve_slots;       /* batches in flight on the serving path (1..8, default 3) */
+    int32_t batch_cap;         /* scenarios per serving batch (default 4096; larger requests are
+                                  split over batches) */
     int32_t main_island;       /* 1: an islanded scenario also gets the OPF of its main island
                                   (see cs_result.main_klass); 0 (default): not run, as in the paper */
+    int32_t autotune;          /* 1: cs_load_network times the launch shapes of the persistent
+                                  kernels (resident OPF blocks per SM, resident small-signal blocks
+                                  per SM) on a sample of the network's N-2 pairs and keeps the
+                                  fastest for that network (cs_network_stats reports it); results
+                                  do not depend on the shape.  0 (default): fixed shapes.  Ignored
+                                  when ctas_per_sm is set. */
 } cs_options;
 
 /* Fills *opt with the defaults (damping_min 0.05, opf_tol 1e-8, opf_max_it 50,
- * FP64 form, no device-memory budget, 2 serving slots, batches of 16384, no
- * main-island OPF). */
+ * FP64 form, no device-memory budget, 3 serving slots, batches of 4096, no
+ * main-island OPF, no autotuning). */
 void cs_default_options(cs_options* opt);
 
 /* Raw network data in structure-of-arrays form, host memory, copied by
@@ -176,7 +190,10 @@ cs_status cs_unload_network(cs_ctx* ctx, int32_t net_id);
  * for work accounting: stats[0..7] = n_bus, n_branch, n_gen, off-diagonal
  * 4x4 blocks of L (and of the bus-level KKT pattern below the diagonal),
  * block updates of one numeric factorisation, elimination-tree levels,
- * largest state-matrix order (5 n_gen - 1), load levels.  The first n_stats
+ * largest state-matrix order (5 n_gen - 1), load levels, then the launch shape
+ * the network's evaluations use: resident OPF blocks per SM, resident
+ * small-signal blocks per SM, and 1 if the autotuner chose them (0 if they are
+ * the defaults or ctas_per_sm).  The first n_stats
  * entries are written (HOST array). */
 cs_status cs_network_stats(cs_ctx* ctx, int32_t net_id, int64_t* stats, int32_t n_stats);
 
@@ -230,10 +247,14 @@ cs_status cs_sync(cs_ctx* ctx, void* stream);
 
 /* Non-blocking submission with HOST buffers (copied before return); the
  * serving path.  A scheduler thread of the context batches queued requests
- * continuously: the oldest request together with every later queued request
- * for the same (net_id, level), in arrival order, up to opt.batch_cap
- * scenarios, on one of opt.serve_slots streams with its own workspace, so
- * batches of different networks run side by side.  A batch starts only when
+ * continuously: whenever one of opt.serve_slots streams (each with its own
+ * workspace) is free, it fills a batch of at most opt.batch_cap scenarios with
+ * the oldest request's next scenarios and those of every later queued request
+ * for the same (net_id, level), in arrival order; a request that does not fit
+ * what is left of the batch is split, the rest waiting for the next free slot.
+ * Batches of different networks run side by side, and a request arriving while
+ * others run starts within about one batch time.  A request completes when its
+ * last slice is back.  A batch starts only when
  * its device footprint fits opt.hbm_budget next to everything the context
  * holds (its chunk shrinks first, then it waits for a running batch).
  * Severities are recorded in the context's severity tables as for

@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
                 ("opf_max_it", ctypes.c_int32), ("require_secure_base", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("hbm_budget", ctypes.c_int64), ("serve_slots", ctypes.c_int32), ("batch_cap", ctypes.c_int32),
-                ("main_island", ctypes.c_int32)]
+                ("main_island", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 
 class NetworkDesc(ctypes.Structure):
@@ -359,9 +359,10 @@ class Context:
 
     def network_stats(self, net_id: int) -> dict:
         """Sizes of a loaded network and its symbolic analysis (cs_network_stats)."""
-        v = np.zeros(8, np.int64)
-        self._check(self.lib.cs_network_stats(self.h, net_id, _ptr(v), 8), "cs_network_stats")
-        keys = ("n_bus", "n_branch", "n_gen", "l_blocks", "block_updates", "levels", "states_max", "levels_load")
+        v = np.zeros(11, np.int64)
+        self._check(self.lib.cs_network_stats(self.h, net_id, _ptr(v), 11), "cs_network_stats")
+        keys = ("n_bus", "n_branch", "n_gen", "l_blocks", "block_updates", "levels", "states_max", "levels_load",
+                "opf_ctas_per_sm", "dyn_ctas_per_sm", "autotuned")
         return dict(zip(keys, (int(x) for x in v)))
 
     # ------------------------------------------------------------ Risk Index --

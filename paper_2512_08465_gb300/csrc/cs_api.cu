@@ -30,10 +30,20 @@ struct Grids {
     int g_opf, g_dyn;
     size_t per_opf, per_dyn;
 };
-Grids grids(const cs_ctx* ctx, const DevNet& dn, int64_t cn) {
-    // persistent kernels sized from occupancy, capped per SM
-    const int cap_opf = ctx->opt.ctas_per_sm > 0 ? ctx->opt.ctas_per_sm : opf_ctas_per_sm();
-    const int cap_dyn = ctx->opt.ctas_per_sm > 0 ? ctx->opt.ctas_per_sm : 2;
+constexpr int kDynCtasDefault = 2;
+int cap_opf_of(const cs_ctx* ctx, const Network& net) {
+    if (ctx->opt.ctas_per_sm > 0) return ctx->opt.ctas_per_sm;
+    return net.opf_cap > 0 ? net.opf_cap : opf_ctas_per_sm();
+}
+int cap_dyn_of(const cs_ctx* ctx, const Network& net) {
+    if (ctx->opt.ctas_per_sm > 0) return ctx->opt.ctas_per_sm;
+    return net.dyn_cap > 0 ? net.dyn_cap : kDynCtasDefault;
+}
+Grids grids(const cs_ctx* ctx, const Network& net, int64_t cn) {
+    // persistent kernels sized from occupancy, capped per SM (the network's tuned shape, if any)
+    const DevNet& dn = net.dev;
+    const int cap_opf = cap_opf_of(ctx, net);
+    const int cap_dyn = cap_dyn_of(ctx, net);
     Grids g;
     g.g_opf = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->sms * cap_opf, cn));
     g.g_dyn = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->sms * cap_dyn, cn));
@@ -49,7 +59,7 @@ bool split_path(const cs_ctx* ctx, const DevNet& dn) {
 size_t workspace_bytes(const cs_ctx* ctx, const Network& net, int64_t chunk) {
     const DevNet& dn = net.dev;
     const int64_t cn = std::max<int64_t>(1, chunk);
-    const Grids g = grids(ctx, dn, cn);
+    const Grids g = grids(ctx, net, cn);
     size_t b = std::max(g.per_opf * g.g_opf, g.per_dyn * g.g_dyn) * sizeof(double);
     b += sizeof(int) * cn + sizeof(double) * (2 * dn.nb + 2 * dn.ng) * cn + sizeof(int) * cn + sizeof(int) * kCounters;
     if (split_path(ctx, dn))
@@ -128,7 +138,7 @@ cs_status csi::evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level
     const int nx = 2 * dn.nb + 2 * dn.ng;
     chunk = std::max<int64_t>(1, chunk);
     const int64_t cn = std::min<int64_t>(n, chunk);
-    const Grids gr = grids(ctx, dn, cn);
+    const Grids gr = grids(ctx, *net, cn);
     const int g_opf = gr.g_opf, g_dyn = gr.g_dyn;
     const size_t per_opf = gr.per_opf, per_dyn = gr.per_dyn;
     const size_t need = std::max(per_opf * g_opf, per_dyn * g_dyn) * sizeof(double);
@@ -220,9 +230,10 @@ void cs_default_options(cs_options* o) {
     o->chunk = 0;
     o->precision = CS_PREC_FP64;
     o->hbm_budget = 0;
-    o->serve_slots = 2;
-    o->batch_cap = 16384;
+    o->serve_slots = 3;
+    o->batch_cap = 4096;
     o->main_island = 0;
+    o->autotune = 0;
 }
 
 cs_status cs_create(const cs_options* opt, cs_ctx** out) {
@@ -357,6 +368,63 @@ std::string check_desc(const cs_network_desc* d) {
     }
     return std::string();
 }
+// Launch-shape autotuner: resident OPF blocks per SM (1..the register limit) and
+// resident small-signal blocks per SM (1, 2, 4), timed with the per-kernel events
+// on a sample of the network's pairs (up to 3 blocks' worth per SM, spread evenly
+// over the pair range, level 0, not recorded).  Shapes are tried in pairs (the two
+// kernel groups are timed separately in each run); the fastest of each group is
+// kept.  Results do not depend on the shape.
+cs_status autotune_network(cs_ctx* ctx, Network* net) {
+    const int64_t nE = net->dev.nE;
+    const int64_t npairs = nE * (nE - 1) / 2;
+    const int64_t ns = std::min<int64_t>(npairs, (int64_t)ctx->sms * 3);
+    if (ns <= 0) return CS_OK;
+    std::vector<int32_t> ids(2 * ns);
+    for (int64_t q = 0, k = 0, i = 0; i < nE && q < ns; ++i)      // pair k = q * npairs / ns
+        for (int64_t j = i + 1; j < nE && q < ns; ++j, ++k)
+            if (k == q * npairs / ns) {
+                ids[q] = (int32_t)i;
+                ids[ns + q] = (int32_t)j;
+                ++q;
+            }
+    DevBuf dids, dres;
+    CS_CUDA(dids.ensure(sizeof(int32_t) * 2 * ns));
+    CS_CUDA(cudaMemcpy(dids.p, ids.data(), sizeof(int32_t) * 2 * ns, cudaMemcpyHostToDevice));
+    CS_CUDA(dres.ensure(result_bytes(ns)));
+    cs_result r{};
+    result_layout((char*)dres.p, ns, &r);
+    const int opf_max = opf_ctas_per_sm();
+    const int dyn_try[3] = {1, 2, 4};
+    const int tries = std::max(opf_max, 3);
+    double best_opf = 1e300, best_dyn = 1e300;
+    int pick_opf = opf_max, pick_dyn = kDynCtasDefault;
+    const bool was_timing = ctx->timing;
+    for (int t = -1; t < tries; ++t) {                 // t = -1: warm-up with the defaults
+        net->opf_cap = (t < 0) ? opf_max : 1 + (t % opf_max);
+        net->dyn_cap = (t < 0) ? kDynCtasDefault : dyn_try[t % 3];
+        ctx->timing = true;
+        ctx->ev_used = 0;
+        cs_status st = evaluate_impl(ctx, ctx->direct, net, 0, (const int32_t*)dids.p, (const int32_t*)dids.p + ns,
+                                     ns, &r, ctx->req_stream, false, ns);
+        ctx->timing = was_timing;
+        if (st != CS_OK) return st;
+        CS_CUDA(cudaStreamSynchronize(ctx->req_stream));
+        double ms[3] = {0.0, 0.0, 0.0};
+        for (size_t q = 0; q < ctx->ev_used; ++q) {
+            float e = 0.f;
+            CS_CUDA(cudaEventElapsedTime(&e, ctx->ev[2 * q], ctx->ev[2 * q + 1]));
+            ms[ctx->ev_kind[q]] += e;
+        }
+        ctx->ev_used = 0;
+        if (t < 0) continue;
+        if (ms[1] < best_opf) { best_opf = ms[1]; pick_opf = net->opf_cap; }
+        if (ms[2] < best_dyn) { best_dyn = ms[2]; pick_dyn = net->dyn_cap; }
+    }
+    net->opf_cap = pick_opf;
+    net->dyn_cap = pick_dyn;
+    return CS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -545,6 +613,10 @@ cs_status cs_load_network(cs_ctx* ctx, const cs_network_desc* d, int32_t* net_id
                 return fail(ctx, CS_E_BASE_INSECURE, "base case of level " + std::to_string(l) + " is not secure");
         }
     }
+    if (ctx->opt.autotune && ctx->opt.ctas_per_sm == 0) {
+        cs_status st = autotune_network(ctx, net.get());
+        if (st != CS_OK) return st;
+    }
     const int id = ctx->next_net++;
     net->id = id;
     ctx->nets[id] = std::move(net);
@@ -573,9 +645,10 @@ cs_status cs_network_stats(cs_ctx* ctx, int32_t net_id, int64_t* stats, int32_t 
     if (!stats || n_stats < 0) return fail(ctx, CS_E_ARG, "NULL stats");
     const DevNet& d = it->second->dev;
     const Symbolic& S = it->second->sym;
-    const int64_t v[8] = {d.nb, d.nbr, d.ng, d.nL, (int64_t)S.upd_a.size(), d.nlevels, 5LL * d.ng - 1,
-                          (int64_t)it->second->nlev};
-    for (int i = 0; i < n_stats && i < 8; ++i) stats[i] = v[i];
+    const int64_t v[11] = {d.nb, d.nbr, d.ng, d.nL, (int64_t)S.upd_a.size(), d.nlevels, 5LL * d.ng - 1,
+                           (int64_t)it->second->nlev, cap_opf_of(ctx, *it->second), cap_dyn_of(ctx, *it->second),
+                           (ctx->opt.ctas_per_sm == 0 && it->second->opf_cap > 0) ? 1 : 0};
+    for (int i = 0; i < n_stats && i < 11; ++i) stats[i] = v[i];
     return CS_OK;
 }
 

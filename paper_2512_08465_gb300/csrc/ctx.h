@@ -42,6 +42,7 @@ struct DevBuf {
 struct Network {
     int id = 0;
     int busy = 0;                     // calls reading its tables outside the context lock
+    int opf_cap = 0, dyn_cap = 0;     // resident blocks per SM chosen by the autotuner (0 = default)
     DevNet dev{};
     DevBuf blob;                      // all static device arrays
     Symbolic sym;
@@ -81,15 +82,26 @@ struct Workspace {
 };
 
 // A request of the serving path: host copies of its element ids, its results
-// once done.  state: 0 queued, 1 running, 2 done, 3 failed (err).
+// once done.  state: 0 queued, 1 running (some of it handed to batches), 2 done,
+// 3 failed (err).  A request is split over batches when it does not fit the one
+// being formed, so a batch never waits for a whole large request.
 struct ServeReq {
     uint64_t id = 0;
     int net_id = 0, level = 0;
     int64_t n = 0;
+    int64_t next = 0;                 // scenarios handed to batches so far (in order)
+    int64_t done_n = 0;               // scenarios whose records are back
     std::vector<int32_t> ei, ej;
     std::vector<char> out;            // records in result_layout order
     int state = 0;
     cs_status err = CS_OK;
+};
+
+// A slice of a request in a batch: records [roff, roff + cnt) of the request sit at
+// [boff, boff + cnt) of the batch.
+struct SliceRef {
+    uint64_t rid;
+    int64_t boff, roff, cnt;
 };
 
 // One batch slot of the scheduler: its own stream, workspace and staging.
@@ -104,7 +116,7 @@ struct Slot {
     size_t h_out_bytes = 0;
     bool busy = false;
     int64_t n = 0;
-    std::vector<std::pair<uint64_t, int64_t>> members;   // (request, offset in the batch)
+    std::vector<SliceRef> members;    // request slices in the batch
     size_t device_bytes() const { return ws.bytes() + d_in.bytes + d_out.bytes; }
     ~Slot() {
         if (h_in) cudaFreeHost(h_in);

@@ -3,11 +3,15 @@
 //
 // cs_submit_contingencies copies a request's element ids and queues it.  A
 // scheduler thread per context keeps up to opt.serve_slots batches in flight,
-// each on its own stream and workspace.  Whenever a slot is free it takes the
-// oldest queued request and packs into the same batch every other queued
-// request for the same (network, level), in arrival order, up to
-// opt.batch_cap scenarios.  Batches of different networks therefore run side
-// by side in different slots.  Before a batch starts, the device bytes it
+// each on its own stream and workspace.  Whenever a slot is free it fills a
+// batch of at most opt.batch_cap scenarios from the queue: the oldest request's
+// next scenarios, then those of every later queued request for the same
+// (network, level), in arrival order.  A request larger than what is left of
+// the batch is split: its first scenarios go into this batch and the rest stay
+// queued for the next free slot, so batches stay small enough to retire often
+// and a request that arrives while others run gets a slot within about one
+// batch time.  A request completes when its last slice is back.  Batches of
+// different networks run side by side in different slots.  Before a batch starts, the device bytes it
 // needs (workspace for its chunk size plus its id and record buffers) are
 // checked against opt.hbm_budget together with everything the context
 // already holds.  If they do not fit, the chunk is halved down to 64
@@ -56,40 +60,54 @@ cudaError_t ensure_pinned(void** p, size_t* have, size_t want) {
     return e;
 }
 
-// Scatter a finished batch into its requests.
+// Scatter a finished batch into its requests' slices.
 void finish_batch(cs_ctx* ctx, Slot& sl, cudaError_t q) {
     cs_result b{};
     result_layout((char*)sl.h_out, sl.n, &b);
-    for (auto& m : sl.members) {
-        auto it = ctx->sreqs.find(m.first);
-        if (it == ctx->sreqs.end()) continue;                // cannot happen: requests stay until polled
+    for (const SliceRef& m : sl.members) {
+        auto it = ctx->sreqs.find(m.rid);
+        if (it == ctx->sreqs.end()) continue;                // failed and already polled
         ServeReq& r = *it->second;
+        if (r.state == 3) continue;
         if (q != cudaSuccess) {
             r.state = 3;
             r.err = CS_E_CUDA;
             continue;
         }
-        const int64_t o = m.second, n = r.n;
-        r.out.resize(result_bytes(n));
+        const int64_t o = m.boff, ro = m.roff, n = m.cnt;
         cs_result d{};
-        result_layout(r.out.data(), n, &d);
-        std::memcpy(d.cost, b.cost + o, 8 * n);
-        std::memcpy(d.max_re, b.max_re + o, 8 * n);
-        std::memcpy(d.min_zeta, b.min_zeta + o, 8 * n);
-        std::memcpy(d.n_islands, b.n_islands + o, 2 * n);
-        std::memcpy(d.opf_iters, b.opf_iters + o, 2 * n);
-        std::memcpy(d.klass, b.klass + o, n);
-        std::memcpy(d.severe, b.severe + o, n);
-        std::memcpy(d.v_margin, b.v_margin + o, 8 * n);
-        std::memcpy(d.max_loading, b.max_loading + o, 8 * n);
-        std::memcpy(d.shed_mw, b.shed_mw + o, 8 * n);
-        std::memcpy(d.main_klass, b.main_klass + o, n);
-        r.state = 2;
-        ctx->stats.completed += 1;
+        result_layout(r.out.data(), r.n, &d);
+        std::memcpy(d.cost + ro, b.cost + o, 8 * n);
+        std::memcpy(d.max_re + ro, b.max_re + o, 8 * n);
+        std::memcpy(d.min_zeta + ro, b.min_zeta + o, 8 * n);
+        std::memcpy(d.n_islands + ro, b.n_islands + o, 2 * n);
+        std::memcpy(d.opf_iters + ro, b.opf_iters + o, 2 * n);
+        std::memcpy(d.klass + ro, b.klass + o, n);
+        std::memcpy(d.severe + ro, b.severe + o, n);
+        std::memcpy(d.v_margin + ro, b.v_margin + o, 8 * n);
+        std::memcpy(d.max_loading + ro, b.max_loading + o, 8 * n);
+        std::memcpy(d.shed_mw + ro, b.shed_mw + o, 8 * n);
+        std::memcpy(d.main_klass + ro, b.main_klass + o, n);
+        r.done_n += n;
+        if (r.done_n == r.n) {
+            r.state = 2;
+            ctx->stats.completed += 1;
+        }
     }
     if (q != cudaSuccess) ctx->err = std::string("serving batch: ") + cudaGetErrorString(q);
     sl.members.clear();
     sl.busy = false;
+}
+
+// Drop from the queue every request that failed or has been handed out in full.
+void prune_queue(cs_ctx* ctx) {
+    ctx->queue.erase(std::remove_if(ctx->queue.begin(), ctx->queue.end(),
+                                    [&](uint64_t q) {
+                                        auto it = ctx->sreqs.find(q);
+                                        return it == ctx->sreqs.end() || it->second->state == 3 ||
+                                               it->second->next >= it->second->n;
+                                    }),
+                     ctx->queue.end());
 }
 
 // Form and launch one batch on slot sl.  Returns false when the oldest
@@ -104,17 +122,28 @@ bool launch_batch(cs_ctx* ctx, Slot& sl) {
         return true;
     }
     Network* net = nit->second.get();
-    // members: the oldest request, then later ones of the same (network, level)
+    // members: the oldest request's next scenarios, then later ones of the same
+    // (network, level), the last one possibly split
     const int64_t cap = ctx->opt.batch_cap;
-    std::vector<uint64_t> take;
+    std::vector<SliceRef> take;
     int64_t total = 0;
     for (uint64_t rid : ctx->queue) {
         ServeReq* r = ctx->sreqs[rid].get();
-        if (r->net_id != r0->net_id || r->level != r0->level) continue;
-        if (!take.empty() && total + r->n > cap) break;
-        take.push_back(rid);
-        total += r->n;
+        if (r->net_id != r0->net_id || r->level != r0->level || r->state == 3) continue;
+        const int64_t cnt = std::min<int64_t>(r->n - r->next, cap - total);
+        if (cnt <= 0) {
+            if (total >= cap) break;
+            continue;
+        }
+        take.push_back(SliceRef{rid, total, r->next, cnt});
+        total += cnt;
+        if (total >= cap) break;
     }
+    auto fail_taken = [&](cs_status st) {
+        for (const SliceRef& m : take) fail_request(ctx, m.rid, st);
+        ctx->stats.nomem += (int64_t)take.size();
+        prune_queue(ctx);
+    };
     // admission: everything else the context holds + this slot's needs
     int64_t chunk = std::min<int64_t>(default_chunk(ctx), std::max<int64_t>(total, 1));
     const size_t io = sizeof(int32_t) * 2 * total + result_bytes(total);
@@ -127,11 +156,7 @@ bool launch_batch(cs_ctx* ctx, Slot& sl) {
                 ctx->stats.admission_waits += 1;
                 return false;
             }
-            for (uint64_t rid : take) fail_request(ctx, rid, CS_E_NOMEM);
-            ctx->stats.nomem += (int64_t)take.size();
-            ctx->queue.erase(std::remove_if(ctx->queue.begin(), ctx->queue.end(),
-                                            [&](uint64_t q) { return std::count(take.begin(), take.end(), q) > 0; }),
-                             ctx->queue.end());
+            fail_taken(CS_E_NOMEM);
             ctx->err = "serving batch does not fit hbm_budget";
             return true;
         }
@@ -150,19 +175,19 @@ bool launch_batch(cs_ctx* ctx, Slot& sl) {
     ok(sl.d_in.ensure(sizeof(int32_t) * 2 * std::max<int64_t>(total, 1)));
     ok(sl.d_out.ensure(result_bytes(std::max<int64_t>(total, 1))));
     if (e != cudaSuccess) {
-        for (uint64_t rid : take) fail_request(ctx, rid, CS_E_NOMEM);
-        ctx->stats.nomem += (int64_t)take.size();
+        fail_taken(CS_E_NOMEM);
+        return true;
     } else {
         int32_t* hi = (int32_t*)sl.h_in;
         sl.members.clear();
-        int64_t off = 0;
-        for (uint64_t rid : take) {
-            ServeReq* r = ctx->sreqs[rid].get();
-            std::memcpy(hi + off, r->ei.data(), sizeof(int32_t) * r->n);
-            std::memcpy(hi + total + off, r->ej.data(), sizeof(int32_t) * r->n);
-            sl.members.emplace_back(rid, off);
+        for (const SliceRef& m : take) {
+            ServeReq* r = ctx->sreqs[m.rid].get();
+            std::memcpy(hi + m.boff, r->ei.data() + m.roff, sizeof(int32_t) * m.cnt);
+            std::memcpy(hi + total + m.boff, r->ej.data() + m.roff, sizeof(int32_t) * m.cnt);
+            sl.members.push_back(m);
+            if (r->out.empty()) r->out.resize(result_bytes(r->n));
             r->state = 1;
-            off += r->n;
+            r->next += m.cnt;
         }
         sl.n = total;
         cs_result dr{};
@@ -179,7 +204,7 @@ bool launch_batch(cs_ctx* ctx, Slot& sl) {
             ok(cudaEventRecord(sl.done, sl.stream));
         }
         if (e != cudaSuccess || st != CS_OK) {
-            for (uint64_t rid : take) fail_request(ctx, rid, st != CS_OK ? st : CS_E_CUDA);
+            for (const SliceRef& m : take) fail_request(ctx, m.rid, st != CS_OK ? st : CS_E_CUDA);
             sl.members.clear();
         } else {
             sl.busy = true;
@@ -187,9 +212,7 @@ bool launch_batch(cs_ctx* ctx, Slot& sl) {
             ctx->stats.merged += (int64_t)take.size() - 1;
         }
     }
-    ctx->queue.erase(std::remove_if(ctx->queue.begin(), ctx->queue.end(),
-                                    [&](uint64_t q) { return std::count(take.begin(), take.end(), q) > 0; }),
-                     ctx->queue.end());
+    prune_queue(ctx);
     ctx->stats.peak_reserved = std::max<int64_t>(ctx->stats.peak_reserved, (int64_t)reserved_bytes(ctx));
     return true;
 }

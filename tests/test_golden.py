@@ -49,3 +49,4 @@ def test_golden_sample_reproduces_from_the_oracle(name, count):
                 assert abs(r[k] - g[k]) <= 1e-9 * max(1.0, abs(g[k])), (name, q, k, r[k], g[k])
         if "Vm" in g:
             assert np.abs(np.asarray(r["Vm"]) - g["Vm"]).max() <= 1e-9
+

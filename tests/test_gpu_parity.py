@@ -469,3 +469,25 @@ def test_severity_indices_match_oracle():
             assert np.isnan(vm[q]) and np.isnan(ld[q]), q
     assert conv > 0
     c.close()
+
+
+def test_autotuned_launch_shape_keeps_every_record():
+    """The autotuner (cs_options.autotune) picks the resident blocks per SM of the
+    persistent kernels for a network; per-scenario results do not depend on them, so
+    every record equals the one of the default shape, bit for bit."""
+    net = synth.case118()
+    ii, jj = synth.all_pairs(net.n_elem)
+    sel = np.random.default_rng(29).choice(ii.size, 600, replace=False)
+    res, stats = {}, {}
+    for tune in (0, 1):
+        c = cs.Context(precision=cs.PREC_MIXED, autotune=tune)
+        nid = c.load_network(net)
+        stats[tune] = c.network_stats(nid)
+        res[tune] = _run(c, nid, 1, ii[sel], jj[sel])
+        c.close()
+    assert stats[0]["autotuned"] == 0 and stats[1]["autotuned"] == 1
+    assert 1 <= stats[1]["opf_ctas_per_sm"] <= 3 and stats[1]["dyn_ctas_per_sm"] in (1, 2, 4)
+    print(f"[autotune] 118-bus: OPF {stats[1]['opf_ctas_per_sm']} and small-signal "
+          f"{stats[1]['dyn_ctas_per_sm']} blocks per SM")
+    for k in res[0]:
+        np.testing.assert_array_equal(res[0][k], res[1][k], err_msg=k)

@@ -143,3 +143,25 @@ def test_main_island_requests_equal_direct_evaluation(nets):
     assert np.all(got["main_klass"][isl] != 255) and np.all(got["main_klass"][~isl] == 255)
     assert np.all(got["shed_mw"][~isl] == 0.0) and np.all(got["shed_mw"][isl] >= 0.0)
     ctx.close()
+
+
+def test_requests_split_over_batches_equal_direct_evaluation(nets):
+    """With a batch cap below the request sizes every request is split over several
+    batches (and slots); each request still completes with all its records, equal bit
+    for bit to direct evaluation, and small requests submitted after a large one are
+    served without waiting for all of it."""
+    small, big = nets
+    ctx = cs.Context(precision=cs.PREC_MIXED, batch_cap=96, serve_slots=3)
+    nid = ctx.load_network(big)
+    rng = np.random.default_rng(19)
+    reqs = _requests(rng, big, 6, lo=150, hi=400) + _requests(rng, big, 4, lo=5, hi=40)
+    rids = [ctx.submit(nid, 1, ei, ej) for ei, ej in reqs]
+    for (ei, ej), rid in zip(reqs, rids):
+        got = ctx.poll(rid, 600_000_000)
+        ref = _direct(ctx, nid, 1, ei, ej)
+        for k in FIELDS:
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
+    st = ctx.serving_stats()
+    total = sum(ei.size for ei, _ in reqs)
+    assert st["completed"] == len(reqs) and st["batches"] >= total // 96
+    ctx.close()
