@@ -43,7 +43,7 @@ def test_binding_loads_and_defaults():
     L = cs.load_library()
     o = cs.default_options()
     assert abs(o.damping_min - 0.05) < 1e-15 and abs(o.opf_tol - 1e-8) < 1e-20 and o.opf_max_it == 50
-    assert o.main_island == 0 and o.serve_slots == 2 and o.batch_cap == 16384
+    assert o.main_island == 0 and o.serve_slots == 3 and o.batch_cap == 4096 and o.autotune == 0
     assert cs.default_options(main_island=1, chunk=4096).main_island == 1
     with pytest.raises(TypeError):
         cs.default_options(main_islnd=1)                 # a misspelt option is an error, not ignored
