@@ -659,6 +659,45 @@ def serve_phase(prec, n_requests, n_burst, seed):
     return out
 
 
+def run_hessenberg(args):
+    """--hessenberg N: the blocked Hessenberg reduction of the eigen screen of large networks
+    (cs_hessenberg_tc: panels on the SIMT pipes, trailing updates on the tensor cores) on a
+    batch of seeded N x N FP32 matrices (N = 2,499 is the state order of a 2000-bus network
+    with 500 generators): time per matrix (CUDA events, inputs resident, after a warm-up),
+    the reduction's algorithmic rate (10/3 N^3 flops per matrix) and the share of that work
+    in the tensor-core products (the trailing updates: 2 N^3 / 3 of the right update plus
+    4 N^3 / 3 of the left one, before the TF32 x 3 split)."""
+    import torch
+    from paper_2512_08465_gb300 import cs
+    n, b = args.hessenberg, args.hessenberg_batch
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(2499)
+    A0 = torch.randn(b, n, n, device=dev, generator=g)
+    ctx = cs.Context()
+    A = A0.clone()
+    ctx.hessenberg_tc(A)                                   # warm-up (workspace, kernels)
+    ctx.sync()
+    times = []
+    for _ in range(args.steps):
+        A.copy_(A0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.hessenberg_tc(A)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ctx.sync()
+    ms = sum(times) / len(times)
+    flops = 10.0 / 3.0 * n ** 3 * b
+    below = torch.tril(A, diagonal=-2).abs().max().item()
+    fro = (torch.linalg.matrix_norm(A.double()) / torch.linalg.matrix_norm(A0.double())).max().item()
+    print(json.dumps({"mode": "hessenberg", "n": n, "batch": b, "steps": args.steps, "ms_per_batch": ms,
+                      "ms_per_matrix": ms / b, "algorithmic_tflops": flops / (ms / 1e3) / 1e12,
+                      "tensor_core_share_of_flops": (2.0 / 3.0 + 4.0 / 3.0) / (10.0 / 3.0),
+                      "max_below_subdiagonal": below, "frobenius_ratio_max": fro}))
+    ctx.close()
+
+
 def run_serve(args):
     """--serve: the serving phase alone, both forms, with the larger request counts."""
     from paper_2512_08465_gb300 import cs
@@ -689,7 +728,13 @@ def main():
     ap.add_argument("--profile", type=int, default=0, metavar="N",
                     help="profiling case for ncu: N pairs of the 70 %% level, one warm-up and one launch set, "
                          "no baseline, no e2e, prints per-kernel times")
+    ap.add_argument("--hessenberg", type=int, default=0, metavar="N",
+                    help="time the tensor-core blocked Hessenberg reduction on N x N matrices")
+    ap.add_argument("--hessenberg-batch", type=int, default=8)
     args = ap.parse_args()
+    if args.hessenberg:
+        run_hessenberg(args)
+        return
     if args.profile:
         run_profile(args)
         return

@@ -340,6 +340,35 @@ cs_status cs_risk_index_pair_freq(cs_ctx* ctx, int32_t net_id, int32_t level, co
 cs_status cs_risk_index_batch(cs_ctx* ctx, int32_t net_id, int32_t level, const double* lambda,
                               int64_t n_samples, int32_t mode, double* R, void* stream);
 
+/* Tensor-core matrix update, the building block of the blocked Hessenberg
+ * reduction that the eigen screen of large networks uses (Section II-B-2: the
+ * eigenvalues of the state matrix, whose reduction to Hessenberg form is, in
+ * blocked form, mostly such updates): C_b += alpha A_b B_b for b = 0..batch-1,
+ * on the tcgen05 tensor cores with every operand split into two TF32 terms and
+ * three products accumulated in FP32 (about FP32 accuracy).  DEVICE arrays,
+ * row-major FP32: A_b = A + b * stride_a (M x K, row stride lda), B_b (K x N,
+ * ldb), C_b (M x N, ldc), read and written in place.  Asynchronous on `stream`.
+ * CS_E_ARG for negative sizes or strides shorter than a row.  A tensor-core wait
+ * that runs out (it never should) leaves C_b unchanged and makes the next cs_sync
+ * of the context return CS_E_TIMEOUT (ctx may be NULL: then the wait is not
+ * reported). */
+cs_status cs_tc_gemm_update(cs_ctx* ctx, int32_t batch, int32_t M, int32_t N, int32_t K, const float* A,
+                            int64_t lda, int64_t stride_a, const float* B, int64_t ldb, int64_t stride_b,
+                            float* C, int64_t ldc, int64_t stride_c, float alpha, void* stream);
+
+/* Reduction of `batch` FP32 matrices to upper Hessenberg form by Householder
+ * similarities (the first step of the eigenvalue screen, Section II-B-2), in the
+ * blocked form for large state matrices: panels of 32 columns reduced with their
+ * reflectors accumulated as V, T and Y = A V T, and the trailing updates
+ * A <- (I - V T V^T)^T (A - Y V^T) on the tensor cores (cs_tc_gemm_update's
+ * TF32 x 3 products).  A: DEVICE, row-major n x n matrices `stride` floats apart,
+ * overwritten by their Hessenberg forms (entries below the subdiagonal set to 0);
+ * the eigenvalues are those of the inputs up to FP32 rounding.  The context keeps
+ * a workspace of about 160 n floats per matrix.  Asynchronous on `stream`;
+ * CS_E_ARG for a bad order, stride or pointer; a tensor-core wait that runs out
+ * makes the next cs_sync return CS_E_TIMEOUT. */
+cs_status cs_hessenberg_tc(cs_ctx* ctx, int32_t batch, int32_t n, float* A, int64_t stride, void* stream);
+
 /* cs_risk_index without any device allocation (the paper has no counterpart:
  * this is a deployment variant of the Eq. 3 reduction).  Same arguments,
  * result and errors as cs_risk_index, bit for bit.  For callers that must not

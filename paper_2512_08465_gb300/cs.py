@@ -33,7 +33,7 @@ EXPORTS = ("cs_default_options", "cs_create", "cs_destroy", "cs_load_network", "
            "cs_last_launch_count", "cs_set_timing", "cs_kernel_times", "cs_alu_peak", "cs_eigen_reruns",
            "cs_risk_index_static", "cs_network_stats", "cs_serving_stats", "cs_risk_index_batch",
            "cs_evaluate_device_n3", "cs_enumerate_triples_device", "cs_risk_index_pair_freq",
-           "cs_symbolic_pattern", "cs_check_network")
+           "cs_symbolic_pattern", "cs_check_network", "cs_tc_gemm_update", "cs_hessenberg_tc")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -154,6 +154,8 @@ def load_library(build_if_missing: bool = True):
         "cs_network_stats": (i32, [P, i32, P, i32]),
         "cs_symbolic_pattern": (i32, [i32, i32, P, P, i32, P, P, P, i64, P, P]),
         "cs_check_network": (i32, [ctypes.POINTER(NetworkDesc), ctypes.c_char_p, i32]),
+        "cs_tc_gemm_update": (i32, [P, i32, i32, i32, i32, P, i64, i64, P, i64, i64, P, i64, i64, ctypes.c_float, P]),
+        "cs_hessenberg_tc": (i32, [P, i32, i32, P, i64, P]),
         "cs_serving_stats": (i32, [P, P, i32]),
         "cs_risk_index_batch": (i32, [P, i32, i32, P, i64, i32, P, P]),
         "cs_evaluate_device_n3": (i32, [P, i32, i32, P, P, P, i64, ctypes.POINTER(Result), P]),
@@ -391,6 +393,16 @@ class Context:
                                           _stream_handle(stream))
         self._check(st, "cs_risk_index_batch")
 
+    def hessenberg_tc(self, A, stream=None):
+        """cs_hessenberg_tc: reduce a float32 device tensor of shape (n, n) or (batch, n, n)
+        (contiguous) to upper Hessenberg form in place."""
+        a3 = A if A.dim() == 3 else A.unsqueeze(0)
+        if A.dtype.itemsize != 4 or not a3.is_contiguous() or a3.shape[1] != a3.shape[2]:
+            raise ValueError("hessenberg_tc wants contiguous square float32 matrices")
+        b, n, _ = a3.shape
+        self._check(self.lib.cs_hessenberg_tc(self.h, b, n, _ptr(a3), n * n, _stream_handle(stream)),
+                    "cs_hessenberg_tc")
+
     def risk_index_static(self, net_id: int, level: int, lam, mode: int = RISK_ORDERED):
         """cs_risk_index_static: the same reduction with its device scratch in a
         static array (no device allocation; at most 4096 outage elements)."""
@@ -400,6 +412,24 @@ class Context:
         st = self.lib.cs_risk_index_static(self.h, net_id, level, _ptr(lam), mode, _ptr(R), ctypes.byref(miss))
         self._check(st, "cs_risk_index_static")
         return R, miss.value
+
+
+def tc_gemm_update(A, B, C, alpha: float = 1.0, ctx=None, stream=None):
+    """cs_tc_gemm_update: C[b] += alpha A[b] @ B[b] on the tensor cores (float32 torch
+    tensors on the device, 2-D or a batch of 3-D, each matrix row-major contiguous)."""
+    lib = load_library()
+    a3, b3, c3 = (x if x.dim() == 3 else x.unsqueeze(0) for x in (A, B, C))
+    batch, M, K = a3.shape
+    N = b3.shape[2]
+    for x in (a3, b3, c3):
+        if x.dtype.itemsize != 4 or not x.is_contiguous():
+            raise ValueError("tc_gemm_update wants contiguous float32 tensors")
+    if b3.shape[:2] != (batch, K) or c3.shape != (batch, M, N):
+        raise ValueError("shape mismatch")
+    st = lib.cs_tc_gemm_update(ctx.h if ctx is not None else None, batch, M, N, K, _ptr(a3), K, M * K, _ptr(b3), N,
+                               K * N, _ptr(c3), N, M * N, float(alpha), _stream_handle(stream))
+    if st != CS_OK:
+        raise CSError(st, "cs_tc_gemm_update")
 
 
 def risk_reduce_device(n_elem: int, S1, S2, lam, R, mode: int = RISK_ORDERED, stream=None):

@@ -69,7 +69,7 @@ size_t workspace_bytes(const cs_ctx* ctx, const Network& net, int64_t chunk) {
 }
 
 size_t reserved_bytes(const cs_ctx* ctx) {
-    size_t b = ctx->direct.bytes() + ctx->direct2.bytes() + ctx->err_word.bytes;
+    size_t b = ctx->direct.bytes() + ctx->direct2.bytes() + ctx->err_word.bytes + ctx->hess_ws.bytes;
     for (auto& kv : ctx->nets) b += kv.second->resident_bytes();
     for (auto& sl : ctx->slots) b += sl->device_bytes();
     return b;
@@ -754,6 +754,7 @@ cs_status cs_sync(cs_ctx* ctx, void* stream) {
             if (e & ERR_BAD_ELEMENT) return fail(ctx, CS_E_ARG, "element id out of range (record marked 255)");
             if (e & ERR_BAD_RATE)
                 return fail(ctx, CS_E_ARG, "failure rate outside [2^-30, 2^10] in a batched Risk Index (entry NaN)");
+            if (e & ERR_TIMEOUT) return fail(ctx, CS_E_TIMEOUT, "a bounded tensor-core wait gave up");
             return fail(ctx, CS_E_NUMERIC, "device error word " + std::to_string(e));
         }
     }
@@ -893,6 +894,43 @@ cs_status cs_risk_reduce_device(int32_t n_elem, const uint8_t* S1, const uint8_t
         return CS_E_ARG;
     cudaError_t e = launch_risk(n_elem, S1, S2, lambda, mode, R, nullptr, (cudaStream_t)stream);
     return e == cudaSuccess ? CS_OK : CS_E_CUDA;
+}
+
+cs_status cs_tc_gemm_update(cs_ctx* ctx, int32_t batch, int32_t M, int32_t N, int32_t K, const float* A,
+                            int64_t lda, int64_t stride_a, const float* B, int64_t ldb, int64_t stride_b,
+                            float* C, int64_t ldc, int64_t stride_c, float alpha, void* stream) {
+    if (batch < 0 || M < 0 || N < 0 || K < 0 || lda < K || ldb < N || ldc < N || stride_a < 0 || stride_b < 0 ||
+        stride_c < 0 || (batch > 0 && M > 0 && N > 0 && K > 0 && (!A || !B || !C)))
+        return CS_E_ARG;
+    int* err = nullptr;
+    if (ctx) {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        if (cudaSetDevice(ctx->device) != cudaSuccess) return CS_E_CUDA;
+        if (!ctx->err_word.p) {
+            CS_CUDA(ctx->err_word.ensure(sizeof(int) * 2));
+            CS_CUDA(cudaMemset(ctx->err_word.p, 0, sizeof(int) * 2));
+        }
+        err = (int*)ctx->err_word.p;
+    }
+    cudaError_t e = launch_tc_gemm(batch, M, N, K, A, lda, stride_a, B, ldb, stride_b, C, ldc, stride_c, alpha, err,
+                                   (cudaStream_t)stream);
+    return e == cudaSuccess ? CS_OK : CS_E_CUDA;
+}
+
+cs_status cs_hessenberg_tc(cs_ctx* ctx, int32_t batch, int32_t n, float* A, int64_t stride, void* stream) {
+    if (!ctx) return CS_E_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (batch < 0 || n < 0 || n > 32767 || stride < (int64_t)n * n || (batch > 0 && n > 0 && !A))
+        return fail(ctx, CS_E_ARG, "bad batch, order, stride or NULL matrix");
+    if (batch == 0 || n < 3) return CS_OK;
+    CS_CUDA(cudaSetDevice(ctx->device));
+    if (!ctx->err_word.p) {
+        CS_CUDA(ctx->err_word.ensure(sizeof(int) * 2));
+        CS_CUDA(cudaMemset(ctx->err_word.p, 0, sizeof(int) * 2));
+    }
+    CS_CUDA(ctx->hess_ws.ensure(sizeof(float) * hess_tc_workspace_floats(n) * (size_t)batch));
+    CS_CUDA(launch_hess_tc(batch, n, A, stride, (float*)ctx->hess_ws.p, (int*)ctx->err_word.p, (cudaStream_t)stream));
+    return CS_OK;
 }
 
 cs_status cs_enumerate_pairs_device(int32_t n_elem, int64_t first, int64_t count, int32_t* ei, int32_t* ej,

@@ -182,10 +182,24 @@ cudaError_t launch_risk(int nE, const uint8_t* S1, const uint8_t* S2, const doub
                         double* R, int64_t* missing, cudaStream_t s, const double* F = nullptr);
 cudaError_t launch_risk_batch(int nE, const uint8_t* S1, const uint8_t* S2, const double* lam, long long ns,
                               int mode, double* R, int* err, int bad_bit, cudaStream_t s);
+// C_b += alpha A_b B_b on the tensor cores (TF32 x 3 terms, FP32 accumulation), row-major
+// FP32, batch strides sA / sB / sC in elements; a bounded wait that gives up sets ERR_TIMEOUT
+cudaError_t launch_tc_gemm(int batch, int M, int N, int K, const float* A, long long lda, long long sA,
+                           const float* B, long long ldb, long long sB, float* C, long long ldc, long long sC,
+                           float alpha, int* err, cudaStream_t s);
+// the same with general element strides: A(m, k) = A[m * am + k * ak], B(k, n) = B[k * bk + n * bn]
+cudaError_t launch_tc_gemm_strided(int batch, int M, int N, int K, const float* A, long long am, long long ak,
+                                   long long sA, const float* B, long long bk, long long bn, long long sB, float* C,
+                                   long long ldc, long long sC, float alpha, int* err, cudaStream_t s);
+// Blocked Householder reduction of `batch` row-major n x n FP32 matrices (stride sA apart)
+// to upper Hessenberg form, in place (entries below the subdiagonal set to zero); the
+// trailing updates on the tensor cores.  ws: hess_tc_workspace_floats(n) floats per matrix.
+size_t hess_tc_workspace_floats(int n);
+cudaError_t launch_hess_tc(int batch, int n, float* A, long long sA, float* ws, int* err, cudaStream_t s);
 cudaError_t launch_enumerate(int nE, int64_t first, int64_t count, int* ei, int* ej,
                              cudaStream_t s);
 cudaError_t launch_enumerate3(int nE, int64_t first, int64_t count, int* ei, int* ej, int* ek,
                               cudaStream_t s);
 
 // error bits of the device error word
-enum { ERR_BAD_ELEMENT = 1, ERR_SCRATCH = 2, ERR_BAD_RATE = 4 };
+enum { ERR_BAD_ELEMENT = 1, ERR_SCRATCH = 2, ERR_BAD_RATE = 4, ERR_TIMEOUT = 8 };

@@ -146,6 +146,7 @@ struct cs_ctx {
     cudaStream_t aux_stream = nullptr;            // second stream of cs_evaluate_device
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     csi::DevBuf err_word;                         // [0] device error bits, [1] FP64 re-run count
+    csi::DevBuf hess_ws;                          // workspace of cs_hessenberg_tc
     int64_t launches = 0;
     // serving: request queue, batch slots, scheduler thread
     uint64_t next_req = 1;
