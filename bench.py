@@ -698,6 +698,61 @@ def run_hessenberg(args):
     ctx.close()
 
 
+def run_scale(args):
+    """--scale K: the 2000-bus configuration on a seeded sample of K random N-2 branch pairs
+    (network: 2,000 buses, 3,000 branches, 500 generators, state order 2,499; 0.85-1.15 p.u.
+    voltage band as for the 300-bus network).  Mixed form (tensor-core Hessenberg reduction,
+    FP32 QR, FP64 re-run in the guard band) and, on the first K/2 pairs, the FP64 form:
+    scenarios/s, per-kernel-group device time, class mix, and the mixed form's deviation from
+    the FP64 form on the common pairs.  Inputs resident; CUDA events on the launching stream."""
+    import numpy as np
+    import torch
+    from paper_2512_08465_gb300 import cs, synth
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    net = synth.case_scaled(2000, seed=2000, vband=(0.85, 1.15))
+    ii, jj = synth.all_pairs(net.n_branch)
+    rng = np.random.default_rng(200000)
+    sel = np.sort(rng.choice(ii.size, args.scale, replace=False))
+    ei = torch.as_tensor(ii[sel].astype(np.int32), device=dev)
+    ej = torch.as_tensor(jj[sel].astype(np.int32), device=dev)
+    out = {"mode": "scale", "network": {"n_bus": net.n_bus, "n_branch": net.n_branch, "n_gen": net.n_gen,
+                                        "state_order": 5 * net.n_gen - 1},
+           "pairs": int(args.scale), "pair_draw": "seeded uniform sample of the 4,498,500 branch pairs"}
+    res = {}
+    for name, prec, m in (("mixed", cs.PREC_MIXED, args.scale), ("fp64", cs.PREC_FP64, max(1, args.scale // 2))):
+        ctx = cs.Context(precision=prec)
+        tl = time.perf_counter()
+        nid = ctx.load_network(net)
+        load_s = time.perf_counter() - tl
+        o = ctx.alloc_results(m, dev)
+        ctx.set_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.evaluate_device(nid, 0, ei[:m], ej[:m], o)
+        e1.record()
+        e1.synchronize()
+        ctx.sync()
+        ms = e0.elapsed_time(e1)
+        kms, _ = ctx.kernel_times()
+        k = o["klass"].cpu().numpy()
+        res[name] = {k2: v.cpu().numpy() for k2, v in o.items()}
+        out[name] = {"scenarios": m, "ms": ms, "scenarios_per_s": m / (ms / 1e3), "load_network_s": load_s,
+                     "kernel_ms": kms, "classes": {cs.CLASSES[c]: int((k == c).sum()) for c in range(7)},
+                     "eigen_fp64_reruns": ctx.eigen_reruns()}
+        ctx.close()
+    m = out["fp64"]["scenarios"]
+    a, b = res["fp64"], res["mixed"]
+    ok = np.isfinite(a["max_re"][:m]) & np.isfinite(b["max_re"][:m])
+    out["mixed_vs_fp64"] = {"classes_identical": bool(np.array_equal(a["klass"][:m], b["klass"][:m])),
+                            "max_abs_dev_max_re": float(np.abs(a["max_re"][:m] - b["max_re"][:m])[ok].max())
+                            if ok.any() else None,
+                            "max_abs_dev_min_zeta": float(np.abs(a["min_zeta"][:m] - b["min_zeta"][:m])[ok].max())
+                            if ok.any() else None}
+    out["wall_s"] = time.perf_counter() - t0
+    print(json.dumps(out))
+
+
 def run_serve(args):
     """--serve: the serving phase alone, both forms, with the larger request counts."""
     from paper_2512_08465_gb300 import cs
@@ -731,7 +786,12 @@ def main():
     ap.add_argument("--hessenberg", type=int, default=0, metavar="N",
                     help="time the tensor-core blocked Hessenberg reduction on N x N matrices")
     ap.add_argument("--hessenberg-batch", type=int, default=8)
+    ap.add_argument("--scale", type=int, default=0, metavar="K",
+                    help="2000-bus configuration on K seeded random branch pairs (mixed and FP64 forms)")
     args = ap.parse_args()
+    if args.scale:
+        run_scale(args)
+        return
     if args.hessenberg:
         run_hessenberg(args)
         return

@@ -22,7 +22,17 @@ cs_status cuda_fail(cs_ctx* c, cudaError_t e, const char* where) {
     return fail(c, CS_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-int64_t default_chunk(const cs_ctx* ctx) { return ctx->opt.chunk > 0 ? ctx->opt.chunk : 16384; }
+int64_t default_chunk(const cs_ctx* ctx, const Network& net) {
+    if (ctx->opt.chunk > 0) return ctx->opt.chunk;
+    // mixed form of a network whose state matrices go through the tensor-core reduction:
+    // the chunk's padded matrices and reduction workspaces within about 6 GB
+    if (ctx->opt.precision == CS_PREC_MIXED && !dyn_split_fits(net.dev, ctx->device)) {
+        const size_t nmax = 5 * (size_t)net.dev.ng - 1;
+        const size_t per = sizeof(float) * (dyn_abuf_stride(net.dev) + hess_tc_workspace_floats((int)nmax));
+        return std::max<int64_t>(64, std::min<int64_t>(16384, (int64_t)(6e9 / (double)per)));
+    }
+    return 16384;
+}
 
 namespace {
 constexpr int kCounters = 6;      // work counters of one chunk: OPF, then five small-signal kernels
@@ -54,6 +64,9 @@ Grids grids(const cs_ctx* ctx, const Network& net, int64_t cn) {
 bool split_path(const cs_ctx* ctx, const DevNet& dn) {
     return ctx->opt.precision == CS_PREC_MIXED && dyn_split_fits(dn, ctx->device);
 }
+bool large_path(const cs_ctx* ctx, const DevNet& dn) {
+    return ctx->opt.precision == CS_PREC_MIXED && !dyn_split_fits(dn, ctx->device) && 5 * dn.ng - 1 >= 3;
+}
 }  // namespace
 
 size_t workspace_bytes(const cs_ctx* ctx, const Network& net, int64_t chunk) {
@@ -65,6 +78,8 @@ size_t workspace_bytes(const cs_ctx* ctx, const Network& net, int64_t chunk) {
     if (split_path(ctx, dn))
         b += (sizeof(float) * (dyn_hbuf_stride(dn) + dyn_abuf_stride(dn) + dyn_cand_stride()) +
               sizeof(double) * dyn_a64_stride(dn)) * cn;
+    if (large_path(ctx, dn))
+        b += sizeof(float) * (dyn_abuf_stride(dn) + hess_tc_workspace_floats(5 * dn.ng - 1)) * cn;
     return b;
 }
 
@@ -155,6 +170,11 @@ cs_status csi::evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level
         CS_CUDA(ws.a64.ensure(sizeof(double) * dyn_a64_stride(dn) * cn));
         CS_CUDA(ws.cand.ensure(sizeof(float) * dyn_cand_stride() * cn));
     }
+    const bool large = large_path(ctx, dn);
+    if (large) {
+        CS_CUDA(ws.abuf.ensure(sizeof(float) * dyn_abuf_stride(dn) * cn));
+        CS_CUDA(ws.hws.ensure(sizeof(float) * hess_tc_workspace_floats(5 * dn.ng - 1) * cn));
+    }
     if (!ctx->err_word.p) {
         CS_CUDA(ctx->err_word.ensure(sizeof(int) * 2));
         CS_CUDA(cudaMemset(ctx->err_word.p, 0, sizeof(int) * 2));
@@ -206,9 +226,10 @@ cs_status csi::evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level
         CS_CUDA(mark(2));
         int nl = 0;
         CS_CUDA(launch_dyn(dn, a, o, ctx->opt.damping_min, ctx->opt.precision, (double*)ws.scratch.p, per_dyn,
-                           std::min<int64_t>(g_dyn, m), split ? (float*)ws.abuf.p : nullptr,
+                           std::min<int64_t>(g_dyn, m), (split || large) ? (float*)ws.abuf.p : nullptr,
                            split ? (float*)ws.hbuf.p : nullptr, split ? (double*)ws.a64.p : nullptr,
-                           split ? (float*)ws.cand.p : nullptr, ctx->sms, counters + 1, &nl, s));
+                           split ? (float*)ws.cand.p : nullptr, large ? (float*)ws.hws.p : nullptr, ctx->sms,
+                           counters + 1, &nl, s));
         CS_CUDA(done());
         ctx->launches += 2 + nl;
     }
@@ -711,7 +732,7 @@ cs_status cs_evaluate_device(cs_ctx* ctx, int32_t net_id, int32_t level, const i
         !out->max_re || !out->min_zeta)
         return fail(ctx, CS_E_ARG, "NULL buffer");
     CS_CUDA(cudaSetDevice(ctx->device));
-    const int64_t chunk = default_chunk(ctx);
+    const int64_t chunk = default_chunk(ctx, *net);
     if (ctx->opt.hbm_budget > 0) {
         const size_t want = workspace_bytes(ctx, *net, std::min<int64_t>(n, chunk)) * (n > chunk ? 2 : 1);
         const size_t have = ctx->direct.bytes() + ctx->direct2.bytes();
@@ -811,7 +832,7 @@ cs_status cs_evaluate_device_n3(cs_ctx* ctx, int32_t net_id, int32_t level, cons
     CS_CUDA(cudaSetDevice(ctx->device));
     ctx->launches = 0;
     return evaluate_impl(ctx, ctx->direct, net, level, ei, ej, n, out, (cudaStream_t)stream, true,
-                         default_chunk(ctx), ek);
+                         default_chunk(ctx, *net), ek);
 }
 
 cs_status cs_enumerate_triples_device(int32_t n_elem, int64_t first, int64_t count, int32_t* ei, int32_t* ej,

@@ -168,10 +168,12 @@ int opf_ctas_per_sm();       // resident OPF CTAs per SM the kernel is built for
 // refinement) and the packed Hessenberg matrices (-> shared-memory QR), a.n *
 // dyn_a64_stride(net) doubles for the FP64 state matrices and a.n *
 // dyn_cand_stride() floats for the refinement candidates; only usable when
-// dyn_split_fits(net, device).  *launches: kernels issued.
+// dyn_split_fits(net, device).  Otherwise, mixed form with abuf and hws (a.n *
+// hess_tc_workspace_floats(5 ng - 1) floats): the tensor-core Hessenberg path.
+// *launches: kernels issued (the reduction's own launches not counted).
 cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double damping_min, int precision,
                        double* scratch, size_t scratch_per_cta, int grid, float* abuf, float* hbuf, double* a64,
-                       float* cand, int sms, int* counters, int* launches, cudaStream_t s);
+                       float* cand, float* hws, int sms, int* counters, int* launches, cudaStream_t s);
 size_t dyn_scratch_doubles(const DevNet& net);
 size_t dyn_hbuf_stride(const DevNet& net);
 size_t dyn_abuf_stride(const DevNet& net);

@@ -65,16 +65,16 @@ struct Network {
 // workspace are chained through `free` (each waits for the previous one,
 // whatever its stream).
 struct Workspace {
-    DevBuf scratch, isl, opfx, opfst, counters, hbuf, abuf, a64, cand;
+    DevBuf scratch, isl, opfx, opfst, counters, hbuf, abuf, a64, cand, hws;
     cudaEvent_t free = nullptr;
     bool used = false;
     size_t bytes() const {
         return scratch.bytes + isl.bytes + opfx.bytes + opfst.bytes + counters.bytes + hbuf.bytes + abuf.bytes +
-               a64.bytes + cand.bytes;
+               a64.bytes + cand.bytes + hws.bytes;
     }
     void release() {
         scratch.release(); isl.release(); opfx.release(); opfst.release(); counters.release();
-        hbuf.release(); abuf.release(); a64.release(); cand.release();
+        hbuf.release(); abuf.release(); a64.release(); cand.release(); hws.release();
     }
     ~Workspace() {
         if (free) cudaEventDestroy(free);
@@ -177,8 +177,9 @@ cs_status cuda_fail(cs_ctx* c, cudaError_t e, const char* where);
         if (e_ != cudaSuccess) return csi::cuda_fail(ctx, e_, #call);   \
     } while (0)
 
-// Chunk of scenarios per internal batch for a context (0 in the options = 16384).
-int64_t default_chunk(const cs_ctx* ctx);
+// Chunk of scenarios per internal batch for a context and network (0 in the options:
+// 16384, less for mixed-form networks whose state matrices take the tensor-core path).
+int64_t default_chunk(const cs_ctx* ctx, const Network& net);
 
 // Device bytes a workspace needs to evaluate chunks of `chunk` scenarios of net.
 size_t workspace_bytes(const cs_ctx* ctx, const Network& net, int64_t chunk);

@@ -46,8 +46,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr double kEps = 2.220446049250313e-16;
-constexpr double kGuardRe = 5e-3;      // |max Re| within this of 0: decide in FP64
-constexpr double kGuardZeta = 5e-3;    // |min zeta - threshold| within this: decide in FP64
+// FP32 screen in global memory (no refinement): a decision this close to a threshold is
+// taken by the FP64 screen instead
+constexpr double kGuardRe = 5e-3;      // |max Re| within this of 0
+constexpr double kGuardZeta = 5e-3;    // |min zeta - threshold| within this
 
 struct DLay {
     int Yu, Yl, Yd, Ydi;      // complex arrays (2 doubles per entry)
@@ -456,6 +458,10 @@ constexpr int kCandStride = 4 + 2 * kRefK;
 // exact one (measured differences are below 3e-5): an eigenvalue can decide max Re
 // or min zeta only if its FP32 value is within this bound of deciding it.
 constexpr float kEigDelta = 1e-3f;
+// Refined statistics within this distance of a threshold (max Re = 0, min zeta =
+// damping_min) are decided by the FP64 screen instead (the refined values are within
+// ~1e-9 of the FP64 screen's).
+constexpr double kRefinedGuard = 1e-7;
 
 // max Re and min damping ratio over the n eigenvalues (block-wide, result on all threads)
 __device__ void eig_stats(DShared& sh, int n, const double* wr, const double* wi, double& maxre, double& minz) {
@@ -474,11 +480,17 @@ __device__ void eig_stats(DShared& sh, int n, const double* wr, const double* wi
 
 // Kernel modes.  FULL64: FP64 screen of every converged OPF point (the FP64
 // form).  MIXED_INLINE: FP32 screen in global memory with the FP64 re-run
-// inline (mixed form, networks whose Hessenberg matrix exceeds shared memory).
+// inline (mixed form, kept for networks the tensor-core path does not take).
 // FRONT: model and FP32 balancing; the balanced matrix goes to a per-scenario
 // buffer for hess_cluster_kernel.  RERUN: FP64 screen of the scenarios that
-// hqr_smem_kernel marked (status 6).
-enum { DYN_FULL64 = 0, DYN_MIXED_INLINE = 1, DYN_FRONT = 2, DYN_RERUN = 3 };
+// the FP32 screen could not decide (status 6).  FRONT_LARGE / QR_LARGE: the
+// mixed form of networks whose Hessenberg matrix exceeds shared memory: the
+// balanced FP32 matrix, padded to the network's largest state order with a
+// decoupled -1 diagonal (so one batch has one order), goes to the tensor-core
+// blocked Hessenberg reduction (k_tc.cu), then FP32 QR in global memory over the
+// padded order with statistics over the first n eigenvalues (the padding's -1
+// eigenvalues deflate first, into the last positions), guard band to RERUN.
+enum { DYN_FULL64 = 0, DYN_MIXED_INLINE = 1, DYN_FRONT = 2, DYN_RERUN = 3, DYN_FRONT_LARGE = 4, DYN_QR_LARGE = 5 };
 
 template <int kMode>
 __global__ void __launch_bounds__(kThreads)
@@ -503,6 +515,39 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
         const int s = sh.scen;
         if (s >= a.n) break;
         if (o.status[s] != (kMode == DYN_RERUN ? 6 : 1)) {
+            __syncthreads();
+            continue;
+        }
+        if (kMode == DYN_QR_LARGE) {                  // QR of the padded Hessenberg matrix (tensor-core reduction)
+            float* slot = hbuf + (size_t)s * hstride;
+            const int n = __float_as_int(slot[0]), nmax = 5 * ng - 1;
+            double* wr = W + L.wr;
+            double* wi = W + L.wi;
+            if (tid == 0) sh.fail = 0;
+            __syncthreads();
+            hqr_global<float>(slot + kHqHead, nmax, wr, wi, sh);
+            double maxre = 0.0, minz = 0.0;
+            eig_stats(sh, n, wr, wi, maxre, minz);
+            if (tid == 0) {
+                const bool near = sh.fail || !(fabs(maxre) > kGuardRe) || !(fabs(minz - damping_min) > kGuardZeta);
+                if (near) {                           // decision too close to call in FP32: FP64 screen
+                    o.status[s] = 6;
+                    atomicAdd(a.reruns, 1);
+                } else {
+                    uint8_t k;
+                    if (maxre >= 0.0) k = CS_SS_UNSTABLE;
+                    else if (minz < damping_min) k = CS_SS_POORLY_DAMPED;
+                    else k = CS_SECURE;
+                    if (a.out.n_islands[s] > 1) {     // main island: the scenario's class stays ISLANDED
+                        if (a.out.main_klass) a.out.main_klass[s] = k;
+                    } else {
+                        a.out.klass[s] = k;
+                        a.out.severe[s] = (k != CS_SECURE);
+                    }
+                    a.out.max_re[s] = maxre;
+                    a.out.min_zeta[s] = minz;
+                }
+            }
             __syncthreads();
             continue;
         }
@@ -726,7 +771,7 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
                 }
                 a.out.max_re[s] = nan;
                 a.out.min_zeta[s] = nan;
-                if (kMode == DYN_FRONT) o.status[s] = 7;
+                if (kMode == DYN_FRONT || kMode == DYN_FRONT_LARGE) o.status[s] = 7;
             }
             __syncthreads();
             continue;
@@ -743,6 +788,23 @@ dyn_kernel(DevNet net, EvalArgs a, OpfOut o, double damping_min, double* scratch
             __syncthreads();
             balance<float>(A32, n, reinterpret_cast<float*>(cs_d), reinterpret_cast<float*>(rs_d), sh,
                            dst + ab_d_off(5 * ng - 1));
+            __syncthreads();
+            continue;
+        }
+        if (kMode == DYN_FRONT_LARGE) {               // balanced FP32 matrix, padded, for the tensor-core reduction
+            float* A32 = reinterpret_cast<float*>(W + L.A32);
+            for (int w = tid; w < n * n; w += kThreads) A32[w] = (float)A[w];
+            __syncthreads();
+            balance<float>(A32, n, reinterpret_cast<float*>(cs_d), reinterpret_cast<float*>(rs_d), sh);
+            __syncthreads();
+            float* slot = hbuf + (size_t)s * hstride;
+            const int nmax = 5 * ng - 1;
+            float* M = slot + kHqHead;
+            for (int w = tid; w < nmax * nmax; w += kThreads) {
+                const int i = w / nmax, j = w % nmax;
+                M[w] = (i < n && j < n) ? A32[i * n + j] : (i == j ? -1.0f : 0.0f);
+            }
+            if (tid == 0) slot[0] = __int_as_float(n);
             __syncthreads();
             continue;
         }
@@ -968,12 +1030,20 @@ hess_cluster_kernel(EvalArgs a, OpfOut o, float* __restrict__ abuf, size_t astri
 // matrix held in shared memory (one scenario per CTA, one CTA per SM).  Every
 // thread carries the same loop state (lo, hi, shifts, reflector), computed
 // redundantly from shared memory in FP32, so a bulge step costs two barriers.
-// A scenario whose decision falls inside the guard band (or whose QR does not
-// converge) is marked for the FP64 re-run; the others are classified here.
+// Exceptional shifts come every tenth sweep without a deflation, and a stalled
+// window also deflates at the normwise FP32 level (kStallIts).  A scenario whose
+// QR does not converge is marked for the FP64 re-run; the others get their
+// refinement candidates and go on to eig_refine_kernel, which classifies them.
 #ifndef CS_QR_THREADS
 #define CS_QR_THREADS 256
 #endif
 constexpr int kQrThreads = CS_QR_THREADS;
+// FP32 QR without a deflation for this many sweeps (the double-shift iteration can
+// stall at FP32 rounding level): from then on a subdiagonal entry below eps_32 times
+// the largest entry of the matrix counts as negligible too.  The screen's eigenvalues
+// only need to be within kEigDelta of the exact ones (the decisive ones are refined in
+// FP64), which that normwise perturbation respects.
+constexpr int kStallIts = 40;
 // the column phase of a bulge step covers at most 2 kQrThreads rows (orders up to 32 kHsCols + 1)
 static_assert(2 * kQrThreads > 32 * kHsCols + 1, "QR column phase: at most two rows per thread");
 
@@ -1050,7 +1120,10 @@ hqr_smem_kernel(EvalArgs a, OpfOut o, const float* __restrict__ hbuf, size_t hst
                 if (l >= 1) {
                     float sd = fabsf(H[rb[l - 1] + l - 1]) + fabsf(H[rb[l] + l]);
                     if (sd == 0.0f) sd = hmax;
-                    neg = fabsf(H[rb[l] + l - 1]) <= eps * sd;
+                    const float h = fabsf(H[rb[l] + l - 1]);
+                    // after kStallIts sweeps without a deflation, a subdiagonal entry at FP32
+                    // rounding level of the whole matrix also counts as negligible
+                    neg = h <= eps * sd || (its >= kStallIts && h <= eps * hmax);
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, neg);
                 if (m) {
@@ -1087,7 +1160,7 @@ hqr_smem_kernel(EvalArgs a, OpfOut o, const float* __restrict__ hbuf, size_t hst
             {
                 const float a11 = H[rb[hi - 1] + hi - 1], a12 = H[rb[hi - 1] + hi];
                 const float a21 = H[rb[hi] + hi - 1], a22 = H[rb[hi] + hi];
-                if (its == 10 || its == 20) {              // exceptional shift
+                if (its % 10 == 0) {                       // exceptional shift, every tenth sweep
                     const float ww = fabsf(a21) + fabsf(H[rb[hi - 1] + hi - 2]);
                     sft = 1.5f * ww;
                     tft = ww * ww;
@@ -1186,9 +1259,10 @@ hqr_smem_kernel(EvalArgs a, OpfOut o, const float* __restrict__ hbuf, size_t hst
                 maxre = fmaxf(maxre, red[0][w]);
                 minz = fminf(minz, red[1][w]);
             }
-            const bool near = fail || !(fabsf(maxre) > (float)kGuardRe) ||
-                              !(fabsf(minz - (float)damping_min) > (float)kGuardZeta);
-            if (near) {                                    // decision too close to call in FP32
+            // The class is decided after the FP64 refinement (eig_refine_kernel), from
+            // values within ~1e-9 of the FP64 screen's, so no FP32 guard band applies here;
+            // a QR that did not converge goes to the FP64 screen.
+            if (fail) {
                 o.status[s] = 6;
                 atomicAdd(a.reruns, 1);
             } else {
@@ -1539,7 +1613,8 @@ eig_refine_kernel(EvalArgs a, OpfOut o, const float* __restrict__ hbuf, size_t h
                 if ((sh.flags >> (2 * c)) & 1) maxre = fmax(maxre, lam.re);
                 if ((sh.flags >> (2 * c)) & 2) minz = fmin(minz, mg > 0.0 ? -lam.re / mg : 1.0);
             }
-            if (!good || !(maxre > -INFINITY) || !(minz < INFINITY)) {
+            if (!good || !(maxre > -INFINITY) || !(minz < INFINITY) || !(fabs(maxre) > kRefinedGuard) ||
+                !(fabs(minz - damping_min) > kRefinedGuard)) {
                 o.status[s] = 6;                                // FP64 screen instead
                 atomicAdd(a.reruns, 1);
             } else {
@@ -1620,7 +1695,7 @@ static cudaError_t launch_mode(const DevNet& net, const EvalArgs& a, OpfOut o, d
 
 cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double damping_min, int precision,
                        double* scratch, size_t scratch_per_cta, int grid, float* abuf, float* hbuf, double* a64,
-                       float* cand, int sms, int* counters, int* launches, cudaStream_t s) {
+                       float* cand, float* hws, int sms, int* counters, int* launches, cudaStream_t s) {
     *launches = 0;
     if (a.n <= 0) return cudaSuccess;
     const DLay L = make_dlayout(net);
@@ -1661,6 +1736,24 @@ cudaError_t launch_dyn(const DevNet& net, const EvalArgs& a, OpfOut o, double da
                                    counters + 2, s);
         if (e != cudaSuccess) return e;
         *launches = 5;
+    } else if (precision == CS_PREC_MIXED && abuf && hws) {
+        // networks whose Hessenberg matrix exceeds one block's shared memory: model and
+        // balancing, the blocked Hessenberg reduction of the whole chunk on the tensor
+        // cores, FP32 QR per scenario, FP64 re-run of the undecided ones
+        const int nmax = 5 * net.ng - 1;
+        const size_t astride = dyn_abuf_stride(net);
+        e = launch_mode<DYN_FRONT_LARGE>(net, a, o, damping_min, scratch, scratch_per_cta, L, abuf, astride, nullptr,
+                                         grid, counters, s);
+        if (e != cudaSuccess) return e;
+        e = launch_hess_tc(a.n, nmax, abuf + kHqHead, (long long)astride, hws, a.err, s);
+        if (e != cudaSuccess) return e;
+        e = launch_mode<DYN_QR_LARGE>(net, a, o, damping_min, scratch, scratch_per_cta, L, abuf, astride, nullptr, grid,
+                                      counters + 1, s);
+        if (e != cudaSuccess) return e;
+        e = launch_mode<DYN_RERUN>(net, a, o, damping_min, scratch, scratch_per_cta, L, nullptr, 0, nullptr, grid,
+                                   counters + 2, s);
+        if (e != cudaSuccess) return e;
+        *launches = 4;
     } else if (precision == CS_PREC_MIXED) {
         e = launch_mode<DYN_MIXED_INLINE>(net, a, o, damping_min, scratch, scratch_per_cta, L, nullptr, 0, nullptr,
                                           grid, counters, s);

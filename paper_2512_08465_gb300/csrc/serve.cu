@@ -145,7 +145,7 @@ bool launch_batch(cs_ctx* ctx, Slot& sl) {
         prune_queue(ctx);
     };
     // admission: everything else the context holds + this slot's needs
-    int64_t chunk = std::min<int64_t>(default_chunk(ctx), std::max<int64_t>(total, 1));
+    int64_t chunk = std::min<int64_t>(default_chunk(ctx, *net), std::max<int64_t>(total, 1));
     const size_t io = sizeof(int32_t) * 2 * total + result_bytes(total);
     if (ctx->opt.hbm_budget > 0) {
         const size_t others = reserved_bytes(ctx) - sl.device_bytes();

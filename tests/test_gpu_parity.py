@@ -358,19 +358,27 @@ def test_mixed_equals_fp64_classes_full_level(ctx, net118, mixed118):
     assert c.eigen_reruns() >= 0
 
 
-def test_mixed_form_inline_path_on_a_300_bus_network():
+def test_mixed_form_tensor_core_path_on_a_300_bus_network():
     """Networks whose Hessenberg matrix exceeds shared memory (300 buses, 75
-    generators, state order 374) take the FP32 screen in global memory with the
-    FP64 re-run inline.  Classes must equal the FP64 form's, eigen statistics
-    agree within the mixed-form tolerance."""
+    generators, state order 374) take the tensor-core blocked Hessenberg reduction
+    of the whole chunk (matrices padded to the largest order) and the FP32 QR in
+    global memory, with the FP64 re-run in the guard band.  Branch pairs and pairs
+    with a generator out (a smaller state order inside the padded batch).  Classes,
+    iterations and costs must equal the FP64 form's, eigen statistics agree within
+    the FP32 tolerance of this path."""
     net = synth.case_scaled(300, seed=300, vband=(0.85, 1.15))
     ii, jj = synth.all_pairs(net.n_branch)
-    sel = np.random.default_rng(8).choice(ii.size, 48, replace=False)
+    rng = np.random.default_rng(8)
+    sel = rng.choice(ii.size, 48, replace=False)
+    gi = rng.choice(net.n_branch, 16, replace=False).astype(np.int32)
+    gj = (net.n_branch + rng.choice(net.n_gen, 16, replace=False)).astype(np.int32)
+    ei = np.concatenate([ii[sel], gi])
+    ej = np.concatenate([jj[sel], gj])
     res = {}
     for prec in (cs.PREC_FP64, cs.PREC_MIXED):
         c = cs.Context(precision=prec)
         nid = c.load_network(net)
-        res[prec] = _run(c, nid, 0, ii[sel], jj[sel])
+        res[prec] = _run(c, nid, 0, ei, ej)
         c.close()
     a, b = res[cs.PREC_FP64], res[cs.PREC_MIXED]
     np.testing.assert_array_equal(a["klass"], b["klass"])
