@@ -50,3 +50,34 @@ def test_golden_sample_reproduces_from_the_oracle(name, count):
         if "Vm" in g:
             assert np.abs(np.asarray(r["Vm"]) - g["Vm"]).max() <= 1e-9
 
+
+
+FULL = os.path.join(HERE, "case118_full.npz")
+
+
+def test_full_study_tables_come_from_the_current_oracle():
+    """The stored tables of the whole 118-bus study (make_full_golden.py) carry the
+    hash of the current oracle sources, cover both levels completely, and a seeded
+    sample of their scenarios re-evaluates to the stored values."""
+    g = np.load(FULL)
+    meta = json.loads(str(g["meta"]))
+    assert meta["oracle"] == _make_golden().oracle_hash()
+    net = synth.case118()
+    E = net.n_elem
+    n = 1 + E + E * (E - 1) // 2
+    assert meta["scenarios_per_level"] == n
+    for lv in (0, 1):
+        k = g[f"{lv}_klass"]
+        assert k.shape == (n,) and k.max() <= 6
+        assert np.all((k == 1) == (g[f"{lv}_islands"] > 1))
+    ii, jj = np.triu_indices(E, k=1)
+    si = np.concatenate([[-1], np.arange(E), ii])
+    sj = np.concatenate([[-1], -np.ones(E, np.int64), jj])
+    rng = np.random.default_rng(31)
+    for lv in (0, 1):
+        for q in rng.choice(n, 3, replace=False):
+            r = pipeline.evaluate(net, lv, int(si[q]), int(sj[q]))
+            assert int(r["klass"]) == int(g[f"{lv}_klass"][q]) and int(r["opf_iters"]) == int(g[f"{lv}_iters"][q])
+            for key, name in (("cost", "cost"), ("max_re", "max_re"), ("min_zeta", "min_zeta")):
+                a, b = r[key], g[f"{lv}_{name}"][q]
+                assert (np.isnan(a) and np.isnan(b)) or abs(a - b) <= 1e-9 * max(1.0, abs(b)), (lv, q, key)
