@@ -701,7 +701,8 @@ def run_hessenberg(args):
 def run_scale(args):
     """--scale K: the 2000-bus configuration on a seeded sample of K random N-2 branch pairs
     (network: 2,000 buses, 3,000 branches, 500 generators, state order 2,499; 0.85-1.15 p.u.
-    voltage band as for the 300-bus network).  Mixed form (tensor-core Hessenberg reduction,
+    voltage band as for the 300-bus network; interior-point cap 150 iterations, as its base-case
+    OPF needs 70).  Mixed form (tensor-core Hessenberg reduction,
     FP32 QR, FP64 re-run in the guard band) and, on the first K/2 pairs, the FP64 form:
     scenarios/s, per-kernel-group device time, class mix, and the mixed form's deviation from
     the FP64 form on the common pairs.  Inputs resident; CUDA events on the launching stream."""
@@ -711,6 +712,7 @@ def run_scale(args):
     dev = torch.device("cuda", 0)
     t0 = time.perf_counter()
     net = synth.case_scaled(2000, seed=2000, vband=(0.85, 1.15))
+    net.opf_max_it = 150                      # this network's cap (cs_network_desc.opf_max_it)
     ii, jj = synth.all_pairs(net.n_branch)
     rng = np.random.default_rng(200000)
     sel = np.sort(rng.choice(ii.size, args.scale, replace=False))

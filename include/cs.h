@@ -121,6 +121,8 @@ typedef struct {
     const double *c2, *c1, *c0;                   /* [n_gen] */
     const double *H, *D, *xd, *xq, *xdp;          /* [n_gen] machine base */
     const double *Td0p, *Tq0p, *KA, *TA;          /* [n_gen] seconds / gain */
+    int32_t opf_max_it;                           /* this network's interior-point iteration cap
+                                                     (0..10000); 0 = the context's opf_max_it */
 } cs_network_desc;
 
 /* Per-scenario results, structure of arrays with n records.  Which memory
@@ -192,8 +194,9 @@ cs_status cs_unload_network(cs_ctx* ctx, int32_t net_id);
  * block updates of one numeric factorisation, elimination-tree levels,
  * largest state-matrix order (5 n_gen - 1), load levels, then the launch shape
  * the network's evaluations use: resident OPF blocks per SM, resident
- * small-signal blocks per SM, and 1 if the autotuner chose them (0 if they are
- * the defaults or ctas_per_sm).  The first n_stats
+ * small-signal blocks per SM, 1 if the autotuner chose them (0 if they are
+ * the defaults or ctas_per_sm), and the network's interior-point iteration
+ * cap (stats[11]).  The first n_stats
  * entries are written (HOST array). */
 cs_status cs_network_stats(cs_ctx* ctx, int32_t net_id, int64_t* stats, int32_t n_stats);
 

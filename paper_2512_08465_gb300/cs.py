@@ -54,7 +54,8 @@ class NetworkDesc(ctypes.Structure):
                [(k, _dp) for k in ("Vmin", "Vmax", "Gs", "Bs", "Pd", "Qd")] + \
                [("f", _ip), ("t", _ip)] + [(k, _dp) for k in ("r", "x", "b", "rate", "tap")] + \
                [("gbus", _ip)] + [(k, _dp) for k in ("Pmin", "Pmax", "Qmin", "Qmax", "c2", "c1", "c0",
-                                                      "H", "D", "xd", "xq", "xdp", "Td0p", "Tq0p", "KA", "TA")]
+                                                      "H", "D", "xd", "xq", "xdp", "Td0p", "Tq0p", "KA", "TA")] + \
+               [("opf_max_it", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -109,6 +110,7 @@ def _network_desc(net):
     for k in ("Pmin", "Pmax", "Qmin", "Qmax", "c2", "c1", "c0", "H", "D", "xd", "xq", "xdp", "Td0p",
               "Tq0p", "KA", "TA"):
         setattr(D, k, d(k, getattr(net, k)))
+    D.opf_max_it = int(getattr(net, "opf_max_it", 0) or 0)   # optional attribute; 0: the context's cap
     return D, arrs
 
 
@@ -361,10 +363,10 @@ class Context:
 
     def network_stats(self, net_id: int) -> dict:
         """Sizes of a loaded network and its symbolic analysis (cs_network_stats)."""
-        v = np.zeros(11, np.int64)
-        self._check(self.lib.cs_network_stats(self.h, net_id, _ptr(v), 11), "cs_network_stats")
+        v = np.zeros(12, np.int64)
+        self._check(self.lib.cs_network_stats(self.h, net_id, _ptr(v), 12), "cs_network_stats")
         keys = ("n_bus", "n_branch", "n_gen", "l_blocks", "block_updates", "levels", "states_max", "levels_load",
-                "opf_ctas_per_sm", "dyn_ctas_per_sm", "autotuned")
+                "opf_ctas_per_sm", "dyn_ctas_per_sm", "autotuned", "opf_max_it")
         return dict(zip(keys, (int(x) for x in v)))
 
     # ------------------------------------------------------------ Risk Index --

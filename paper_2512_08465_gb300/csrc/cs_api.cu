@@ -220,7 +220,7 @@ cs_status csi::evaluate_impl(cs_ctx* ctx, Workspace& ws, Network* net, int level
         CS_CUDA(launch_islands(dn, a, (int*)ws.isl.p, s));
         CS_CUDA(done());
         CS_CUDA(mark(1));
-        CS_CUDA(launch_opf(dn, a, (const int*)ws.isl.p, o, ctx->opt.opf_tol, ctx->opt.opf_max_it,
+        CS_CUDA(launch_opf(dn, a, (const int*)ws.isl.p, o, ctx->opt.opf_tol, net->max_it,
                            (double*)ws.scratch.p, per_opf, std::min<int64_t>(g_opf, m), counters, s));
         CS_CUDA(done());
         CS_CUDA(mark(2));
@@ -357,6 +357,7 @@ std::string check_desc(const cs_network_desc* d) {
     for (const void* p : req)
         if (!p) return "NULL array in network descriptor";
     if ((long long)nbr + ng > 32767) return "too many outage elements";
+    if (d->opf_max_it < 0 || d->opf_max_it > 10000) return "interior-point iteration cap outside 0..10000";
     auto fin = [](double v) { return std::isfinite(v); };
     for (int i = 0; i < nb; ++i) {
         if (!fin(d->Vmin[i]) || !fin(d->Vmax[i]) || !(d->Vmin[i] > 0) || !(d->Vmin[i] <= d->Vmax[i]))
@@ -471,6 +472,7 @@ cs_status cs_load_network(cs_ctx* ctx, const cs_network_desc* d, int32_t* net_id
     const int nb = d->n_bus, nbr = d->n_branch, ng = d->n_gen, nlev = d->n_levels;
     CS_CUDA(cudaSetDevice(ctx->device));
     std::unique_ptr<Network> net(new Network());
+    net->max_it = d->opf_max_it > 0 ? d->opf_max_it : ctx->opt.opf_max_it;
     std::vector<int> f(d->f, d->f + nbr), t(d->t, d->t + nbr);
     std::string msg = symbolic_analysis(nb, f, t, d->ref_bus, net->sym);
     if (!msg.empty()) return fail(ctx, CS_E_ARG, msg);
@@ -666,10 +668,10 @@ cs_status cs_network_stats(cs_ctx* ctx, int32_t net_id, int64_t* stats, int32_t 
     if (!stats || n_stats < 0) return fail(ctx, CS_E_ARG, "NULL stats");
     const DevNet& d = it->second->dev;
     const Symbolic& S = it->second->sym;
-    const int64_t v[11] = {d.nb, d.nbr, d.ng, d.nL, (int64_t)S.upd_a.size(), d.nlevels, 5LL * d.ng - 1,
+    const int64_t v[12] = {d.nb, d.nbr, d.ng, d.nL, (int64_t)S.upd_a.size(), d.nlevels, 5LL * d.ng - 1,
                            (int64_t)it->second->nlev, cap_opf_of(ctx, *it->second), cap_dyn_of(ctx, *it->second),
-                           (ctx->opt.ctas_per_sm == 0 && it->second->opf_cap > 0) ? 1 : 0};
-    for (int i = 0; i < n_stats && i < 11; ++i) stats[i] = v[i];
+                           (ctx->opt.ctas_per_sm == 0 && it->second->opf_cap > 0) ? 1 : 0, it->second->max_it};
+    for (int i = 0; i < n_stats && i < 12; ++i) stats[i] = v[i];
     return CS_OK;
 }
 

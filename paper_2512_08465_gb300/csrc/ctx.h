@@ -43,6 +43,7 @@ struct Network {
     int id = 0;
     int busy = 0;                     // calls reading its tables outside the context lock
     int opf_cap = 0, dyn_cap = 0;     // resident blocks per SM chosen by the autotuner (0 = default)
+    int max_it = 50;                  // interior-point iteration cap of this network
     DevNet dev{};
     DevBuf blob;                      // all static device arrays
     Symbolic sym;

@@ -120,8 +120,9 @@ tc_gemm_kernel(int M, int N, int K, const float* __restrict__ A, long long am, l
     for (int rd = 0; rd < rounds && !timed_out; ++rd) {
         const int k0 = rd * kBK;
         // stage A (kBM x kBK) and B^T (kBN x kBK) as TF32 pairs; zeros outside the matrices
+        // consecutive threads walk the operand's contiguous dimension (coalesced loads)
         for (int w = tid; w < kBM * kBK; w += kTcThreads) {
-            const int r = w / kBK, k = w % kBK;
+            const int r = (am == 1) ? w % kBM : w / kBK, k = (am == 1) ? w / kBM : w % kBK;
             const int gr = m0 + r, gk = k0 + k;
             const float x = (gr < M && gk < K) ? Ab[(long long)gr * am + (long long)gk * ak] : 0.0f;
             const float hi = tf32_round(x);
@@ -129,7 +130,7 @@ tc_gemm_kernel(int M, int N, int K, const float* __restrict__ A, long long am, l
             a_lo[tile_index(r, k)] = tf32_round(x - hi);
         }
         for (int w = tid; w < kBN * kBK; w += kTcThreads) {
-            const int k = w / kBN, n = w % kBN;
+            const int k = (bk == 1) ? w % kBK : w / kBN, n = (bk == 1) ? w / kBK : w % kBN;
             const int gn = n0 + n, gk = k0 + k;
             const float x = (gn < N && gk < K) ? alpha * Bb[(long long)gk * bk + (long long)gn * bn] : 0.0f;
             const float hi = tf32_round(x);

@@ -301,6 +301,29 @@ def test_base_case_secure_and_edges(ctx, net118):
     assert a["klass"][0] == a["klass"][1] and a["cost"][0] == a["cost"][1]
 
 
+def test_per_network_iteration_cap(ctx, net118):
+    """cs_network_desc.opf_max_it replaces the context's cap for that network only: the
+    same 118-bus network loaded with a cap of 5 stops every OPF at 5 iterations (not
+    converged), while the copy loaded with the default cap converges as before."""
+    net, nid = net118
+    capped = synth.case118()
+    capped.opf_max_it = 5
+    nid5 = ctx.load_network(capped)
+    try:
+        assert ctx.network_stats(nid5)["opf_max_it"] == 5 and ctx.network_stats(nid)["opf_max_it"] == 50
+        b5, b = ctx.base_result(nid5, 0), ctx.base_result(nid, 0)
+        assert int(b5["klass"]) == 2 and int(b5["opf_iters"]) == 5
+        assert int(b["klass"]) == 0 and int(b["opf_iters"]) > 5
+        a5 = _run(ctx, nid5, 0, [3, 10, 40], [50, -1, 200])
+        a = _run(ctx, nid, 0, [3, 10, 40], [50, -1, 200])
+        for q in range(3):
+            assert int(a5["opf_iters"][q]) <= 5
+            if int(a["klass"][q]) != 1:
+                assert int(a5["klass"][q]) == 2 and int(a5["opf_iters"][q]) == 5
+    finally:
+        ctx.unload_network(nid5)
+
+
 # ------------------------------------------------------------ mixed precision form --
 # The mixed form refines the decisive eigenvalues in FP64 (two-sided Rayleigh quotient
 # with the FP64 state matrix), so it is held to the FP64 tolerance.  Networks whose

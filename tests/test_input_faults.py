@@ -66,3 +66,16 @@ def test_self_loop_and_zero_impedance_name_the_branch(net):
     r[9] = x[9] = 0.0
     with pytest.raises(cs.CSError, match="branch 9: impedance zero"):
         cs.check_network(_with(net, r=r, x=x))
+
+
+@pytest.mark.parametrize("cap,ok", [(0, True), (150, True), (10000, True), (-1, False), (10001, False)])
+def test_per_network_iteration_cap_range(net, cap, ok):
+    """cs_network_desc.opf_max_it: 0 keeps the context's cap, 1..10000 replace it for this
+    network, anything else is rejected."""
+    bad = dataclasses.replace(net)
+    bad.opf_max_it = cap
+    if ok:
+        cs.check_network(bad)
+    else:
+        with pytest.raises(cs.CSError, match="iteration cap"):
+            cs.check_network(bad)
