@@ -65,10 +65,11 @@ constexpr double kSigma = 0.1;
 constexpr double kLimitTol = 1e-6;
 constexpr int kRefineSteps = 3;              // FP64 iterative refinement steps per Newton solve (at most)
 constexpr double kRefineTol = 4.0 * 2.220446049250313e-16;   // refinement done: backward error at rounding level
-constexpr double kBackwardTol = 1e-13;       // componentwise backward error accepted from the block solve
+constexpr double kBackwardTol = 1e-15;       // componentwise backward error accepted from the block solve + GMRES
 constexpr int kDenseMax = 1024;              // dense fallback for reduced systems up to this order
 constexpr int kPanel = 8;                    // panel width of the dense fallback's blocked LU
 constexpr int kGmresM = 8;                   // GMRES iterations per Newton solve (at most)
+constexpr int kRedMax = kGmresM + 1 > 10 ? kGmresM + 1 : 10;   // values per block reduction (at most)
 
 // record layout
 constexpr int R_DSF = 0, R_DST = 8, R_GF = 16, R_GT = 20, R_H = 24, R_LG = 34, R_NG = 38, R_SF = 42, R_ST = 44;
@@ -88,7 +89,7 @@ struct Lay {
     // branch
     int zf, zt, muf, mut, hf, ht, dzf, dzt, dmuf, dmut, rec;
     // KKT: assembled blocks (Kb, Kd) kept for refinement, factor (Ub, Lb, Db, Di), vectors
-    int Kb, Kd, Ub, Lb, Db, Di, x, bv, rv, cs;
+    int Kb, Kd, Ub, Lb, Db, Di, x, bv, rv, cs, drs, dpiv;   // drs, dpiv: dense backstop's row scales, pivots
     int kv, kz, gx0, gxb, gr;   // GMRES: Krylov basis, preconditioned basis, start, best iterate, work
     int uf, cap, dead;          // main island: union-find parents (int), capacity per root, bus flags (bytes)
     long dense;                 // dense fallback matrix (4nb)^2, -1 if the network is too large
@@ -114,6 +115,7 @@ Lay make_layout(const DevNet& n) {
     L.Kb = take(16 * n.nL); L.Kd = take(16 * nb);
     L.Ub = take(16 * n.nL); L.Lb = take(16 * n.nL); L.Db = take(16 * nb); L.Di = take(16 * nb);
     L.x = take(4 * nb); L.bv = take(4 * nb); L.rv = take(4 * nb); L.cs = take(4 * nb);
+    L.drs = take(4 * nb); L.dpiv = take(2 * nb);
     L.kv = take(4 * nb * (kGmresM + 1)); L.kz = take(4 * nb * kGmresM);
     L.gx0 = take(4 * nb); L.gxb = take(4 * nb); L.gr = take(4 * nb);
     L.uf = take((nb + 1) / 2); L.cap = take(nb); L.dead = take((nb + 7) / 8);
@@ -131,7 +133,7 @@ Lay make_layout(const DevNet& n) {
 
 // ------------------------------------------------------------------ helpers --
 struct RedBuf {
-    double v[10][kWarps];
+    double v[kRedMax][kWarps];
 };
 
 __device__ __forceinline__ double red_op(int op, double a, double b) {
@@ -142,6 +144,7 @@ __device__ __forceinline__ double red_op(int op, double a, double b) {
 // (shared).  Warp shuffles, then one pass over the per-warp results.
 template <int K>
 __device__ void block_reduce(RedBuf& rb, double (&val)[K], const int (&ops)[K], double* out) {
+    static_assert(K <= kRedMax, "block_reduce: more values than RedBuf and Scal::red hold");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int k = 0; k < K; ++k) {
         double v = val[k];
@@ -611,8 +614,10 @@ struct DenseShared {
 
 // Dense LU with partial pivoting of the equilibrated assembled reduced system
 // (order 4 nb, row-major in scratch), solving for b into x.  Backstop for the Newton steps
-// whose block solve did not reach the backward-error target.  Returns false
-// when a pivot column is exactly zero.
+// whose block solve did not reach the backward-error target.  The factors, the
+// scales and the pivot sequence stay in the scratch for dense_resolve (the
+// refinement of the backstop's solution).  Returns false when a pivot column is
+// exactly zero.
 __device__ bool dense_solve(const DevNet& net, double* W, const Lay& L, DenseShared& ds) {
     const int tid = threadIdx.x, nb = net.nb, N = 4 * nb;
     const int warp = tid >> 5, lane = tid & 31;
@@ -634,8 +639,9 @@ __device__ bool dense_solve(const DevNet& net, double* W, const Lay& L, DenseSha
     // Equilibrate rows then columns by powers of two (exact): the reduced system's
     // rows span ~1e-5..1e12 near convergence, and partial pivoting is only normwise
     // stable, so without scaling the balance rows lose all accuracy.
-    double* rs = W + L.rv;          // row scales (the refinement residual is free here)
+    double* rs = W + L.drs;         // row scales
     double* cs = W + L.cs;          // column scales
+    int* piv = reinterpret_cast<int*>(W + L.dpiv);   // row exchanged with row k at step k
     for (int i = tid; i < N; i += kThreads) {
         double m = 0.0;
         for (int j = 0; j < N; ++j) m = fmax(m, fabs(A[(long)i * N + j]));
@@ -689,6 +695,7 @@ __device__ bool dense_solve(const DevNet& net, double* W, const Lay& L, DenseSha
                     if (ds.val[q] > b0 || (ds.val[q] == b0 && ds.idx[q] < i0)) { b0 = ds.val[q]; i0 = ds.idx[q]; }
                 ds.piv = i0;
                 ds.pv = b0;
+                piv[k] = i0;
             }
             __syncthreads();
             if (!(ds.pv > 0.0) || !isfinite(ds.pv)) return false;
@@ -751,9 +758,41 @@ __device__ bool dense_solve(const DevNet& net, double* W, const Lay& L, DenseSha
     return true;
 }
 
+// v <- K^{-1} v with the factors dense_solve left (row scaling, the recorded row
+// exchanges, unit lower and upper triangular solves, column scaling).
+__device__ void dense_resolve(const DevNet& net, double* W, const Lay& L, double* v) {
+    const int tid = threadIdx.x, N = 4 * net.nb;
+    const double* A = W + L.dense;
+    const double* rs = W + L.drs;
+    const double* cs = W + L.cs;
+    const int* piv = reinterpret_cast<const int*>(W + L.dpiv);
+    for (int w = tid; w < N; w += kThreads) v[w] *= rs[w];
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < N; ++k) {
+            const int p = piv[k];
+            if (p != k) { const double t = v[k]; v[k] = v[p]; v[p] = t; }
+        }
+    __syncthreads();
+    for (int k = 0; k < N - 1; ++k) {
+        const double vk = v[k];
+        for (int i = k + 1 + tid; i < N; i += kThreads) v[i] -= A[(long)i * N + k] * vk;
+        __syncthreads();
+    }
+    for (int k = N - 1; k >= 0; --k) {
+        if (tid == 0) v[k] /= A[(long)k * N + k];
+        __syncthreads();
+        const double vk = v[k];
+        for (int i = tid; i < k; i += kThreads) v[i] -= A[(long)i * N + k] * vk;
+        __syncthreads();
+    }
+    for (int w = tid; w < N; w += kThreads) v[w] *= cs[w];
+    __syncthreads();
+}
+
 struct Scal {          // per-scenario scalars in shared memory
     double gamma, f, f_prev, lref, dlref, ap, ad;
-    double red[10];
+    double red[kRedMax];
     double niq, shed;  // number of inequality rows; load outside the main island (p.u.)
     int fail;
     int conv;
@@ -1192,6 +1231,27 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
                     if (!dense_solve(net, W, L, ds)) sc.fail = 1;
                     __syncthreads();
                     if (sc.fail) break;
+                    // FP64 refinement of the backstop's solution with its own factors; the
+                    // best iterate is kept (refinement diverges on a system too ill-conditioned
+                    // for FP64, and then the backstop's first solution is the best there is)
+                    double best = INFINITY;
+                    for (int ref_step = 0;; ++ref_step) {
+                        double v1[1] = {kkt_residual(net, W, L, W + L.x, W + L.rv)};
+                        const int ops1[1] = {0};
+                        block_reduce<1>(rb, v1, ops1, sc.red);
+                        const double om_now = sc.red[0];
+                        if (ref_step > 0 && !(om_now < best)) {          // no progress: back to the best
+                            for (int w = tid; w < 4 * nb; w += kThreads) W[L.x + w] = W[L.gxb + w];
+                            __syncthreads();
+                            break;
+                        }
+                        best = om_now;
+                        if (om_now <= kRefineTol || ref_step == kRefineSteps) break;
+                        for (int w = tid; w < 4 * nb; w += kThreads) W[L.gxb + w] = W[L.x + w];
+                        dense_resolve(net, W, L, W + L.rv);
+                        for (int w = tid; w < 4 * nb; w += kThreads) W[L.x + w] += W[L.rv + w];
+                        __syncthreads();
+                    }
                 }
             }
             // ---------------- recover the eliminated steps, dz, dmu, ratios ----------------
