@@ -28,6 +28,9 @@ Module map (paper passages in parentheses):
 * ``pipeline``  one scenario end to end and the severity class (Sections II-A,
                  II-B).
 * ``risk``      the Risk Index of Eq. 3 computed exactly with rationals.
+* ``variants``  other backward-stable solves of the Newton systems (permuted LU,
+                 Bunch-Kaufman LDL^T, refinement with exactly rounded residuals):
+                 which scenarios' outcomes FP64 rounding decides.
 * ``island``    main-island OPF of an islanded scenario with the reference
                  re-assigned, and its load shed (Sections II-A, V-A, VI: the
                  extension those passages point to).

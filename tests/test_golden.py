@@ -5,6 +5,7 @@ damping ratio to 1e-9 relative (BLAS builds may round differently)."""
 import importlib.util
 import json
 import os
+import sys
 
 import numpy as np
 import pytest
@@ -81,3 +82,25 @@ def test_full_study_tables_come_from_the_current_oracle():
             for key, name in (("cost", "cost"), ("max_re", "max_re"), ("min_zeta", "min_zeta")):
                 a, b = r[key], g[f"{lv}_{name}"][q]
                 assert (np.isnan(a) and np.isnan(b)) or abs(a - b) <= 1e-9 * max(1.0, abs(b)), (lv, q, key)
+
+
+def test_rounding_variant_table_comes_from_the_current_oracle():
+    """tests/golden/case118_rounding_variants.json (make_rounding_variants.py): the
+    current oracle's hash, every listed scenario, every variant, and -- on the kind of
+    machine that wrote it -- two of its outcomes re-derived from the oracle."""
+    import platform
+    sys.path.insert(0, HERE)
+    import make_rounding_variants as mrv
+    from oracle import variants
+    d = json.load(open(mrv.OUT))
+    assert d["meta"]["oracle"] == _make_golden().oracle_hash()
+    assert d["meta"]["variants"] == variants.names()
+    assert [(e["level"], e["i"], e["j"]) for e in d["scenarios"]] == [tuple(s) for s in mrv.SCENARIOS]
+    for e in d["scenarios"]:
+        assert set(e["outcomes"]) == set(variants.names())
+        assert len({tuple(v) for v in e["outcomes"].values()}) > 1      # each is rounding-decided
+    if platform.machine() != d["meta"]["machine"]:
+        pytest.skip("outcomes depend on the machine's floating-point library")
+    e = next(e for e in d["scenarios"] if (e["level"], e["i"], e["j"]) == (1, 48, 192))
+    outs = variants.outcomes(synth.case118(), 1, 48, 192, which=("lu", "perm18"), processes=2)
+    assert outs == {k: tuple(e["outcomes"][k]) for k in ("lu", "perm18")}
