@@ -879,6 +879,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, int max_it,
            double* scratch, size_t per_cta, Lay L, int* counter) {
     __shared__ RedBuf rb;
+    __shared__ double fsum[kThreads];      // partial update sums of the narrow factorisation levels
     __shared__ Scal sc;
     const int tid = threadIdx.x;
     double* W = scratch + per_cta * blockIdx.x;
@@ -1172,18 +1173,46 @@ opf_kernel(DevNet net, EvalArgs a, const int* islanded, OpfOut o, double tol, in
             __syncthreads();
             // ---------------- block LDL^T, level by level ----------------
             for (int lev = 0; lev < net.nlevels; ++lev) {
-                const int t0 = net.tgt_ptr[lev], t1 = net.tgt_ptr[lev + 1];
-                for (int w = tid; w < 16 * (t1 - t0); w += kThreads) {
-                    const int tg = net.tgt[t0 + (w >> 4)];
-                    const int r = (w & 15) >> 2, c = w & 3;
-                    double* A = (tg < nb) ? (W + L.Db + 16 * tg) : (W + L.Ub + 16 * (tg - nb));
-                    double acc = A[4 * r + c];
-                    for (int u = net.upd_ptr[tg]; u < net.upd_ptr[tg + 1]; ++u) {
-                        const double* La = W + L.Lb + 16 * net.upd_a[u] + 4 * r;
-                        const double* Ubb = W + L.Ub + 16 * net.upd_b[u] + 4 * c;
-                        acc -= La[0] * Ubb[0] + La[1] * Ubb[1] + La[2] * Ubb[2] + La[3] * Ubb[3];
+                const int t0 = net.tgt_ptr[lev], t1 = net.tgt_ptr[lev + 1], nt = t1 - t0;
+                if (nt > 0 && 32 * nt <= kThreads) {
+                    // few targets (the top of the elimination tree, where each target has the
+                    // longest update lists): S groups of 16 threads per target each sum every
+                    // S-th update, then one thread per entry subtracts the S partial sums
+                    const int S = kThreads / (16 * nt);
+                    if (tid < 16 * nt * S) {
+                        const int ti = tid / (16 * S), g = (tid / 16) % S, e = tid & 15;
+                        const int tg = net.tgt[t0 + ti];
+                        const int r = e >> 2, c = e & 3;
+                        double acc = 0.0;
+                        for (int u = net.upd_ptr[tg] + g; u < net.upd_ptr[tg + 1]; u += S) {
+                            const double* La = W + L.Lb + 16 * net.upd_a[u] + 4 * r;
+                            const double* Ubb = W + L.Ub + 16 * net.upd_b[u] + 4 * c;
+                            acc += La[0] * Ubb[0] + La[1] * Ubb[1] + La[2] * Ubb[2] + La[3] * Ubb[3];
+                        }
+                        fsum[tid] = acc;
                     }
-                    A[4 * r + c] = acc;
+                    __syncthreads();
+                    if (tid < 16 * nt) {
+                        const int ti = tid >> 4, e = tid & 15;
+                        const int tg = net.tgt[t0 + ti];
+                        double* A = (tg < nb) ? (W + L.Db + 16 * tg) : (W + L.Ub + 16 * (tg - nb));
+                        double part = 0.0;
+                        for (int g = 0; g < S; ++g) part += fsum[ti * 16 * S + g * 16 + e];
+                        A[e] -= part;
+                    }
+                } else {
+                    for (int w = tid; w < 16 * nt; w += kThreads) {
+                        const int tg = net.tgt[t0 + (w >> 4)];
+                        const int r = (w & 15) >> 2, c = w & 3;
+                        double* A = (tg < nb) ? (W + L.Db + 16 * tg) : (W + L.Ub + 16 * (tg - nb));
+                        double acc = A[4 * r + c];
+                        for (int u = net.upd_ptr[tg]; u < net.upd_ptr[tg + 1]; ++u) {
+                            const double* La = W + L.Lb + 16 * net.upd_a[u] + 4 * r;
+                            const double* Ubb = W + L.Ub + 16 * net.upd_b[u] + 4 * c;
+                            acc -= La[0] * Ubb[0] + La[1] * Ubb[1] + La[2] * Ubb[2] + La[3] * Ubb[3];
+                        }
+                        A[4 * r + c] = acc;
+                    }
                 }
                 __syncthreads();
                 {
