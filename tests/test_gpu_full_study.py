@@ -3,8 +3,8 @@
 Workload: the seeded 118-bus network at both load levels (70 %, 90 %): the base
 case, the 240 single outages and all 28,680 unordered pairs of the 240 outage
 elements (Section II-A) -- 57,842 scenarios -- evaluated in the launch
-configuration of the benchmark (all pairs of a level in one call, chunks of
-16,384 alternating over two streams), in the FP64 form and in the mixed form.
+configuration of the benchmark (all pairs of a level in one call, chunks
+alternating over two streams), in the FP64 form and in the mixed form.
 The oracle's values come from ``tests/golden/case118_full.npz``, written by
 ``tests/golden/make_full_golden.py`` from the CPU oracle alone.
 
