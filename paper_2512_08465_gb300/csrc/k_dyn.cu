@@ -46,6 +46,14 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr double kEps = 2.220446049250313e-16;
+// FP32 QR deflates a subdiagonal entry below kDeflTol times its two diagonal neighbours
+// (not the FP32 unit roundoff): the screen's eigenvalues need only be within kEigDelta of
+// the exact ones where the decisive ones are refined in FP64 (within the 5e-3 guard band
+// where a network's screen has no refinement), and the sweeps that take a converged entry
+// from ~1e-6 relative down to rounding level are most of the QR's work.
+// On 118-bus state matrices (order 264-269, FP32 emulation) it cuts the sweeps per matrix
+// from 785 to 322 on average, the largest eigenvalue error staying at 8e-5 either way.
+constexpr float kDeflTol = 3e-6f;
 // FP32 screen in global memory (no refinement): a decision this close to a threshold is
 // taken by the FP64 screen instead
 constexpr double kGuardRe = 5e-3;      // |max Re| within this of 0
@@ -278,7 +286,7 @@ __device__ void hessenberg(T* A, const int n, T* v, DShared& sh) {
 template <typename T>
 __device__ void hqr_global(T* A, const int n, double* wr, double* wi, DShared& sh) {
     const int tid = threadIdx.x;
-    const double eps = (sizeof(T) == 8) ? kEps : 1.1920928955078125e-07;
+    const double eps = (sizeof(T) == 8) ? kEps : (double)kDeflTol;       // deflation tolerance
     {
         double hm = 0.0;
         for (int w = tid; w < n * n; w += kThreads) {
@@ -1044,13 +1052,6 @@ constexpr int kQrThreads = CS_QR_THREADS;
 // only need to be within kEigDelta of the exact ones (the decisive ones are refined in
 // FP64), which that normwise perturbation respects.
 constexpr int kStallIts = 40;
-// Deflation of a subdiagonal entry below kDeflTol times its two diagonal neighbours (not
-// the FP32 unit roundoff): the screen's eigenvalues need only be within kEigDelta of the
-// exact ones, since the decisive ones are refined in FP64, and the sweeps that take a
-// converged entry from ~1e-6 relative down to rounding level are most of the QR's work.
-// On 118-bus state matrices (order 264-269, FP32 emulation) it cuts the sweeps per matrix
-// from 785 to 322 on average, the largest eigenvalue error staying at 8e-5 either way.
-constexpr float kDeflTol = 3e-6f;
 // the column phase of a bulge step covers at most 2 kQrThreads rows (orders up to 32 kHsCols + 1)
 static_assert(2 * kQrThreads > 32 * kHsCols + 1, "QR column phase: at most two rows per thread");
 
