@@ -54,7 +54,7 @@ namespace {
 #define CS_OPF_THREADS 128
 #endif
 #ifndef CS_OPF_CTAS
-#define CS_OPF_CTAS 3
+#define CS_OPF_CTAS 4
 #endif
 constexpr int kThreads = CS_OPF_THREADS;   // threads per scenario CTA
 constexpr int kCtasPerSm = CS_OPF_CTAS;    // resident CTAs per SM the register budget is sized for
