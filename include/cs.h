@@ -83,7 +83,7 @@ typedef struct {
     int32_t opf_max_it;        /* interior-point iteration cap */
     int32_t require_secure_base; /* 1: cs_load_network fails with CS_E_BASE_INSECURE */
     int32_t ctas_per_sm;       /* resident scenario blocks per SM; 0 = automatic */
-    int32_t chunk;             /* scenarios per internal batch; 0 = automatic (4096, fewer where a
+    int32_t chunk;             /* scenarios per internal batch; 0 = automatic (8192, fewer where a
                                   network's workspaces would pass ~6 GB) */
     int32_t precision;         /* CS_PREC_FP64 (default) or CS_PREC_MIXED */
     int64_t hbm_budget;        /* device bytes the context may hold (networks, workspaces,

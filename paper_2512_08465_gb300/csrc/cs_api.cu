@@ -32,9 +32,11 @@ int64_t default_chunk(const cs_ctx* ctx, const Network& net) {
         return std::max<int64_t>(64, std::min<int64_t>(16384, (int64_t)(6e9 / (double)per)));
     }
     // Chunks alternate over two streams, so that one chunk's small-signal kernels run beside
-    // the next one's OPF; smaller chunks overlap more.  Measured on the 118-bus study (both
-    // levels, mixed form): 8,076 ms with chunks of 16,384, 7,950 with 8,192, 7,916 with 4,096.
-    return 4096;
+    // the next one's OPF; a chunk must still give each of the OPF's resident CTAs (four per SM)
+    // a dozen scenarios.  Measured on the 118-bus study (both levels, mixed form): 7,870 ms
+    // with chunks of 4,096, 7,444 with 6,144, 7,400 with 8,192; on another box 7,540 with
+    // 8,192, ~7,900 with 12,288 and with 16,384.
+    return 8192;
 }
 
 namespace {

@@ -179,7 +179,7 @@ cs_status cuda_fail(cs_ctx* c, cudaError_t e, const char* where);
     } while (0)
 
 // Chunk of scenarios per internal batch for a context and network (0 in the options:
-// 4096, or what fits ~6 GB for mixed-form networks whose state matrices take the
+// 8192, or what fits ~6 GB for mixed-form networks whose state matrices take the
 // tensor-core path).
 int64_t default_chunk(const cs_ctx* ctx, const Network& net);
 
